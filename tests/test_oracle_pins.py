@@ -1,0 +1,478 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these retypes the oracle's formulas: each checks a closed form, an
+invariant, a special case that reduces to a textbook routine, a hand-computed
+value or a brute-force count, chosen so that a dropped term, a wrong sign, a
+swapped index or a transposed operand in the oracle fails at least one.
+"""
+
+import numpy as np
+import pytest
+from scipy import stats
+
+pytestmark = []
+
+CFG1 = dict(L=8, F=2, log2T=14, n_min=16, n_max=256, width=32, hidden=2, lambda_d=0.1, lambda_sigma=0.0)
+CFG2 = dict(L=16, F=2, log2T=19, n_min=16, n_max=2048, width=64, hidden=2, lambda_d=0.1, lambda_sigma=0.0)
+
+
+# ----------------------------------------------------------------- hash grid
+def test_level_resolutions_hand_computed(orc):
+    # b = 16^(1/7) = 1.48599...; 16 b^l = 16, 23.78, 35.33, 52.50, 78.02, 115.93, 172.27, 256
+    a = orc.Arch(**CFG1)
+    assert [orc.level_res(a, l) for l in range(8)] == [16, 23, 35, 52, 78, 115, 172, 256]
+    # b = 128^(1/15) = 1.38191...; the finest level must land exactly on N_max
+    a2 = orc.Arch(**CFG2)
+    res = [orc.level_res(a2, l) for l in range(16)]
+    assert res[0] == 16 and res[-1] == 2048
+    assert res == [16, 22, 30, 42, 58, 80, 111, 153, 212, 294, 406, 561, 776, 1072, 1482, 2048]
+
+
+def test_dense_hashed_split_and_sizes(orc):
+    # cfg 1: (17^3 = 4913) and (24^3 = 13824) fit in 2^14 = 16384; 36^3 = 46656 does not
+    a = orc.Arch(**CFG1)
+    assert [orc.level_dense(a, l) for l in range(8)] == [True, True] + [False] * 6
+    assert orc.n_hash_params(a) == 2 * (4913 + 13824 + 6 * 16384)
+    # cfg 2: 17^3, 23^3, 31^3, 43^3, 59^3 fit in 2^19; 81^3 = 531441 > 524288
+    a2 = orc.Arch(**CFG2)
+    assert [orc.level_dense(a2, l) for l in range(16)] == [True] * 5 + [False] * 11
+    assert orc.n_hash_params(a2) == 2 * (4913 + 12167 + 29791 + 79507 + 205379 + 11 * 524288)
+    # MLP: 32->64, 64->64, 64->4 without biases
+    assert orc.n_mlp_params(a2) == 32 * 64 + 64 * 64 + 4 * 64
+    assert orc.param_count(a2) == orc.n_hash_params(a2) + 6400
+
+
+def test_hash_index_hand_values(orc):
+    a = orc.Arch(**CFG1)
+    l = 5  # hashed level, T = 2^14
+    assert orc.grid_index(a, l, 1, 0, 0) == 1  # pi_1 = 1
+    assert orc.grid_index(a, l, 0, 1, 0) == 0x9E3779B1 & 0x3FFF  # 2654435761 mod 2^14 = 14769
+    assert orc.grid_index(a, l, 0, 0, 1) == 0x30025795 & 0x3FFF  # 805459861 mod 2^14 = 6037
+    assert orc.grid_index(a, l, 1, 1, 1) == (1 ^ 0x39B1 ^ 0x1795)  # = 11813
+    # wraparound of the uint32 products
+    assert orc.grid_index(a, l, 0, 3, 0) == (3 * 2654435761 % 2**32) & 0x3FFF
+
+
+def test_dense_index_is_a_bijection(orc):
+    a = orc.Arch(**CFG1)
+    for l in (0, 1):
+        n1 = orc.level_res(a, l) + 1
+        seen = np.zeros(n1 ** 3, dtype=np.int32)
+        for z in range(n1):
+            for y in range(n1):
+                for x in (0, 1, n1 - 1):
+                    seen[orc.grid_index(a, l, x, y, z)] += 1
+        # x covers 0,1,N per (y,z): 3 n1^2 distinct entries, never out of range
+        assert seen.sum() == 3 * n1 * n1 and seen.max() == 1
+        assert orc.grid_index(a, l, n1 - 1, n1 - 1, n1 - 1) == n1 ** 3 - 1
+
+
+def test_hashed_index_x_is_a_permutation(orc):
+    # with pi_1 = 1, x -> x xor h(y, z) mod T is a bijection of [0, T) for fixed (y, z)
+    a = orc.Arch(L=2, F=2, log2T=8, n_min=16, n_max=600, width=16, hidden=1)
+    assert not orc.level_dense(a, 1)
+    idx = {orc.grid_index(a, 1, x, 7, 11) for x in range(256)}
+    assert idx == set(range(256))
+
+
+# -------------------------------------------------------------------- encoding
+def _dense_arch(orc):
+    # every level collision-free: (8+1)^3 = 729 <= 4096
+    a = orc.Arch(L=3, F=2, log2T=12, n_min=2, n_max=8, width=16, hidden=1)
+    assert all(orc.level_dense(a, l) for l in range(3))
+    return a
+
+
+def test_encoding_reproduces_affine_fields(orc):
+    a = _dense_arch(orc)
+    rng = np.random.default_rng(0)
+    theta = np.zeros(orc.param_count(a))
+    coef = rng.normal(size=(a.L, a.F, 4))  # feature f of level l = c0 + c . vertex / N_l
+    for l in range(a.L):
+        n = orc.level_res(a, l)
+        off = orc.level_offset(a, l)
+        for z in range(n + 1):
+            for y in range(n + 1):
+                for x in range(n + 1):
+                    i = orc.grid_index(a, l, x, y, z)
+                    for f in range(a.F):
+                        c = coef[l, f]
+                        theta[off + i * a.F + f] = c[0] + c[1] * x / n + c[2] * y / n + c[3] * z / n
+    for p in rng.random((50, 3)):
+        enc = orc.encode(a, theta, p)
+        want = [coef[l, f, 0] + coef[l, f, 1:] @ p for l in range(a.L) for f in range(a.F)]
+        np.testing.assert_allclose(enc, want, rtol=0, atol=1e-12)
+    # p on the far faces uses the last cell with weight 1 (corner clamp)
+    enc = orc.encode(a, theta, np.ones(3))
+    want = [coef[l, f, 0] + coef[l, f, 1:].sum() for l in range(a.L) for f in range(a.F)]
+    np.testing.assert_allclose(enc, want, atol=1e-12)
+
+
+def test_encoding_partition_of_unity_and_vertex_lookup(orc):
+    a = orc.Arch(**CFG1)
+    rng = np.random.default_rng(1)
+    theta = np.zeros(orc.param_count(a))
+    # constant tables -> every level's encoding equals the constant (weights sum to 1)
+    for l in range(a.L):
+        off = orc.level_offset(a, l)
+        n = orc.level_entries(a, l)
+        theta[off:off + n * a.F].reshape(n, a.F)[:] = [l + 1.0, -(l + 1.0)]
+    for p in rng.random((20, 3)):
+        enc = orc.encode(a, theta, p).reshape(a.L, a.F)
+        np.testing.assert_allclose(enc[:, 0], np.arange(1, a.L + 1), atol=1e-12)
+        np.testing.assert_allclose(enc[:, 1], -np.arange(1, a.L + 1), atol=1e-12)
+    # a table holding its own index, probed exactly on a vertex, returns the hash of that vertex
+    l = 5
+    n = orc.level_res(a, l)
+    off = orc.level_offset(a, l)
+    theta[off:off + orc.level_entries(a, l) * a.F] = np.repeat(np.arange(orc.level_entries(a, l)), a.F)
+    v = (3, 5, 7)
+    p = np.array(v, dtype=np.float64) / n
+    enc = orc.encode(a, theta, p).reshape(a.L, a.F)
+    assert enc[l, 0] == float((3 ^ (5 * 2654435761) ^ (7 * 805459861)) % 2**32 & 0x3FFF)
+
+
+def test_encoding_backward_is_the_transpose(orc):
+    # <J x, y> = <x, J^T y> for the linear map theta -> enc
+    a = orc.Arch(L=4, F=2, log2T=12, n_min=4, n_max=64, width=16, hidden=1)
+    rng = np.random.default_rng(2)
+    n = orc.param_count(a)
+    for p in rng.random((5, 3)):
+        x = rng.normal(size=n)
+        y = rng.normal(size=a.n_in)
+        lhs = orc.encode(a, x, p) @ y
+        rhs = orc.encode_backward(a, p, y, n) @ x
+        assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + 1)
+
+
+# ------------------------------------------------------------------------- MLP
+def test_mlp_matches_numpy_matmul_chain(orc):
+    a = orc.Arch(**CFG2)
+    rng = np.random.default_rng(3)
+    theta = rng.normal(size=orc.param_count(a)) * 0.3
+    Ws = []
+    for layer, (o_, i_) in enumerate(a.mlp_shapes()):
+        off = orc.mlp_offset(a, layer)
+        Ws.append(theta[off:off + o_ * i_].reshape(o_, i_))
+    for _ in range(5):
+        x = rng.normal(size=a.n_in)
+        h = x
+        hs = []
+        for W in Ws[:-1]:
+            h = np.maximum(W @ h, 0.0)
+            hs.append(h)
+        out = Ws[-1] @ h
+        acts, o = orc.mlp_forward(a, theta, x)
+        np.testing.assert_allclose(o, out, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(acts, np.concatenate(hs), rtol=1e-12, atol=1e-12)
+        # backward = transposed products with the ReLU masks
+        dout = rng.normal(size=4)
+        g, denc = orc.mlp_backward(a, theta, x, acts, dout)
+        dh = Ws[-1].T @ dout
+        gw = [np.outer(dout, hs[-1])]
+        for k in range(len(Ws) - 2, -1, -1):
+            dh = dh * (hs[k] > 0)
+            below = hs[k - 1] if k > 0 else x
+            gw.append(np.outer(dh, below))
+            dh = Ws[k].T @ dh
+        np.testing.assert_allclose(denc, dh, rtol=1e-10, atol=1e-12)
+        for layer, gwl in zip(range(len(Ws) - 1, -1, -1), gw):
+            off = orc.mlp_offset(a, layer)
+            np.testing.assert_allclose(g[off:off + gwl.size], gwl.ravel(), rtol=1e-10, atol=1e-12)
+
+
+def test_mlp_zero_weights(orc):
+    a = orc.Arch(**CFG1)
+    theta = np.zeros(orc.param_count(a))
+    acts, out = orc.mlp_forward(a, theta, np.ones(a.n_in))
+    assert np.all(out == 0) and np.all(acts == 0)
+
+
+# -------------------------------------------------------------------- ray box
+def test_ray_box_cases(orc):
+    hit, tn, tf = orc.ray_box([-1.0, 0.5, 0.5], [1.0, 0.0, 0.0])
+    assert hit and tn == 1.0 and tf == 2.0
+    hit, tn, tf = orc.ray_box([0.5, 0.5, 0.5], [0.0, 0.0, 1.0])  # starts inside
+    assert hit and tn == 0.0 and tf == 0.5
+    s = 1 / np.sqrt(3)
+    hit, tn, tf = orc.ray_box([-1.0, -1.0, -1.0], [s, s, s])  # diagonal
+    assert hit and abs(tn - np.sqrt(3)) < 1e-12 and abs(tf - 2 * np.sqrt(3)) < 1e-12
+    assert not orc.ray_box([-1.0, 2.0, 0.5], [1.0, 0.0, 0.0])[0]  # parallel, outside in y
+    assert not orc.ray_box([2.0, 0.5, 0.5], [1.0, 0.0, 0.0])[0]  # points away
+
+
+# --------------------------------------------------------------- prior lookup
+def test_prior_lookup_affine_and_centres(orc):
+    R = 8
+    c = (np.arange(R) + 0.5) / R
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    grid = 1.5 + 2.0 * x - 3.0 * y + 0.5 * z
+    rng = np.random.default_rng(4)
+    for p in rng.uniform(0.5 / R, 1 - 0.5 / R, (50, 3)):
+        assert abs(orc.prior_lookup(grid, p) - (1.5 + 2 * p[0] - 3 * p[1] + 0.5 * p[2])) < 1e-12
+    g2 = rng.random((R, R, R))
+    for (i, j, k) in [(0, 0, 0), (3, 5, 7), (7, 7, 7), (2, 6, 1)]:
+        p = np.array([(i + 0.5) / R, (j + 0.5) / R, (k + 0.5) / R])
+        assert abs(orc.prior_lookup(g2, p) - g2[k, j, i]) < 1e-12
+    # outside the centre lattice the value is held constant (clamped)
+    assert abs(orc.prior_lookup(g2, [0.0, 0.0, 0.0]) - g2[0, 0, 0]) < 1e-12
+    assert abs(orc.prior_lookup(g2, [1.0, 1.0, 1.0]) - g2[-1, -1, -1]) < 1e-12
+
+
+# ------------------------------------------------------------------- sampling
+def _straight_ray():
+    return np.array([-1.0, 0.5, 0.5]), np.array([1.0, 0.0, 0.0])  # tn = 1, tf = 2
+
+
+def test_constant_density_slab_closed_form(orc):
+    R, nc, nr = 8, 32, 16
+    sigma0 = 3.0
+    grid = np.full((R, R, R), sigma0)
+    o, d = _straight_ray()
+    u = (np.arange(nr) + 0.5) / nr
+    out = orc.sample_ray(grid, o, d, nc, nr, 1e-4, u)
+    delta = 1.0 / nc
+    i = np.arange(nc)
+    rho = (1 - np.exp(-sigma0 * delta)) * np.exp(-sigma0 * delta * i)  # T at depth s = exp(-sigma s)
+    np.testing.assert_allclose(out["probe_sigma"], sigma0, rtol=1e-14)
+    np.testing.assert_allclose(out["rho_term"], rho, rtol=1e-12)
+    k = np.arange(nc + 1)
+    cdf = (1 - np.exp(-sigma0 * delta * k)) / (1 - np.exp(-sigma0 * delta * nc))
+    np.testing.assert_allclose(out["cdf"], cdf, rtol=1e-12, atol=1e-15)
+    assert not out["escape"] and out["tn"] == 1.0 and out["tf"] == 2.0
+    # inverse of the piecewise-linear CDF evaluated at the samples gives back u
+    t = out["t"]
+    s = (t - 1.0) / delta
+    cdf_at = np.interp(s, k, cdf)
+    np.testing.assert_allclose(cdf_at, u, atol=1e-12)
+
+
+def test_cdf_invert_dyadic_edges_and_empty_bins(orc):
+    # masses in multiples of 2^-10 so every edge is exact
+    mass = np.array([0, 256, 0, 128, 512, 0, 0, 128], dtype=np.float64) / 1024
+    cdf = np.concatenate([[0.0], np.cumsum(mass)])
+    u = np.array([0.0, 0.25 - 2**-20, 0.25, 0.375, 0.5, 0.875, 0.875 + 2**-11, 1 - 2**-24])
+    bins, t = orc.cdf_invert(cdf, u, 2.0, 10.0)
+    # u = 0 -> first non-empty bin; u on an edge -> the next non-empty bin (strict >)
+    assert bins.tolist() == [1, 1, 3, 4, 4, 7, 7, 7]
+    assert 0 not in bins and 2 not in bins and 5 not in bins and 6 not in bins
+    # positions: bin b covers [2 + b, 3 + b]; linear inside the bin
+    assert t[0] == 3.0 and t[2] == 5.0 and t[3] == 6.0
+    assert abs(t[4] - (6.0 + 0.25)) < 1e-15  # (0.5 - 0.375) / 0.5 = 1/4 of bin 4
+
+
+def test_escape_gives_uniform_bins(orc):
+    R, nc, nr = 8, 32, 32
+    grid = np.zeros((R, R, R))
+    o, d = _straight_ray()
+    u = np.random.default_rng(5).random(nr)
+    out = orc.sample_ray(grid, o, d, nc, nr, 1e-4, u)
+    assert out["escape"]
+    np.testing.assert_array_equal(out["bins"], np.floor(u * nc).astype(int))
+    np.testing.assert_allclose(out["t"], 1.0 + u, atol=1e-14)
+    # a density just under / over the threshold: total = 1 - exp(-sigma * 1)
+    for sig, esc in [(0.99e-4, True), (1.01e-4, False)]:
+        out = orc.sample_ray(np.full((R, R, R), sig), o, d, nc, nr, 1e-4, u)
+        assert out["escape"] == esc
+
+
+def test_one_hot_with_opaque_voxels(orc):
+    R, nc, nr = 16, 32, 16
+    grid = np.zeros((R, R, R))
+    grid[:, :, 10:] = 1e30  # x >= 10/16 opaque
+    o, d = _straight_ray()
+    u = np.random.default_rng(6).random(nr)
+    out = orc.sample_ray(grid, o, d, nc, nr, 1e-4, u)
+    b = out["bins"]
+    assert np.all(b == b[0])
+    assert out["probe_sigma"][b[0]] > 0 and np.all(out["probe_sigma"][:b[0]] == 0)
+    assert out["rho_term"][b[0]] == 1.0 and np.all(np.delete(out["rho_term"], b[0]) == 0)
+
+
+def test_sample_counts_match_bin_masses(orc):
+    R, nc = 8, 16
+    rng = np.random.default_rng(7)
+    grid = rng.uniform(0, 6, (R, R, R))
+    o, d = _straight_ray()
+    nr = 64
+    u = (np.arange(nr) + 0.5) / nr
+    out = orc.sample_ray(grid, o, d, nc, nr, 1e-4, u)
+    p = np.diff(out["cdf"])
+    counts = np.bincount(out["bins"], minlength=nc)
+    assert np.all(np.abs(counts - nr * p) <= 1.0 + 1e-9)
+    # chi^2 of 10^6 random draws against the bin masses
+    uu = rng.random(1_000_000)
+    bins, _ = orc.cdf_invert(out["cdf"], uu, out["tn"], out["tf"])
+    counts = np.bincount(bins, minlength=nc)
+    keep = p > 0
+    pval = stats.chisquare(counts[keep], 1_000_000 * p[keep]).pvalue
+    assert pval > 1e-4, pval
+
+
+# ------------------------------------------------------------------ rendering
+def test_composite_closed_forms(orc):
+    nr = 12
+    t = np.linspace(1.0, 2.0, nr, endpoint=False)
+    tf = 2.0
+    rng = np.random.default_rng(8)
+    c = rng.random((nr, 3))
+    # sigma = 0 -> nothing
+    w, Cc, D, A = orc.composite(np.zeros(nr), c, t, tf)
+    assert A == 0 and D == 0 and np.all(Cc == 0)
+    # constant density: A = 1 - exp(-sigma (tf - t_0)); w_k = exp(-sigma (t_k - t_0)) (1 - exp(-sigma delta))
+    s0 = 2.5
+    w, Cc, D, A = orc.composite(np.full(nr, s0), c, t, tf)
+    assert abs(A - (1 - np.exp(-s0 * (tf - t[0])))) < 1e-14
+    dl = np.diff(np.append(t, tf))
+    np.testing.assert_allclose(w, np.exp(-s0 * (t - t[0])) * (1 - np.exp(-s0 * dl)), rtol=1e-13)
+    np.testing.assert_allclose(Cc, w @ c, rtol=1e-13)
+    assert abs(D - w @ t) < 1e-13
+    # constant colour -> C = A c
+    w, Cc, D, A = orc.composite(rng.uniform(0, 4, nr), np.tile([0.2, 0.5, 0.9], (nr, 1)), t, tf)
+    np.testing.assert_allclose(Cc, A * np.array([0.2, 0.5, 0.9]), rtol=1e-13)
+    # a single opaque sample takes all the weight
+    sig = np.zeros(nr)
+    sig[4] = 1e30
+    w, Cc, D, A = orc.composite(sig, c, t, tf)
+    assert w[4] == 1.0 and np.all(np.delete(w, 4) == 0) and D == t[4]
+
+
+def test_ray_loss_hand_values(orc):
+    L, gC, gD, gA = orc.ray_loss(True, [0.5, 0.2, 0.1], 1.0, 0.7, [0.4, 0.4, 0.1], 1.5, None, 0.1)
+    assert abs(L - (0.01 + 0.04 + 0.0 + 0.1 * 0.5)) < 1e-15
+    np.testing.assert_allclose(gC, [0.2, -0.4, 0.0], atol=1e-15)
+    assert gD == -0.1 and gA == 0.0
+    # background: C + (1 - A) C_rand - C_rand = C - A C_rand = (0.2, -0.2, -0.3)
+    L, gC, gD, gA = orc.ray_loss(False, [0.3, 0.0, 0.0], 0.0, 0.5, [0, 0, 0], 0.0, [0.2, 0.4, 0.6], 0.1)
+    assert abs(L - 0.17) < 1e-15
+    np.testing.assert_allclose(gC, [0.4, -0.4, -0.6], atol=1e-15)
+    assert gD == 0.0 and abs(gA - (-(0.4 * 0.2 - 0.4 * 0.4 - 0.6 * 0.6))) < 1e-15
+
+
+def test_batch_one_ray_two_samples_by_hand(orc):
+    # zero MLP -> sigma = exp(0) = 1, c = sigmoid(0) = 1/2 at every sample
+    a = orc.Arch(L=2, F=2, log2T=10, n_min=2, n_max=4, width=8, hidden=1, lambda_d=0.1)
+    theta = np.zeros(orc.param_count(a))
+    rays = dict(o=[[-1.0, 0.5, 0.5]], d=[[1.0, 0.0, 0.0]], rgb=[[0.1, 0.2, 0.3]], depth=[1.4],
+                is_obj=[1])
+    t_in = np.array([[1.2, 1.7]])
+    out = orc.batch(a, theta, np.zeros((2, 2, 2)), rays, 4, 2, t_in=t_in)
+    w0 = 1 - np.exp(-0.5)
+    w1 = np.exp(-0.5) * (1 - np.exp(-0.3))
+    A = w0 + w1
+    D = w0 * 1.2 + w1 * 1.7
+    assert abs(out["acc"][0] - A) < 1e-15 and abs(out["depth"][0] - D) < 1e-15
+    np.testing.assert_allclose(out["rgb"][0], 0.5 * A, rtol=1e-15)
+    want = (0.5 * A - 0.1) ** 2 + (0.5 * A - 0.2) ** 2 + (0.5 * A - 0.3) ** 2 + 0.1 * abs(D - 1.4)
+    assert abs(out["loss"] - want) < 1e-15
+
+
+# ------------------------------------------------------------------ gradients
+def _fd_setup(orc, lambda_sigma=0.0):
+    from synth import scene_sphere_box, cameras_on_sphere, make_ray_pool, prior_grid, sample_batch
+    from synth import stratified_uniforms, random_colours, init_params
+
+    a = orc.Arch(L=4, F=2, log2T=12, n_min=4, n_max=32, width=16, hidden=2, lambda_d=0.1,
+                 lambda_sigma=lambda_sigma)
+    sc = scene_sphere_box()
+    pool = make_ray_pool(sc, cameras_on_sphere(4, 2.0, 40, 32, 32, 0), 256, 0)
+    rays = sample_batch(pool, 6, 1)
+    rays["is_obj"][:2] = 0  # keep some background rays in the batch
+    grid = prior_grid(sc, 16, 0)
+    nr, nc = 8, 16
+    u = stratified_uniforms(6, nr, 2)
+    cr = random_colours(6, 3)
+    theta = init_params(orc.n_hash_params(a), a.mlp_shapes(), 4, hash_range=0.5).astype(np.float64)
+    return a, theta, grid, rays, nc, nr, u, cr
+
+
+def _fd4(f, theta, i):
+    """Fourth-order central difference; its roundoff is ~eps |L| / h = 1e-12 here."""
+    h = 1e-4 * max(1.0, abs(theta[i]))
+    vals = []
+    for s in (-2, -1, 1, 2):
+        tp = theta.copy()
+        tp[i] += s * h
+        vals.append(f(tp))
+    return (vals[0] - 8 * vals[1] + 8 * vals[2] - vals[3]) / (12 * h)
+
+
+def _check_fd(f, theta, g, idx):
+    scale = np.abs(g[idx]).max()
+    assert scale > 0
+    bad = []
+    for i in idx:
+        fd = _fd4(f, theta, i)
+        if abs(fd - g[i]) > 1e-6 * abs(g[i]) + 1e-9 * scale:
+            bad.append((int(i), fd, g[i]))
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("lambda_sigma", [0.0, 1e-2])
+def test_gradient_matches_central_differences(orc, lambda_sigma):
+    a, theta, grid, rays, nc, nr, u, cr = _fd_setup(orc, lambda_sigma)
+    out = orc.batch(a, theta, grid, rays, nc, nr, u=u, c_rand=cr, want_grad=True)
+    g = out["grad"]
+    rng = np.random.default_rng(9)
+    nh = orc.n_hash_params(a)
+    touched = np.nonzero(g[:nh])[0]
+    idx = np.concatenate([rng.choice(touched, 40, replace=False), nh + rng.choice(g.size - nh, 40, replace=False)])
+    _check_fd(lambda tt: orc.batch(a, tt, grid, rays, nc, nr, u=u, c_rand=cr, want_samples=False)["loss"],
+              theta, g, idx)
+
+
+def test_upstream_gradient_matches_central_differences(orc):
+    a, theta, grid, rays, nc, nr, u, cr = _fd_setup(orc)
+    up = np.random.default_rng(10).normal(size=(6, 5))
+    out = orc.batch(a, theta, grid, rays, nc, nr, u=u, upstream=up, want_grad=True)
+    # the upstream functional equals sum_r up_r . (C_r, D_r, A_r)
+    lin = np.sum(up[:, :3] * out["rgb"]) + up[:, 3] @ out["depth"] + up[:, 4] @ out["acc"]
+    assert abs(lin - out["loss"]) < 1e-12
+    g = out["grad"]
+    nh = orc.n_hash_params(a)
+    idx = np.concatenate([np.nonzero(g[:nh])[0][:30], np.arange(nh, nh + 30)])
+    _check_fd(lambda tt: orc.batch(a, tt, grid, rays, nc, nr, u=u, upstream=up, want_samples=False)["loss"],
+              theta, g, idx)
+
+
+def test_sampler_does_not_depend_on_theta(orc):
+    a, theta, grid, rays, nc, nr, u, cr = _fd_setup(orc)
+    o1 = orc.batch(a, theta, grid, rays, nc, nr, u=u, c_rand=cr)
+    o2 = orc.batch(a, theta * 3.0, grid, rays, nc, nr, u=u, c_rand=cr)
+    np.testing.assert_array_equal(o1["t"], o2["t"])
+    np.testing.assert_array_equal(o1["bins"], o2["bins"])
+
+
+# ------------------------------------------------------------------------ Adam
+def test_adam_constant_gradient_steps(orc):
+    n = 7
+    g = np.array([3.0, -2.0, 1e-3, -1e-6, 5.0, -7.0, 0.0])
+    theta = np.zeros(n)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    lr = 1e-2
+    for step in (1, 2, 3):
+        before = theta.copy()
+        orc.adam(theta, m, v, g, step, lr, 0.9, 0.99, 1e-15)
+        # bias-corrected moments of a constant gradient are g and g^2, so each step is
+        # -lr g / (|g| + eps): lr sign(g) up to the eps term (visible at |g| = 1e-6)
+        np.testing.assert_allclose(theta - before, -lr * g / (np.abs(g) + 1e-15), rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------------- Philox
+def test_philox_known_answers(orc):
+    # Known-answer vectors of Philox4x32-10 published with the Random123 library
+    assert orc.philox4x32_10([0, 0, 0, 0], [0, 0]).tolist() == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+    assert orc.philox4x32_10([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2).tolist() == [
+        0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]
+    assert orc.philox4x32_10([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0]).tolist() == [
+        0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]
+
+
+def test_philox_uniforms_are_stratified(orc):
+    nr = 48
+    u = orc.philox_uniforms(1234, 3, 1, 200, nr)
+    k = np.arange(nr)
+    assert np.all(u >= k / nr) and np.all(u < (k + 1) / nr)
+    c = orc.philox_colours(1234, 3, 1, 5000)
+    assert c.min() >= 0 and c.max() < 1 and abs(c.mean() - 0.5) < 0.01
