@@ -1,0 +1,387 @@
+"""Throughput of the PRENOM object-NeRF training step (fwd + bwd + Adam) on GB300.
+
+Default workload: one object at full size -- hash grid L=16, F=2, T=2^19,
+resolutions 16..2048, MLP 32-64-64-4, 4096 rays x 64 samples per step (Nc=64)
+drawn by the prior sampler over a 64^3 prior grid of a random CSG shape.
+One step = sampling, encoding, MLP, compositing, loss, backward and Adam for
+every parameter.  Under torchrun each rank trains its own object (weak scaling,
+no collective: objects are independent).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead (bounded ray sample per step, extrapolated).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NeRF training samples/s (fwd+bwd+Adam), batched FP16 vs plain FP32, at equal error"
+ARCH = dict(L=16, F=2, log2T=19, n_min=16, n_max=2048, width=64, hidden=2, lambda_d=0.1, lambda_sigma=0.0)
+N_RAYS, NR, NC, GRID_RES = 4096, 64, 64, 64
+WORKLOAD = ("single object at full size: hash grid L=16 F=2 T=2^19 res 16..2048, MLP 32-64-64-4 (ReLU, exp "
+            "density, sigmoid colour), 4096 rays x 64 samples/step from the prior sampler (Nc=64) over a 64^3 "
+            "prior grid, random CSG scene, 480x640 views, depth noise 2 mm, FP32 per-object form")
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+
+
+def mlp_macs(a):
+    return a["width"] * a["L"] * a["F"] + (a["hidden"] - 1) * a["width"] ** 2 + 4 * a["width"]
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return dict(hbm_gbs=float(p["hbm_gbs"]), bf16=float(p["bf16_tflops"]), src="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, bf16=1900.0, src="fallback")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload(seed: int, n_batches: int, n_params_hash: int):
+    from synth import (cameras_on_sphere, init_params, make_ray_pool, prior_grid, random_colours, sample_batch,
+                       scene_random_csg, stratified_uniforms)
+
+    sc = scene_random_csg(seed)
+    pool = make_ray_pool(sc, cameras_on_sphere(24, 2.0, 50, 480, 640, seed), 65536, seed, depth_noise=0.004)
+    grid = prior_grid(sc, GRID_RES, seed)
+    shapes = [(ARCH["width"], ARCH["L"] * ARCH["F"])] + [(ARCH["width"], ARCH["width"])] * (ARCH["hidden"] - 1) + \
+        [(4, ARCH["width"])]
+    theta = init_params(n_params_hash, shapes, seed + 1)
+    batches = []
+    for i in range(n_batches):
+        b = sample_batch(pool, N_RAYS, 1000 * seed + i)
+        b["uniforms"] = stratified_uniforms(N_RAYS, NR, 2000 * seed + i)
+        b["c_rand"] = random_colours(N_RAYS, 3000 * seed + i)
+        batches.append(b)
+    return grid, theta, batches
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_identifier(dev: int) -> str:
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except Exception:
+        return None
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for fn in rec.get("sources", []):
+        with open(os.path.join(ROOT, fn), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("sources_sha256"):
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+# ------------------------------------------------------------------- oracle arm
+def oracle_throughput(seed: int, budget_s: float):
+    """FP64 oracle (as it stands, one host thread) on a bounded sample of the
+    workload: rays of one step until budget_s of fwd+bwd, plus one full Adam
+    pass over every parameter; the step time is extrapolated to 4096 rays."""
+    import oracle as orc
+
+    a = orc.Arch(**ARCH)
+    grid, theta, batches = _workload(seed, 1, orc.n_hash_params(a))
+    b = batches[0]
+    theta = theta.astype(np.float64)
+    done = 0
+    t_rays = 0.0
+    chunk = 16
+    while t_rays < budget_s and done < N_RAYS:
+        sl = slice(done, done + chunk)
+        sub = {k: b[k][sl] for k in ("o", "d", "rgb", "depth", "is_obj")}
+        t0 = time.perf_counter()
+        orc.batch(a, theta, grid, sub, NC, NR, u=b["uniforms"][sl], c_rand=b["c_rand"][sl], want_grad=True,
+                  want_samples=False)
+        t_rays += time.perf_counter() - t0
+        done += chunk
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    g = np.zeros_like(theta)
+    t0 = time.perf_counter()
+    orc.adam(theta, m, v, g, 1, 1e-2)
+    t_adam = time.perf_counter() - t0
+    step_s = t_rays * (N_RAYS / done) + t_adam
+    return dict(value=N_RAYS * NR / step_s, rays=done, t_rays=t_rays, t_adam=t_adam, step_s=step_s)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    budget = float(os.environ.get("PRENOM_ORACLE_BUDGET_S", "4"))
+    if args.warmup > 0:
+        oracle_throughput(0, 0.5)
+    vals, times = [], []
+    for _ in range(args.steps):
+        r = oracle_throughput(0, budget)
+        vals.append(r["value"])
+        times.append(r["step_s"])
+    value = statistics.median(vals)
+    sample = (f"per step: {r['rays']} of {N_RAYS} rays fwd+bwd ({r['t_rays']:.1f} s) + one full Adam pass "
+              f"({r['t_adam']:.2f} s), extrapolated to the 4096-ray step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2503_01582_gb300 as pkg
+    from paper_2503_01582_gb300 import build
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    pkg._abi.lib()
+
+    stream = torch.cuda.Stream()
+    ctx = pkg.Context(seed=rank, stream=stream)
+    arch = pkg.make_arch(**{k: v for k, v in ARCH.items()})
+    probe = ctx.create_object(arch)
+    n_params = ctx.param_count(probe)
+    ctx.destroy_object(probe)
+    n_hash = n_params - mlp_macs(ARCH)
+    grid, theta, batches_np = _workload(rank, 8, n_hash)
+    obj = ctx.create_object(arch, theta)
+    ctx.set_prior_grid(obj, grid)
+    dev_batches = []
+    with torch.cuda.stream(stream):
+        for b in batches_np:
+            d = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in b.items()}
+            d["obj"] = obj
+            dev_batches.append(d)
+    opts = pkg.make_opts(nc=NC, nr=NR, lr=1e-2)
+    loss = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for i in range(args.warmup):
+        ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.enable_timing(True)
+    launches0 = ctx.launch_count()
+    clocks = ClockSampler(gpu_identifier(local))
+    barrier()
+    torch.cuda.synchronize()
+    with clocks:
+        ev0.record(stream)
+        for i in range(args.steps):
+            ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    k_train_ms, k_train_n = ctx.kernel_time(pkg.PRENOM_KERNEL_TRAIN)
+    k_adam_ms, k_adam_n = ctx.kernel_time(pkg.PRENOM_KERNEL_ADAM)
+    ctx.enable_timing(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    samples_per_step = N_RAYS * NR
+    value = samples_per_step * args.steps * world / (ms / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    pinned = []
+    for b in batches_np:
+        pinned.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in b.items()})
+    h2d = sum(t.numel() * t.element_size() for t in pinned[0].values())
+    loss_host = torch.zeros(1).pin_memory()
+    staging = [{k: torch.empty_like(v, device="cuda") for k, v in p.items()} for p in pinned[:2]]
+    e2e_steps = max(args.steps, 5)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        src = pinned[i % len(pinned)]
+        dst = staging[i % 2]
+        with torch.cuda.stream(stream):
+            for k in src:
+                dst[k].copy_(src[k], non_blocking=True)
+        b = dict(dst)
+        b["obj"] = obj
+        ctx.train_step([b], opts, loss)
+        with torch.cuda.stream(stream):
+            loss_host.copy_(loss, non_blocking=True)
+        stream.synchronize()
+        _ = float(loss_host.item())
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e_value = samples_per_step * e2e_steps * world / e2e_s
+
+    # ---- roofline of the dominant kernel (the fused training kernel)
+    peaks = load_peaks()
+    train_avg_s = (k_train_ms / max(k_train_n, 1)) / 1e3
+    adam_avg_s = (k_adam_ms / max(k_adam_n, 1)) / 1e3
+    flops = samples_per_step * mlp_macs(ARCH) * 6  # MLP: 2 MAC fwd + 4 MAC bwd flops per sample
+    achieved = flops / train_avg_s / 1e12
+    traffic = profiled_traffic("fused_fp32_kernel")
+    adam_bytes = n_params * 28  # read g, m, v, theta; write m, v, theta
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
+                "kernel": "fused_fp32_kernel (sample+encode+MLP+render+loss+backward+scatter)",
+                "algorithmic": f"{mlp_macs(ARCH) * 6} MLP flop/sample x {samples_per_step} samples",
+                "peak_src": "FP32 FFMA: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                "other_kernels": {"adam": {"bound": "hbm", "achieved": round(adam_bytes / adam_avg_s / 1e9, 1),
+                                           "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                           "frac": round(adam_bytes / adam_avg_s / 1e9 / peaks["hbm_gbs"], 4),
+                                           "peak_src": peaks["src"], "avg_us": round(adam_avg_s * 1e6, 2)},
+                                  "train_avg_us": round(train_avg_s * 1e6, 2)}}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            r = oracle_throughput(0, float(os.environ.get("PRENOM_ORACLE_BUDGET_S", "12")))
+            cpu = {"value": r["value"], "unit": "samples/s", "cores": 1, "kind": "oracle",
+                   "sample": (f"{r['rays']} of {N_RAYS} rays fwd+bwd ({r['t_rays']:.1f} s) + one full Adam pass "
+                              f"({r['t_adam']:.2f} s), FP64, 1 host thread, extrapolated to the 4096-ray step")}
+        line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "rays_per_step": N_RAYS, "samples_per_ray": NR, "probes": NC,
+                           "params": n_params, "form": "fp32 per-object",
+                           "parallelism": f"{world} independent objects (one per GPU)" if world > 1 else "1 object",
+                           "l2": "working set > L2: theta, grad, Adam m and v (4 x %.0f MB) stream every step"
+                                 % (n_params * 4 / 1e6)},
+                "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": 4},
+                "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": clocks.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/* prenom.h — C ABI of the GB300 (sm_103a) object-NeRF training library.
+ *
+ * The library implements the hot path of the online object mapper of
+ * "Category-level Meta-learned NeRF Priors for Efficient Object Mapping"
+ * (PRENOM, arXiv 2503.01582): one training step of many small object-level
+ * NeRFs (§III-B), made of
+ *   (a) probabilistic ray sampling over a prior density grid
+ *       (§III-B "Probabilistic Ray Sampling", Eq. 4-6, escape rule),
+ *   (b) a multiresolution hash-grid encoding and a shallow MLP
+ *       (§III-B "Object-level NeRFs"),
+ *   (c) volume rendering and the RGB-D loss (§III-B "Volume Rendering",
+ *       Eq. 7-9),
+ *   (d) the backward pass and an Adam update (last sentence of §III-B).
+ *
+ * Conventions for every call:
+ *   - return 0 (PRENOM_OK) on success or a negative PRENOM_ERR_* code; the
+ *     message of the last failure is available from prenom_last_error();
+ *     no C++ exception crosses this interface;
+ *   - all work is stream-ordered on the stream given to prenom_create();
+ *     calls return before the GPU has finished unless stated otherwise;
+ *   - pointers marked "device" must be CUDA device (or managed) memory that
+ *     stays valid until the stream reaches the call's work; the library
+ *     never frees or keeps them;
+ *   - the library owns every object's parameters theta, gradients and Adam
+ *     moments, allocated once by prenom_create_object();
+ *   - one context belongs to one host thread at a time (no internal locks).
+ *
+ * Parameter vector layout of one object (what prenom_get_state copies):
+ * hash tables level by level, each level entry-major with F features per
+ * entry, then one row-major (out x in) matrix per MLP layer:
+ * W_1 [W][L*F], W_2 .. W_H [W][W], W_out [4][W]; no biases.
+ */
+#ifndef PRENOM_H
+#define PRENOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PRENOM_API __attribute__((visibility("default")))
+#else
+#define PRENOM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define PRENOM_OK 0
+#define PRENOM_ERR_INVALID_ARG (-1)    /* bad pointer, size, index or architecture */
+#define PRENOM_ERR_OOM (-2)            /* a device allocation failed */
+#define PRENOM_ERR_CUDA (-3)           /* a CUDA runtime call or a launch failed */
+#define PRENOM_ERR_DEVICE_TIMEOUT (-4) /* a bounded device-side wait gave up */
+#define PRENOM_ERR_NONFINITE (-5)      /* a checked loss was NaN or infinite */
+
+#define PRENOM_PRECISION_FP32 0 /* FP32 features, MLP and accumulation */
+
+/* prenom_train_opts.flags */
+#define PRENOM_FLAG_NO_ADAM 1u      /* accumulate gradients, skip Adam (step count unchanged) */
+#define PRENOM_FLAG_CHECK_FINITE 2u /* synchronise and fail with NONFINITE on a NaN/inf loss */
+
+/* prenom_get_state / prenom_set_state: which buffer */
+#define PRENOM_STATE_THETA 0
+#define PRENOM_STATE_GRAD 1
+#define PRENOM_STATE_ADAM_M 2
+#define PRENOM_STATE_ADAM_V 3
+
+/* Kernel ids for the timing interface. */
+#define PRENOM_KERNEL_TRAIN 0  /* fused sample+encode+MLP+render+loss+backward */
+#define PRENOM_KERNEL_ADAM 1   /* dense Adam over every parameter of the step's objects */
+#define PRENOM_KERNEL_RENDER 2 /* forward only */
+#define PRENOM_KERNEL_RENDER_BWD 3
+#define PRENOM_KERNEL_INIT 4   /* random parameter initialisation */
+#define PRENOM_N_KERNELS 5
+
+typedef struct prenom_ctx prenom_ctx; /* opaque; owns all device state */
+
+/* Architecture alpha of one object NeRF (§III-A "Architecture Optimization"
+ * lists hash-grid and MLP hyper-parameters and lambda_d, lambda_sigma).
+ * Limits of this build: F = 2; L in {4, 8, 16}; width in {16, 32, 64};
+ * 1 <= hidden <= 3; 8 <= log2T <= 24; 2 <= n_min <= n_max <= 2^20;
+ * precision = PRENOM_PRECISION_FP32. */
+typedef struct {
+    int32_t L, F, log2T, n_min, n_max; /* levels, features/level, log2 table size, resolutions */
+    int32_t width, hidden;             /* MLP hidden width W and hidden layer count H */
+    int32_t precision;                 /* PRENOM_PRECISION_* */
+    float lambda_d, lambda_sigma;      /* Eq. 9 loss weights */
+} prenom_arch;
+
+/* Step options.  lr, beta1, beta2, eps: Adam (§III-B).  nc, nr: probes and
+ * samples per ray (§III-B, N_c and N_r; 4 <= nr <= 128, 1 <= nc <= 256).
+ * escape_eps: the escape threshold epsilon of §III-B (the paper uses 1e-4).
+ * loss_scale_init: reserved (must be 0 or 1 in FP32).  flags: PRENOM_FLAG_*. */
+typedef struct {
+    float lr, beta1, beta2, eps;
+    int32_t nc, nr;
+    float escape_eps;
+    float loss_scale_init;
+    uint32_t flags;
+} prenom_train_opts;
+
+/* One object's rays for one step, in the object's normalized frame (the
+ * unit cube of §III-A; rays "transformed into the object frame", §III-B).
+ * All arrays are device memory, row-major, n_rays rows:
+ *   o, d      [n][3] float  origin and direction (d need not be unit; t is in units of |d|)
+ *   rgb       [n][3] float  target colour C(r) of object rays (read for R_o only)
+ *   depth     [n]    float  target depth D(r) of object rays (read for R_o only)
+ *   is_obj    [n]    uint8  1 = ray of R_o (hits the object), 0 = R_b (background)
+ *   c_rand    [n][3] float  background supervision colour C_rand, or NULL to draw it
+ *                           from the library's Philox stream (seed, step, obj, ray)
+ *   uniforms  [n][nr] float stratified uniforms in [0,1) for the inverse transform,
+ *                           sorted along each ray, or NULL to draw them from Philox
+ *   t_in      [n][nr] float optional sample depths, sorted, inside the ray's box
+ *                           interval; when non-NULL the prior sampler is skipped
+ *                           (uniforms are then ignored). */
+typedef struct {
+    int32_t obj;
+    int32_t n_rays;
+    const float *o, *d;
+    const float *rgb, *depth;
+    const uint8_t *is_obj;
+    const float *c_rand;
+    const float *uniforms;
+    const float *t_in;
+} prenom_ray_batch;
+
+/* Creates a context on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream) on which all work is ordered; seed keys
+ * the Philox stream used when a batch omits uniforms or c_rand and for random
+ * initialisation.  *out receives the context (NULL on failure). */
+PRENOM_API int prenom_create(prenom_ctx **out, void *cuda_stream, uint64_t seed);
+
+/* Destroys a context, its objects and device buffers (synchronises first). */
+PRENOM_API void prenom_destroy(prenom_ctx *ctx);
+
+/* The message of the last failing call on ctx ("" if none; ctx may be NULL,
+ * then the message of the last failed prenom_create is returned). */
+PRENOM_API const char *prenom_last_error(const prenom_ctx *ctx);
+
+/* Registers one object NeRF (§III-B "Object-level NeRFs": a known category
+ * loads its meta-learned theta, an unknown one uses random initialisation).
+ * init_params: host or device pointer to param_count floats in the layout
+ * above (copied), or NULL for random initialisation (hash entries uniform in
+ * [-1e-4, 1e-4], MLP matrices Xavier-uniform, from the context's Philox
+ * stream).  Gradients and Adam moments start at zero, the step count at 0.
+ * Allocates the object's device arena (4 x param_count floats). */
+PRENOM_API int prenom_create_object(prenom_ctx *ctx, const prenom_arch *arch, const float *init_params,
+                         int32_t *obj_out);
+
+/* Frees an object's device memory; its id is not reused. */
+PRENOM_API int prenom_destroy_object(prenom_ctx *ctx, int32_t obj);
+
+/* Number of floats in the object's parameter vector. */
+PRENOM_API int prenom_param_count(prenom_ctx *ctx, int32_t obj, size_t *n);
+
+/* Level geometry of the hash grid, for checking the layout contract:
+ * res[l] = N_l, offset[l] = float offset of level l in theta (l = 0..L;
+ * offset[L] = offset of W_1), dense[l] = 1 if level l is stored densely. */
+PRENOM_API int prenom_level_info(prenom_ctx *ctx, int32_t obj, int32_t *res, int64_t *offset, int32_t *dense);
+
+/* Sets the prior density grid F (§III-A "Normalized mesh generation", used by
+ * §III-B sampling): res^3 floats, x fastest, value of the voxel centred at
+ * ((i+1/2)/res, (j+1/2)/res, (k+1/2)/res); finite and >= 0; res >= 2.
+ * grid: host or device pointer, copied (the caller keeps ownership). */
+PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *grid, int32_t res);
+
+/* One training step (§III-B): for every batch, sample, encode, run the MLP,
+ * composite, form the loss of Eq. 9 averaged over that batch's rays, and
+ * back-propagate into the object's gradient buffer; then one Adam step for
+ * every distinct object named by the batches (unless PRENOM_FLAG_NO_ADAM).
+ * Gradients are zeroed by the Adam step, so NO_ADAM steps accumulate.
+ * loss_dev: device [n_batches] floats receiving each batch's loss, or NULL.
+ * Each object named must have a prior grid unless every batch naming it
+ * gives t_in. */
+PRENOM_API int prenom_train_step(prenom_ctx *ctx, const prenom_ray_batch *batches, int32_t n_batches,
+                      const prenom_train_opts *opts, float *loss_dev);
+
+/* Forward rendering of one batch (§III-B "Volume Rendering", Eq. 7): colour
+ * rgb [n][3], depth [n], accumulated opacity acc [n] (sum of the weights), all
+ * device, any may be NULL.  bins_out [n][nr] int32 (0-based prior bin of each
+ * sample, -1 when t_in was given) and t_out [n][nr] (sample depths) are
+ * optional. */
+PRENOM_API int prenom_render(prenom_ctx *ctx, const prenom_ray_batch *batch, const prenom_train_opts *opts,
+                  float *rgb, float *depth, float *acc, int32_t *bins_out, float *t_out);
+
+/* Adjoint of prenom_render for upstream gradients d_out [n][5] (dL/dC[3],
+ * dL/dD, dL/dA per ray, device): adds dL/dtheta into grad (device,
+ * param_count floats, caller-owned, accumulated, not zeroed). */
+PRENOM_API int prenom_render_backward(prenom_ctx *ctx, const prenom_ray_batch *batch,
+                           const prenom_train_opts *opts, const float *d_out, float *grad);
+
+/* Blocking copies of one object buffer (which = PRENOM_STATE_*) to / from
+ * host or device memory; n must equal param_count. */
+PRENOM_API int prenom_get_state(prenom_ctx *ctx, int32_t obj, int32_t which, float *dst, size_t n);
+PRENOM_API int prenom_set_state(prenom_ctx *ctx, int32_t obj, int32_t which, const float *src, size_t n);
+
+/* Adam step count of an object (bias correction uses step + 1 next). */
+PRENOM_API int prenom_get_step(prenom_ctx *ctx, int32_t obj, int32_t *step);
+PRENOM_API int prenom_set_step(prenom_ctx *ctx, int32_t obj, int32_t step);
+
+/* Zeroes an object's gradient buffer (stream-ordered). */
+PRENOM_API int prenom_zero_grads(prenom_ctx *ctx, int32_t obj);
+
+/* Waits for the context's stream; returns the first asynchronous error. */
+PRENOM_API int prenom_sync(prenom_ctx *ctx);
+
+/* Kernel timing: when enabled, every library launch is bracketed by CUDA
+ * events on the context's stream.  prenom_kernel_time() synchronises and
+ * returns, for kernel id k (PRENOM_KERNEL_*), the summed device time in ms
+ * and the launch count since timing was last enabled or reset. */
+PRENOM_API int prenom_enable_timing(prenom_ctx *ctx, int32_t enable);
+PRENOM_API int prenom_kernel_time(prenom_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
+
+/* Total kernel launches made by the library on this context. */
+PRENOM_API int prenom_launch_count(prenom_ctx *ctx, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRENOM_H */

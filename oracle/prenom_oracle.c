@@ -454,7 +454,7 @@ double orc_ray_loss(int is_obj, const double *C, double D, double A, const doubl
  * upstream != NULL ([n][5] = dC[3], dD, dA per ray) replaces the loss: the
  * returned value is then sum_r upstream_r . (C_r, D_r, A_r) and the gradient
  * is that of this linear functional (no 1/R, no L_sigma).
- * Colours c_rand may be NULL when no background ray is present. */
+ * Colours c_rand may be NULL: background rays then use C_rand = 0. */
 double orc_batch(const orc_arch *a, const double *theta, const double *grid, int R,
                  int n, const double *o, const double *d, const double *rgb,
                  const double *depth, const uint8_t *is_obj, const double *crand,
@@ -539,8 +539,9 @@ double orc_batch(const orc_arch *a, const double *theta, const double *grid, int
             total += gC[0] * C[0] + gC[1] * C[1] + gC[2] * C[2] + gD * D + gA * A;
         } else {
             background = !is_obj[r];
+            static const double no_colour[3] = {0.0, 0.0, 0.0}; /* when the caller gives none */
             double Lr = orc_ray_loss(is_obj[r], C, D, A, rgb + 3 * r, depth[r],
-                                     crand ? crand + 3 * r : NULL, a->lambda_d, gC, &gD, &gA);
+                                     crand ? crand + 3 * r : no_colour, a->lambda_d, gC, &gD, &gA);
             if (background) /* L_sigma: sum_j |sigma_j| over background rays (Eq. 8) */
                 for (int k = 0; k < Nr; ++k)
                     Lr += a->lambda_sigma * fabs(sigma[k]);

@@ -1,0 +1,201 @@
+"""GB300-native training step of PRENOM's object-level NeRFs (arXiv 2503.01582).
+
+The computation lives in libprenom.so (hand-written CUDA for sm_103a behind the
+C ABI of include/prenom.h).  This package only marshals torch tensors (device
+memory and streams) into that ABI:
+
+    ctx = Context(seed=0)
+    obj = ctx.create_object(make_arch(L=16, log2T=19, n_max=2048, width=64))
+    ctx.set_prior_grid(obj, grid)                  # [R, R, R] float32
+    ctx.train_step([dict(obj=obj, o=o, d=d, rgb=rgb, depth=depth, is_obj=m)],
+                   make_opts(nc=64, nr=64, lr=1e-2), loss=loss_buf)
+"""
+
+from __future__ import annotations
+
+from . import _abi
+from ._abi import (  # noqa: F401
+    KERNEL_NAMES,
+    PRENOM_FLAG_CHECK_FINITE,
+    PRENOM_FLAG_NO_ADAM,
+    PRENOM_KERNEL_ADAM,
+    PRENOM_KERNEL_RENDER,
+    PRENOM_KERNEL_RENDER_BWD,
+    PRENOM_KERNEL_TRAIN,
+    PRENOM_N_KERNELS,
+    PRENOM_PRECISION_FP32,
+    PRENOM_STATE_ADAM_M,
+    PRENOM_STATE_ADAM_V,
+    PRENOM_STATE_GRAD,
+    PRENOM_STATE_THETA,
+    PrenomError,
+    prenom_arch,
+    prenom_ray_batch,
+    prenom_train_opts,
+)
+
+__all__ = ["Context", "make_arch", "make_opts", "PrenomError"]
+
+
+def make_arch(L=8, F=2, log2T=14, n_min=16, n_max=256, width=32, hidden=2, precision=PRENOM_PRECISION_FP32,
+              lambda_d=0.1, lambda_sigma=0.0) -> prenom_arch:
+    return prenom_arch(L, F, log2T, n_min, n_max, width, hidden, precision, lambda_d, lambda_sigma)
+
+
+def make_opts(nc=32, nr=32, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, escape_eps=1e-4, flags=0,
+              loss_scale_init=0.0) -> prenom_train_opts:
+    return prenom_train_opts(lr, beta1, beta2, eps, nc, nr, escape_eps, loss_scale_init, flags)
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (0 for None)."""
+    if t is None:
+        return 0
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def ray_batch(b: dict) -> prenom_ray_batch:
+    """prenom_ray_batch from a dict of CUDA tensors (o, d, rgb, depth, is_obj,
+    c_rand, uniforms, t_in; all but o and d optional for rendering)."""
+    import torch
+
+    f32, u8 = torch.float32, torch.uint8
+    n = int(b["o"].shape[0]) if b.get("o") is not None else int(b.get("n_rays", 0))
+    return prenom_ray_batch(
+        int(b["obj"]), n,
+        _dptr(b.get("o"), f32, "o") or None, _dptr(b.get("d"), f32, "d") or None,
+        _dptr(b.get("rgb"), f32, "rgb") or None, _dptr(b.get("depth"), f32, "depth") or None,
+        _dptr(b.get("is_obj"), u8, "is_obj") or None, _dptr(b.get("c_rand"), f32, "c_rand") or None,
+        _dptr(b.get("uniforms"), f32, "uniforms") or None, _dptr(b.get("t_in"), f32, "t_in") or None,
+    )
+
+
+class Context:
+    """One library context on the current CUDA device and a torch stream."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        import torch
+
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = _abi.prenom_create(self.stream.cuda_stream, seed)
+        self._archs = {}
+
+    def close(self):
+        if self._ctx is not None:
+            _abi.prenom_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- objects ----
+    def create_object(self, arch: prenom_arch, init_params=None) -> int:
+        """init_params: None (random), a CUDA float32 tensor or a numpy float32 array."""
+        ptr = 0
+        keep = None
+        if init_params is not None:
+            import numpy as np
+
+            if isinstance(init_params, np.ndarray):
+                keep = np.ascontiguousarray(init_params, dtype=np.float32)
+                ptr = keep.ctypes.data
+            else:
+                ptr = _dptr(init_params, None, "init_params")
+        obj = _abi.prenom_create_object(self._ctx, arch, ptr)
+        self._archs[obj] = arch
+        del keep
+        return obj
+
+    def destroy_object(self, obj: int):
+        _abi.prenom_destroy_object(self._ctx, obj)
+
+    def param_count(self, obj: int) -> int:
+        return _abi.prenom_param_count(self._ctx, obj)
+
+    def level_info(self, obj: int):
+        return _abi.prenom_level_info(self._ctx, obj, self._archs[obj].L)
+
+    def set_prior_grid(self, obj: int, grid):
+        import numpy as np
+
+        if isinstance(grid, np.ndarray):
+            g = np.ascontiguousarray(grid, dtype=np.float32)
+            _abi.prenom_set_prior_grid(self._ctx, obj, g.ctypes.data, g.shape[0])
+            _abi.prenom_sync(self._ctx)
+        else:
+            _abi.prenom_set_prior_grid(self._ctx, obj, _dptr(grid, None, "grid"), int(grid.shape[0]))
+
+    # ---- steps ----
+    def train_step(self, batches, opts: prenom_train_opts, loss=None):
+        cb = [ray_batch(b) for b in batches]
+        _abi.prenom_train_step(self._ctx, cb, opts, _dptr(loss, None, "loss"))
+
+    def render(self, batch: dict, opts: prenom_train_opts, want_samples: bool = False):
+        import torch
+
+        n = int(batch["o"].shape[0])
+        dev = batch["o"].device
+        out = dict(rgb=torch.empty((n, 3), device=dev), depth=torch.empty(n, device=dev),
+                   acc=torch.empty(n, device=dev))
+        if want_samples:
+            out["bins"] = torch.empty((n, opts.nr), dtype=torch.int32, device=dev)
+            out["t"] = torch.empty((n, opts.nr), device=dev)
+        _abi.prenom_render(self._ctx, ray_batch(batch), opts, out["rgb"].data_ptr(), out["depth"].data_ptr(),
+                           out["acc"].data_ptr(), out["bins"].data_ptr() if want_samples else 0,
+                           out["t"].data_ptr() if want_samples else 0)
+        return out
+
+    def render_backward(self, batch: dict, opts: prenom_train_opts, d_out, grad):
+        _abi.prenom_render_backward(self._ctx, ray_batch(batch), opts, _dptr(d_out, None, "d_out"),
+                                    _dptr(grad, None, "grad"))
+
+    # ---- state ----
+    def get_state(self, obj: int, which: int = PRENOM_STATE_THETA):
+        import torch
+
+        t = torch.empty(self.param_count(obj), device="cuda")
+        _abi.prenom_get_state(self._ctx, obj, which, t.data_ptr(), t.numel())
+        return t
+
+    def set_state(self, obj: int, which: int, src):
+        import numpy as np
+
+        if isinstance(src, np.ndarray):
+            s = np.ascontiguousarray(src, dtype=np.float32)
+            _abi.prenom_set_state(self._ctx, obj, which, s.ctypes.data, s.size)
+        else:
+            _abi.prenom_set_state(self._ctx, obj, which, _dptr(src, None, "src"), src.numel())
+
+    def get_step(self, obj: int) -> int:
+        return _abi.prenom_get_step(self._ctx, obj)
+
+    def set_step(self, obj: int, step: int):
+        _abi.prenom_set_step(self._ctx, obj, step)
+
+    def zero_grads(self, obj: int):
+        _abi.prenom_zero_grads(self._ctx, obj)
+
+    def sync(self):
+        _abi.prenom_sync(self._ctx)
+
+    # ---- instrumentation ----
+    def enable_timing(self, on: bool = True):
+        _abi.prenom_enable_timing(self._ctx, on)
+
+    def kernel_time(self, kernel: int):
+        """(total ms, launches) since timing was enabled."""
+        return _abi.prenom_kernel_time(self._ctx, kernel)
+
+    def launch_count(self) -> int:
+        return _abi.prenom_launch_count(self._ctx)

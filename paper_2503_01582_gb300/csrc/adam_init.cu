@@ -1,0 +1,145 @@
+// Adam update over every parameter of a step's objects, random initialisation,
+// and the host-side dispatch of the fused kernels.
+#include "fused_fp32.cuh"
+
+namespace prenom {
+
+// ---------------------------------------------------------------- Adam
+// Dense Adam (Kingma & Ba) with bias correction, streamed once over theta,
+// grad, m and v of all segments (32 bytes moved per parameter: 16 read, 16
+// written, the gradient being zeroed for the next step's atomics).  Work is
+// cut into 4096-float chunks numbered across segments; a block finds its
+// segment by binary search over the chunk prefix sums held in parameter space.
+__device__ __forceinline__ void adam_one(float &th, float &m, float &v, float g, float b1, float b2, float eps,
+                                         float lr_c1, float inv_c2)
+{
+    m = fmaf(b1, m, (1.f - b1) * g);
+    v = fmaf(b2, v, (1.f - b2) * g * g);
+    th -= lr_c1 * m / (sqrtf(v * inv_c2) + eps);
+}
+
+__global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
+{
+    const int64_t total = a.chunk_start[a.n_segs];
+    for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+        int lo = 0, hi = a.n_segs - 1;
+        while (lo < hi) {  // last segment whose first chunk is <= c
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.chunk_start[mid] <= c)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const AdamSeg &sg = a.seg[lo];
+        const int64_t base = (c - a.chunk_start[lo]) * kAdamChunk;
+        const int64_t end = min(base + (int64_t)kAdamChunk, sg.n);
+        for (int64_t i = base + threadIdx.x * 4; i < end; i += blockDim.x * 4) {
+            if (i + 4 <= end) {
+                float4 th = *reinterpret_cast<float4 *>(sg.theta + i);
+                const float4 g = __ldcs(reinterpret_cast<const float4 *>(sg.grad + i));
+                float4 m = __ldcs(reinterpret_cast<const float4 *>(sg.m + i));
+                float4 v = __ldcs(reinterpret_cast<const float4 *>(sg.v + i));
+                adam_one(th.x, m.x, v.x, g.x, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
+                adam_one(th.y, m.y, v.y, g.y, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
+                adam_one(th.z, m.z, v.z, g.z, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
+                adam_one(th.w, m.w, v.w, g.w, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
+                *reinterpret_cast<float4 *>(sg.theta + i) = th;
+                __stcs(reinterpret_cast<float4 *>(sg.m + i), m);
+                __stcs(reinterpret_cast<float4 *>(sg.v + i), v);
+                *reinterpret_cast<float4 *>(sg.grad + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                for (int64_t j = i; j < end; ++j) {
+                    adam_one(sg.theta[j], sg.m[j], sg.v[j], sg.grad[j], a.beta1, a.beta2, a.eps, sg.lr_c1,
+                             sg.inv_c2);
+                    sg.grad[j] = 0.f;
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_adam(const AdamArgs &a, int grid, cudaStream_t st)
+{
+    adam_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- initialisation
+// theta[i] = (2 u_i - 1) * bound, u_i from word 0 of Philox(ctr = (i lo, i hi,
+// 'INIT', obj), key = seed); bound = 1e-4 for hash entries, sqrt(6 / (in + out))
+// for MLP matrices (Xavier-uniform).
+struct InitArgs {
+    float *theta;
+    int64_t n_hash;
+    int32_t n_layers;
+    int64_t layer_end[8];
+    float bound[8];
+    uint64_t seed;
+    uint32_t obj;
+};
+
+__global__ void init_kernel(const InitArgs a)
+{
+    const int64_t n = a.layer_end[a.n_layers - 1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float bound = 1e-4f;
+        if (i >= a.n_hash) {
+            int l = 0;
+            while (l < a.n_layers - 1 && i >= a.layer_end[l])
+                ++l;
+            bound = a.bound[l];
+        }
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)(i >> 32), 0x494E4954u, a.obj),
+                                      make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32)));
+        a.theta[i] = (2.f * u24(r.x) - 1.f) * bound;
+    }
+}
+
+cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_shape, int n_layers, uint64_t seed,
+                               uint32_t obj, int grid, cudaStream_t st)
+{
+    if (n_layers < 1 || n_layers > 8)
+        return cudaErrorInvalidValue;
+    InitArgs a{};
+    a.theta = theta;
+    a.n_hash = n_hash;
+    a.n_layers = n_layers;
+    int64_t off = n_hash;
+    for (int l = 0; l < n_layers; ++l) {
+        const int out = mlp_shape[2 * l], in = mlp_shape[2 * l + 1];
+        off += (int64_t)out * in;
+        a.layer_end[l] = off;
+        a.bound[l] = sqrtf(6.f / (float)(in + out));
+    }
+    a.seed = seed;
+    a.obj = obj;
+    init_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- fused dispatch
+size_t fused_fp32_smem(int W, int IN, int H, int S)
+{
+    return fused_fp32_smem_floats(W, IN, H, S) * sizeof(float);
+}
+
+int fused_fp32_pick_tile(int W, int IN, int H, size_t smem_limit)
+{
+    if (fused_fp32_smem(W, IN, H, 128) <= smem_limit)
+        return 128;
+    if (W == 64 && fused_fp32_smem(W, IN, H, 64) <= smem_limit)
+        return 64;
+    return 0;
+}
+
+cudaError_t launch_fused_fp32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st)
+{
+    switch (od.W) {
+    case 16: return launch_fused_fp32_w16(od, bd, S, grid, st);
+    case 32: return launch_fused_fp32_w32(od, bd, S, grid, st);
+    case 64: return launch_fused_fp32_w64(od, bd, S, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace prenom

@@ -1,0 +1,201 @@
+// Device helpers of the fused PRENOM kernels: counter-based random numbers,
+// error-free position arithmetic, hash-grid indexing, prior-grid lookup and warp scans.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prenom_internal.h"
+
+namespace prenom {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC 2011).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-8f; }
+
+__device__ __forceinline__ uint32_t pick(uint4 v, int i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Stratified uniform u_{r,k} = (k + xi) / nr in IEEE single precision, xi from
+// word k mod 4 of Philox(ctr = (ray, k div 4, step, 2 obj), key = seed).
+__device__ __forceinline__ float philox_uniform(uint64_t seed, uint32_t step, uint32_t obj, uint32_t ray,
+                                                int k, int nr)
+{
+    const uint4 o = philox4x32_10(make_uint4(ray, (uint32_t)k >> 2, step, 2u * obj),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    return __fdiv_rn(__fadd_rn((float)k, u24(pick(o, k & 3))), (float)nr);
+}
+
+// Background colour C_rand of a ray: words 0..2 of Philox(ctr = (ray, 0, step, 2 obj + 1)).
+__device__ __forceinline__ float3 philox_colour(uint64_t seed, uint32_t step, uint32_t obj, uint32_t ray)
+{
+    const uint4 o = philox4x32_10(make_uint4(ray, 0u, step, 2u * obj + 1u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    return make_float3(u24(o.x), u24(o.y), u24(o.z));
+}
+
+// p = o + t d as an unevaluated sum hi + lo (error-free product and sum), so
+// that the cell coordinates p N_l keep ~48 bits even at N_l = 2048.
+__device__ __forceinline__ void pos_two_float(float o, float t, float d, float &hi, float &lo)
+{
+    const float p = __fmul_rn(t, d);
+    const float pe = __fmaf_rn(t, d, -p);  // exact error of the product
+    const float s = __fadd_rn(o, p);
+    const float bb = __fsub_rn(s, o);
+    const float se = __fadd_rn(__fsub_rn(o, __fsub_rn(s, bb)), __fsub_rn(p, bb));  // exact error of the sum
+    const float l = __fadd_rn(se, pe);
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+    // clamp to the unit cube (a NaN position maps to the origin)
+    if (!(hi >= 0.f) || (hi == 0.f && lo < 0.f)) {
+        hi = 0.f;
+        lo = 0.f;
+    } else if (hi > 1.f || (hi == 1.f && lo > 0.f)) {
+        hi = 1.f;
+        lo = 0.f;
+    }
+}
+
+// Cell c0 = min(floor(p N), N - 1) and local coordinate w = p N - c0 in [0, 1]
+// from p = hi + lo.
+__device__ __forceinline__ void level_cell(float hi, float lo, int N, int &c0, float &w)
+{
+    const float nf = (float)N;
+    const float s = __fmul_rn(hi, nf);
+    const float se = __fmaf_rn(hi, nf, -s);  // exact error of hi * N
+    const float sl = __fmaf_rn(lo, nf, se);
+    float f = floorf(s);
+    float fr = __fadd_rn(__fsub_rn(s, f), sl);  // s - f is exact
+    if (fr < 0.f) {
+        f -= 1.f;
+        fr = __fadd_rn(fr, 1.f);
+    } else if (fr >= 1.f) {
+        f += 1.f;
+        fr = __fsub_rn(fr, 1.f);
+    }
+    if (f < 0.f) {
+        f = 0.f;
+        fr = 0.f;
+    }
+    if (f > nf - 1.f) {
+        fr = __fadd_rn(fr, f - (nf - 1.f));
+        f = nf - 1.f;
+    }
+    c0 = (int)f;
+    w = fr;
+}
+
+constexpr uint32_t kPi2 = 2654435761u;
+constexpr uint32_t kPi3 = 805459861u;
+
+// Entry of vertex (x, y, z) on a level: dense (x fastest) or spatial hash mod T.
+__device__ __forceinline__ uint32_t grid_index(bool dense, uint32_t n1, uint32_t tmask, uint32_t x, uint32_t y,
+                                               uint32_t z)
+{
+    return dense ? x + n1 * (y + n1 * z) : ((x ^ (y * kPi2) ^ (z * kPi3)) & tmask);
+}
+
+// The 8 corner entries and trilinear weights of point (hi+lo) on level lv.
+struct Corners {
+    uint32_t idx[8];
+    float wt[8];
+};
+
+__device__ __forceinline__ void level_corners(const LevelDesc &lv, uint32_t tmask, const float (&ph)[3],
+                                              const float (&pl)[3], Corners &cs)
+{
+    int c[3];
+    float w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        level_cell(ph[a], pl[a], lv.res, c[a], w[a]);
+    const bool dense = lv.dense != 0;
+    const uint32_t n1 = (uint32_t)lv.res + 1u;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        const int bx = corner & 1, by = (corner >> 1) & 1, bz = (corner >> 2) & 1;
+        const float wx = bx ? w[0] : 1.f - w[0];
+        const float wy = by ? w[1] : 1.f - w[1];
+        const float wz = bz ? w[2] : 1.f - w[2];
+        cs.wt[corner] = __fmul_rn(__fmul_rn(wx, wy), wz);
+        cs.idx[corner] = grid_index(dense, n1, tmask, (uint32_t)(c[0] + bx), (uint32_t)(c[1] + by),
+                                    (uint32_t)(c[2] + bz));
+    }
+}
+
+// Prior density at x: trilinear over voxel centres, g = x R - 1/2 clamped to [0, R-1].
+__device__ __forceinline__ float prior_lookup(const float *__restrict__ grid, int R, float x, float y, float z)
+{
+    const float rf = (float)R;
+    const float q[3] = {x, y, z};
+    int c[3];
+    float w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float g = __fmaf_rn(q[a], rf, -0.5f);
+        g = fminf(fmaxf(g, 0.f), rf - 1.f);
+        float f = fminf(floorf(g), rf - 2.f);
+        c[a] = (int)f;
+        w[a] = g - f;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+        const int bx = corner & 1, by = (corner >> 1) & 1, bz = (corner >> 2) & 1;
+        const float wt = (bx ? w[0] : 1.f - w[0]) * (by ? w[1] : 1.f - w[1]) * (bz ? w[2] : 1.f - w[2]);
+        const float v = __ldg(grid + ((size_t)(c[2] + bz) * R + (c[1] + by)) * R + (c[0] + bx));
+        s += (wt == 0.f) ? 0.f : wt * v;
+    }
+    return s;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_incl_scan(float v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float n = __shfl_up_sync(kFull, v, o);
+        if (lane >= o)
+            v += n;
+    }
+    return v;
+}
+
+// Inclusive suffix scan: lane i gets the sum of lanes i..31.
+__device__ __forceinline__ float warp_incl_suffix(float v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float n = __shfl_down_sync(kFull, v, o);
+        if (lane + o < 32)
+            v += n;
+    }
+    return v;
+}
+
+}  // namespace prenom

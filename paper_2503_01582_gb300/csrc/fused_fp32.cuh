@@ -1,0 +1,703 @@
+// Fused FP32 training step of one object NeRF on sm_103a.
+//
+// One persistent CTA (256 threads) per SM walks tiles of whole rays.  A tile
+// holds S samples (S = 128 or 64) as rows of shared-memory activation
+// matrices stored feature-major ([feature][sample], row stride S + 4 floats),
+// so every stage of the step reads its operands from shared memory and no
+// per-sample intermediate ever goes to HBM:
+//   1. ray setup and prior sampling, one warp per ray (§III-B "Probabilistic
+//      Ray Sampling": probes, Eq. 4-6 via a warp scan of sigma*delta, escape
+//      rule, inverse transform by binary search over the CDF in shared memory);
+//   2. hash-grid encoding, two (or four) threads per sample, levels split
+//      between them, with error-free position arithmetic;
+//   3. MLP forward as register-tiled FFMA GEMMs over the tile;
+//   4. compositing (Eq. 7), loss (Eq. 8-9) and its adjoint, one warp per ray
+//      with shuffle scans (prefix for transmittance, suffix for the adjoint);
+//   5. MLP backward: dW accumulated in shared memory across all tiles of the
+//      CTA (flushed once with atomics at the end), dX by GEMM;
+//   6. hash-grid scatter of dX with vector float2 atomics.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace prenom {
+
+// Per-ray fields kept in shared memory during a tile.
+enum RayField { RF_O = 0, RF_D = 3, RF_RGB = 6, RF_DEPTH = 9, RF_OBJ = 10, RF_CR = 11, RF_TN = 14, RF_TF = 15 };
+constexpr int kRayStride = 16;
+
+enum Epi { kStore = 0, kRelu = 1, kMaskByOld = 2 };
+
+template <int R>
+__device__ __forceinline__ void ld_vec(const float *p, float (&v)[R])
+{
+    if constexpr (R == 8) {
+        const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if constexpr (R == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if constexpr (R == 2) {
+        const float2 a = *reinterpret_cast<const float2 *>(p);
+        v[0] = a.x; v[1] = a.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            v[i] = p[i];
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void st_vec(float *p, const float (&v)[R])
+{
+    if constexpr (R == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (R == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+            p[i] = v[i];
+    }
+}
+
+// C_T[n][s] = epi( sum_k A_T[k][s] * B[k][n] ) for the tile's S samples and N
+// outputs.  A_T, C_T: [.][S+4]; B: [K][N].  Each thread owns S/32 samples x N/8
+// outputs; a warp covers 8 sample groups x 4 output groups, so operand loads
+// are single-wavefront broadcasts and stores fill whole 128-byte rows.
+template <int S, int N, int EPI>
+__device__ __forceinline__ void gemm_sn(const float *__restrict__ AT, const float *__restrict__ B, int K,
+                                        float *CT)
+{
+    constexpr int SP = S + 4;
+    constexpr int RM = S / 32;
+    constexpr int RN = N / 8;
+    static_assert(RN >= 1 && RM >= 1, "tile shape");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cg = (warp & 1) * 4 + (lane & 3);
+    const int rg = (warp >> 1) * 8 + (lane >> 2);
+    const int s0 = rg * RM, n0 = cg * RN;
+    float acc[RM][RN];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RN; ++j)
+            acc[i][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        float a[RM], b[RN];
+        ld_vec<RM>(AT + k * SP + s0, a);
+        ld_vec<RN>(B + k * N + n0, b);
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RN; ++j)
+                acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+        float *c = CT + (n0 + j) * SP + s0;
+        float v[RM];
+        if constexpr (EPI == kMaskByOld) {
+            float old[RM];
+            ld_vec<RM>(c, old);
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+                v[i] = old[i] > 0.f ? acc[i][j] : 0.f;
+        } else {
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+                v[i] = (EPI == kRelu) ? fmaxf(acc[i][j], 0.f) : acc[i][j];
+        }
+        st_vec<RM>(c, v);
+    }
+}
+
+template <int N, int K>
+struct DwShape {
+    static constexpr int total = N * K;
+    static constexpr int per = total >= kThreads ? total / kThreads : 1;
+    static constexpr int rn0 = per >= 16 ? 4 : (per >= 4 ? 2 : (per >= 2 && N >= K ? 2 : 1));
+    static constexpr int RN = rn0 > N ? N : rn0;
+    static constexpr int RK = per / RN > K ? K : (per / RN < 1 ? 1 : per / RN);
+    static constexpr int TN = N / RN, TK = K / RK;
+    static_assert(TN * TK <= kThreads, "dW tile");
+    static_assert(RN * RK * TN * TK == total, "dW cover");
+};
+
+// D[n][k] += sum_s A_T[n][s] * B_T[k][s] (weight gradient of one layer over the
+// tile's samples).  D is row-major [N][K] in shared memory and every entry has
+// exactly one owning thread, so the update needs no atomics.  Rows owned by a
+// thread are interleaved (n = ni + i*TN) so a phase of 8 lanes reads 8
+// consecutive rows: with the +4 row padding these hit disjoint banks.
+template <int S, int N, int K>
+__device__ __forceinline__ void gemm_dw(const float *__restrict__ AT, const float *__restrict__ BT, float *D)
+{
+    using Sh = DwShape<N, K>;
+    constexpr int SP = S + 4;
+    const int tid = threadIdx.x;
+    if (tid >= Sh::TN * Sh::TK)
+        return;
+    const int ki = tid % Sh::TK, ni = tid / Sh::TK;
+    float acc[Sh::RN][Sh::RK];
+#pragma unroll
+    for (int i = 0; i < Sh::RN; ++i)
+#pragma unroll
+        for (int j = 0; j < Sh::RK; ++j)
+            acc[i][j] = 0.f;
+#pragma unroll 2
+    for (int s = 0; s < S; s += 4) {
+        float4 a[Sh::RN], b[Sh::RK];
+#pragma unroll
+        for (int i = 0; i < Sh::RN; ++i)
+            a[i] = *reinterpret_cast<const float4 *>(AT + (ni + i * Sh::TN) * SP + s);
+#pragma unroll
+        for (int j = 0; j < Sh::RK; ++j)
+            b[j] = *reinterpret_cast<const float4 *>(BT + (ki + j * Sh::TK) * SP + s);
+#pragma unroll
+        for (int i = 0; i < Sh::RN; ++i)
+#pragma unroll
+            for (int j = 0; j < Sh::RK; ++j) {
+                float t = acc[i][j];
+                t = fmaf(a[i].x, b[j].x, t);
+                t = fmaf(a[i].y, b[j].y, t);
+                t = fmaf(a[i].z, b[j].z, t);
+                t = fmaf(a[i].w, b[j].w, t);
+                acc[i][j] = t;
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < Sh::RN; ++i)
+#pragma unroll
+        for (int j = 0; j < Sh::RK; ++j)
+            D[(ni + i * Sh::TN) * K + ki + j * Sh::TK] += acc[i][j];
+}
+
+// Output layer forward: O_T[o][s] = sum_i H_T[i][s] * Wf_out[i][o], o < 4.
+template <int W, int S>
+__device__ __forceinline__ void out_layer_fwd(const float *__restrict__ HTl, const float *__restrict__ Wfo, float *OT)
+{
+    constexpr int SP = S + 4;
+    constexpr int PARTS = kThreads / S;
+    constexpr int OPT = 4 / PARTS;
+    const int s = threadIdx.x % S, og = threadIdx.x / S;
+    float acc[OPT];
+#pragma unroll
+    for (int j = 0; j < OPT; ++j)
+        acc[j] = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < W; ++i) {
+        const float h = HTl[i * SP + s];
+#pragma unroll
+        for (int j = 0; j < OPT; ++j)
+            acc[j] = fmaf(h, Wfo[i * 4 + og * OPT + j], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < OPT; ++j)
+        OT[(og * OPT + j) * SP + s] = acc[j];
+}
+
+// ---------------------------------------------------------------- sampling
+// One warp samples one ray: slab intersection with the unit cube, nc probes at
+// bin centres, sigma = prior density (trilinear), s_i = sum_{j<=i} sigma_j delta
+// by a warp scan, sum_{j<=i} rho_term_j = 1 - exp(-s_i) (the telescoped form of
+// Eq. 5), CDF of Eq. 6, uniform CDF i/nc for escaping rays, then for each
+// uniform the first bin b with CDF(b+1) > u and a linear position inside it.
+__device__ __forceinline__ void sample_ray_warp(const ObjDesc &od, const BatchDesc &bd, int r, int gr, float *rf,
+                                                float *ts, float *cdf, int lane)
+{
+    const int nc = bd.nc, nr = bd.nr;
+    const float o[3] = {rf[RF_O], rf[RF_O + 1], rf[RF_O + 2]};
+    const float d[3] = {rf[RF_D], rf[RF_D + 1], rf[RF_D + 2]};
+    float t0 = 0.f, t1 = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] != 0.f) {
+            const float ta = __fdiv_rn(0.f - o[a], d[a]);
+            const float tb = __fdiv_rn(1.f - o[a], d[a]);
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (o[a] < 0.f || o[a] > 1.f) {
+            t1 = -INFINITY;
+        }
+    }
+    const bool hit = t1 > t0;
+    const float tn = hit ? t0 : 0.f, tf = hit ? t1 : 0.f;
+    if (lane == 0) {
+        rf[RF_TN] = tn;
+        rf[RF_TF] = tf;
+    }
+    const int Q = (nr + 31) >> 5;
+    if (bd.t_in) {
+        for (int q = 0; q < Q; ++q) {
+            const int k = lane * Q + q;
+            if (k < nr) {
+                const float t = bd.t_in[(size_t)gr * nr + k];
+                ts[r * nr + k] = t;
+                if (bd.out_t)
+                    bd.out_t[(size_t)gr * nr + k] = t;
+                if (bd.out_bins)
+                    bd.out_bins[(size_t)gr * nr + k] = -1;
+            }
+        }
+        return;
+    }
+    const float delta = __fdiv_rn(tf - tn, (float)nc);
+    const int Qc = (nc + 31) >> 5;
+    float inc[kMaxNc / 32];
+    float run = 0.f;
+#pragma unroll
+    for (int q = 0; q < kMaxNc / 32; ++q) {
+        if (q < Qc) {
+            const int i = lane * Qc + q;
+            float tau = 0.f;
+            if (hit && i < nc) {
+                const float ti = __fmaf_rn((float)i + 0.5f, delta, tn);
+                const float sig = prior_lookup(od.grid, od.R, __fmaf_rn(ti, d[0], o[0]), __fmaf_rn(ti, d[1], o[1]),
+                                               __fmaf_rn(ti, d[2], o[2]));
+                tau = sig * delta;
+            }
+            run += tau;
+            inc[q] = run;
+        }
+    }
+    const float incl = warp_incl_scan(run, lane);
+    float base = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0)
+        base = 0.f;
+    const float s_total = __shfl_sync(kFull, incl, 31);
+    const float total = -expm1f(-s_total);
+    const bool escape = !(total >= bd.escape_eps);
+#pragma unroll
+    for (int q = 0; q < kMaxNc / 32; ++q) {
+        if (q < Qc) {
+            const int i = lane * Qc + q;
+            if (i < nc - 1) {
+                const float ci = -expm1f(-(base + inc[q]));
+                cdf[i + 1] = escape ? __fdiv_rn((float)(i + 1), (float)nc) : __fdiv_rn(ci, total);
+            }
+        }
+    }
+    if (lane == 0) {
+        cdf[0] = 0.f;
+        cdf[nc] = 1.f;
+    }
+    __syncwarp();
+    for (int q = 0; q < Q; ++q) {
+        const int k = lane * Q + q;
+        if (k < nr) {
+            const float u = bd.u ? bd.u[(size_t)gr * nr + k] : philox_uniform(bd.seed, bd.step, bd.obj_id, gr, k, nr);
+            int lo = 0, hi = nc - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (cdf[mid + 1] > u)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            const float c0 = cdf[lo], c1 = cdf[lo + 1];
+            const float frac = __fdiv_rn(u - c0, c1 - c0);
+            const float t = __fmaf_rn((float)lo + frac, delta, tn);
+            ts[r * nr + k] = t;
+            if (bd.out_t)
+                bd.out_t[(size_t)gr * nr + k] = t;
+            if (bd.out_bins)
+                bd.out_bins[(size_t)gr * nr + k] = lo;
+        }
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- encoding
+// Thread (s, part) encodes levels part, part + PARTS, ... of sample s.  Rows of
+// samples beyond the tile's valid count are zeroed (they stay inert through
+// the GEMMs and are never scattered).
+template <int IN, int S, bool SCATTER>
+__device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const BatchDesc &bd, const float *rayf,
+                                                  const float *ts, float *XT, float *dOT, int ns)
+{
+    constexpr int SP = S + 4;
+    constexpr int PARTS = kThreads / S;
+    constexpr int L = IN / 2;
+    const int s = threadIdx.x % S, part = threadIdx.x / S;
+    if (s >= ns) {
+        if constexpr (!SCATTER) {
+            for (int l = part; l < L; l += PARTS) {
+                XT[(2 * l) * SP + s] = 0.f;
+                XT[(2 * l + 1) * SP + s] = 0.f;
+            }
+            if (part == 0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dOT[c * SP + s] = 0.f;
+            }
+        }
+        return;
+    }
+    const int r = s / bd.nr;
+    const float *rf = rayf + r * kRayStride;
+    const float t = ts[s];
+    float ph[3], pl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        pos_two_float(rf[RF_O + a], t, rf[RF_D + a], ph[a], pl[a]);
+    const float2 *tab = reinterpret_cast<const float2 *>(od.theta);
+    float2 *gtab = reinterpret_cast<float2 *>(od.grad);
+#pragma unroll 2
+    for (int l = part; l < L; l += PARTS) {
+        const LevelDesc lv = od.lv[l];
+        Corners cs;
+        level_corners(lv, od.tmask, ph, pl, cs);
+        if constexpr (!SCATTER) {
+            float2 f[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                f[c] = __ldg(tab + lv.offset + cs.idx[c]);
+            float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                e0 = fmaf(cs.wt[c], f[c].x, e0);
+                e1 = fmaf(cs.wt[c], f[c].y, e1);
+            }
+            XT[(2 * l) * SP + s] = e0;
+            XT[(2 * l + 1) * SP + s] = e1;
+        } else {
+            const float g0 = XT[(2 * l) * SP + s], g1 = XT[(2 * l + 1) * SP + s];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float w = cs.wt[c];
+                if (w != 0.f)
+                    atomicAdd(gtab + lv.offset + cs.idx[c], make_float2(w * g0, w * g1));
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- compositing
+// One warp per ray; lane holds samples lane*Q .. lane*Q+Q-1 (Q = ceil(nr/32)).
+// Forward: tau_k = sigma_k delta_k, T_k = exp(-sum_{j<k} tau_j), w_k = T_k (1 - exp(-tau_k)).
+// Adjoint with v_k = gC.c_k + gD t_k + gA:
+//   dL/dsigma_k = delta_k (T_{k+1} v_k - sum_{j>k} w_j v_j).
+// Writes dL/do (o = raw MLP outputs) into dOT; returns the ray's loss (train mode).
+__device__ __forceinline__ float composite_warp(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
+                                                const float *rf, const float *ts, const float *OT, float *dOT,
+                                                int SP, int lane)
+{
+    constexpr int QM = kMaxNr / 32;
+    const int nr = bd.nr;
+    const int Q = (nr + 31) >> 5;
+    const float tf = rf[RF_TF];
+    float sig[QM], col[QM][3], tk[QM], dl[QM], tau[QM], o0[QM], pre[QM];
+    float run = 0.f;
+#pragma unroll
+    for (int q = 0; q < QM; ++q) {
+        sig[q] = 0.f;
+        tau[q] = 0.f;
+        dl[q] = 0.f;
+        tk[q] = 0.f;
+        o0[q] = 0.f;
+        col[q][0] = col[q][1] = col[q][2] = 0.f;
+        const int k = lane * Q + q;
+        if (q < Q && k < nr) {
+            const int s = r * nr + k;
+            o0[q] = OT[s];
+            sig[q] = expf(fminf(o0[q], 15.f));
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                col[q][c] = 1.f / (1.f + expf(-OT[(1 + c) * SP + s]));
+            tk[q] = ts[s];
+            const float tnext = (k + 1 < nr) ? ts[s + 1] : tf;
+            dl[q] = tnext - tk[q];
+            tau[q] = sig[q] * dl[q];
+        }
+        pre[q] = run;  // sum of tau over this lane's earlier samples
+        run += tau[q];
+    }
+    const float incl = warp_incl_scan(run, lane);
+    float base = __shfl_up_sync(kFull, incl, 1);
+    if (lane == 0)
+        base = 0.f;
+    float w[QM], T[QM];
+    float cr0 = 0.f, cr1 = 0.f, cr2 = 0.f, dsum = 0.f, asum = 0.f, ssum = 0.f;
+#pragma unroll
+    for (int q = 0; q < QM; ++q) {
+        T[q] = expf(-(base + pre[q]));
+        w[q] = T[q] * (-expm1f(-tau[q]));
+        cr0 = fmaf(w[q], col[q][0], cr0);
+        cr1 = fmaf(w[q], col[q][1], cr1);
+        cr2 = fmaf(w[q], col[q][2], cr2);
+        dsum = fmaf(w[q], tk[q], dsum);
+        asum += w[q];
+        ssum += sig[q];
+    }
+    const float Cr[3] = {warp_sum(cr0), warp_sum(cr1), warp_sum(cr2)};
+    const float D = warp_sum(dsum), A = warp_sum(asum);
+    if (bd.mode == kRender) {
+        if (lane == 0) {
+            if (bd.out_rgb) {
+                bd.out_rgb[(size_t)gr * 3 + 0] = Cr[0];
+                bd.out_rgb[(size_t)gr * 3 + 1] = Cr[1];
+                bd.out_rgb[(size_t)gr * 3 + 2] = Cr[2];
+            }
+            if (bd.out_depth)
+                bd.out_depth[gr] = D;
+            if (bd.out_acc)
+                bd.out_acc[gr] = A;
+        }
+        return 0.f;
+    }
+    float gC[3], gD, gA, loss = 0.f;
+    bool background = false;
+    if (bd.mode == kRenderBwd) {
+        const float *up = bd.upstream + (size_t)gr * 5;
+        gC[0] = up[0];
+        gC[1] = up[1];
+        gC[2] = up[2];
+        gD = up[3];
+        gA = up[4];
+    } else {
+        background = rf[RF_OBJ] < 0.5f;
+        if (!background) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float e = Cr[c] - rf[RF_RGB + c];
+                loss = fmaf(e, e, loss);
+                gC[c] = 2.f * e;
+            }
+            const float ed = D - rf[RF_DEPTH];
+            loss += od.lambda_d * fabsf(ed);
+            gD = ed > 0.f ? od.lambda_d : (ed < 0.f ? -od.lambda_d : 0.f);
+            gA = 0.f;
+        } else {
+            float dot = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float crd = rf[RF_CR + c];
+                const float e = (Cr[c] + (1.f - A) * crd) - crd;
+                loss = fmaf(e, e, loss);
+                gC[c] = 2.f * e;
+                dot = fmaf(2.f * e, crd, dot);
+            }
+            gD = 0.f;
+            gA = -dot;
+            loss = fmaf(od.lambda_sigma, warp_sum(ssum), loss);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            gC[c] *= bd.inv_r;
+        gD *= bd.inv_r;
+        gA *= bd.inv_r;
+        loss *= bd.inv_r;
+    }
+    // adjoint: suffix sums of w v
+    float wv[QM], v[QM];
+    float lsum = 0.f;
+#pragma unroll
+    for (int q = 0; q < QM; ++q) {
+        v[q] = fmaf(gC[0], col[q][0], fmaf(gC[1], col[q][1], fmaf(gC[2], col[q][2], fmaf(gD, tk[q], gA))));
+        wv[q] = w[q] * v[q];
+        lsum += wv[q];
+    }
+    const float sincl = warp_incl_suffix(lsum, lane);
+    float after = __shfl_down_sync(kFull, sincl, 1);  // sum over later lanes
+    if (lane == 31)
+        after = 0.f;
+    const float sig_reg = background ? od.lambda_sigma * bd.inv_r : 0.f;
+#pragma unroll
+    for (int q = QM - 1; q >= 0; --q) {
+        const int k = lane * Q + q;
+        if (q < Q && k < nr) {
+            const int s = r * nr + k;
+            const float Tn = expf(-(base + pre[q] + tau[q]));
+            const float dsig = fmaf(dl[q], fmaf(Tn, v[q], -after), sig_reg);
+            dOT[s] = (o0[q] < 15.f) ? dsig * sig[q] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float dc = w[q] * gC[c];
+                dOT[(1 + c) * SP + s] = dc * col[q][c] * (1.f - col[q][c]);
+            }
+        }
+        if (q < Q)
+            after += wv[q];
+    }
+    return loss;
+}
+
+// ------------------------------------------------------------------ kernel
+template <int W, int IN, int S>
+__global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const ObjDesc od, const BatchDesc bd)
+{
+    constexpr int SP = S + 4;
+    constexpr int MAXR = S / kMinNr;
+    extern __shared__ __align__(16) float sm[];
+    const int H = od.H;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nW = IN * W + (H - 1) * W * W + 4 * W;  // multiple of 4
+    const int off_out = IN * W + (H - 1) * W * W;
+    float *Wf = sm;             // [in][out] per layer (forward operand)
+    float *Wb = Wf + nW;        // [out][in] per layer (backward operand, = theta layout)
+    float *dWs = Wb + nW;       // weight-gradient accumulators, [out][in]
+    float *XT = dWs + nW;       // [IN][SP]: encoding, then dL/dX
+    float *HT = XT + IN * SP;   // [H][W][SP]: activations, then dL/dH in place
+    float *OT = HT + H * W * SP;  // [4][SP] raw outputs
+    float *dOT = OT + 4 * SP;   // [4][SP] dL/d(raw outputs)
+    float *ts = dOT + 4 * SP;   // [SP] sample depths
+    float *rayf = ts + SP;      // [MAXR][16]
+    float *cdfs = rayf + MAXR * kRayStride;  // [8][kMaxNc + 1]
+
+    const float *th = od.theta + od.mlp_off;
+    for (int i = tid; i < nW; i += kThreads) {
+        const float v = th[i];
+        Wb[i] = v;
+        dWs[i] = 0.f;
+        int lo, nin, nout, j;
+        if (i < IN * W) {
+            lo = 0; nin = IN; nout = W; j = i;
+        } else if (i < off_out) {
+            const int jj = i - IN * W;
+            lo = IN * W + (jj / (W * W)) * W * W; nin = W; nout = W; j = jj % (W * W);
+        } else {
+            lo = off_out; nin = W; nout = 4; j = i - off_out;
+        }
+        Wf[lo + (j % nin) * nout + (j / nin)] = v;
+    }
+    __syncthreads();
+
+    const int nr = bd.nr, NR = bd.rays_per_tile;
+    float loss_acc = 0.f;
+    for (int tile = blockIdx.x; tile < bd.n_tiles; tile += gridDim.x) {
+        const int ray0 = tile * NR;
+        const int nrt = min(NR, bd.n_rays - ray0);
+        const int ns = nrt * nr;
+        // (1) ray data
+        for (int i = tid; i < nrt; i += kThreads) {
+            const int g = ray0 + i;
+            float *rf = rayf + i * kRayStride;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                rf[RF_O + a] = bd.o[(size_t)g * 3 + a];
+                rf[RF_D + a] = bd.d[(size_t)g * 3 + a];
+            }
+            if (bd.mode == kTrain) {
+                const bool obj = bd.is_obj[g] != 0;
+                rf[RF_OBJ] = obj ? 1.f : 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    rf[RF_RGB + a] = obj ? bd.rgb[(size_t)g * 3 + a] : 0.f;
+                rf[RF_DEPTH] = obj ? bd.depth[g] : 0.f;
+                if (!obj) {
+                    if (bd.c_rand) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            rf[RF_CR + a] = bd.c_rand[(size_t)g * 3 + a];
+                    } else {
+                        const float3 c = philox_colour(bd.seed, bd.step, bd.obj_id, (uint32_t)g);
+                        rf[RF_CR] = c.x;
+                        rf[RF_CR + 1] = c.y;
+                        rf[RF_CR + 2] = c.z;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // (2) sampling
+        for (int r = warp; r < nrt; r += kThreads / 32)
+            sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
+        __syncthreads();
+        // (3) encoding
+        encode_or_scatter<IN, S, false>(od, bd, rayf, ts, XT, dOT, ns);
+        __syncthreads();
+        // (4) MLP forward
+        gemm_sn<S, W, kRelu>(XT, Wf, IN, HT);
+        __syncthreads();
+        for (int l = 1; l < H; ++l) {
+            gemm_sn<S, W, kRelu>(HT + (l - 1) * W * SP, Wf + IN * W + (l - 1) * W * W, W, HT + l * W * SP);
+            __syncthreads();
+        }
+        out_layer_fwd<W, S>(HT + (H - 1) * W * SP, Wf + off_out, OT);
+        __syncthreads();
+        // (5) compositing, loss and its adjoint
+        for (int r = warp; r < nrt; r += kThreads / 32) {
+            const float lr = composite_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane);
+            if (lane == 0)
+                loss_acc += lr;
+        }
+        __syncthreads();
+        if (bd.mode == kRender)
+            continue;
+        // (6) MLP backward
+        gemm_dw<S, 4, W>(dOT, HT + (H - 1) * W * SP, dWs + off_out);
+        __syncthreads();
+        gemm_sn<S, W, kMaskByOld>(dOT, Wb + off_out, 4, HT + (H - 1) * W * SP);
+        __syncthreads();
+        for (int l = H - 1; l >= 1; --l) {
+            gemm_dw<S, W, W>(HT + l * W * SP, HT + (l - 1) * W * SP, dWs + IN * W + (l - 1) * W * W);
+            __syncthreads();
+            gemm_sn<S, W, kMaskByOld>(HT + l * W * SP, Wb + IN * W + (l - 1) * W * W, W, HT + (l - 1) * W * SP);
+            __syncthreads();
+        }
+        gemm_dw<S, W, IN>(HT, XT, dWs);
+        __syncthreads();
+        gemm_sn<S, IN, kStore>(HT, Wb, W, XT);
+        __syncthreads();
+        // (7) hash-grid scatter
+        encode_or_scatter<IN, S, true>(od, bd, rayf, ts, XT, dOT, ns);
+        __syncthreads();
+    }
+    if (bd.mode == kRender)
+        return;
+    if (lane == 0 && bd.mode == kTrain && loss_acc != 0.f)
+        atomicAdd(bd.loss, loss_acc);
+    float *gw = od.grad + od.mlp_off;
+    for (int i = tid; i < nW; i += kThreads) {
+        const float v = dWs[i];
+        if (v != 0.f)
+            atomicAdd(gw + i, v);
+    }
+}
+
+inline size_t fused_fp32_smem_floats(int W, int IN, int H, int S)
+{
+    const size_t SP = (size_t)S + 4;
+    const size_t nW = (size_t)IN * W + (size_t)(H - 1) * W * W + 4 * (size_t)W;
+    return 3 * nW + IN * SP + (size_t)H * W * SP + 8 * SP + SP + (size_t)(S / kMinNr) * kRayStride +
+           8 * (size_t)(kMaxNc + 1);
+}
+
+template <int W, int IN, int S>
+cudaError_t launch_fused_t(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
+{
+    const size_t smem = fused_fp32_smem_floats(W, IN, od.H, S) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fused_fp32_kernel<W, IN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    fused_fp32_kernel<W, IN, S><<<grid, kThreads, smem, st>>>(od, bd);
+    return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_fused_w(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st)
+{
+    if (S == 128) {
+        switch (od.IN) {
+        case 8: return launch_fused_t<W, 8, 128>(od, bd, grid, st);
+        case 16: return launch_fused_t<W, 16, 128>(od, bd, grid, st);
+        case 32: return launch_fused_t<W, 32, 128>(od, bd, grid, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if constexpr (W == 64) {  // only the widest MLP ever needs the smaller tile
+        if (S != 64)
+            return cudaErrorInvalidValue;
+        switch (od.IN) {
+        case 8: return launch_fused_t<W, 8, 64>(od, bd, grid, st);
+        case 16: return launch_fused_t<W, 16, 64>(od, bd, grid, st);
+        case 32: return launch_fused_t<W, 32, 64>(od, bd, grid, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace prenom

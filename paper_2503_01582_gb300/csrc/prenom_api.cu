@@ -1,0 +1,693 @@
+// C ABI of the PRENOM training library: object registry, device arenas,
+// argument checking, launch configuration, Adam bookkeeping and kernel timing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "prenom.h"
+#include "prenom_internal.h"
+
+using namespace prenom;
+
+namespace {
+
+std::string g_create_error;
+
+struct Object {
+    bool alive = false;
+    prenom_arch arch{};
+    int IN = 0;
+    int64_t n = 0, n_hash = 0, n_pad = 0;
+    std::vector<int32_t> res, dense;
+    std::vector<int64_t> off;  // float offsets, L + 1 entries
+    float *arena = nullptr, *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    float *grid = nullptr;
+    int32_t R = 0;
+    int32_t step = 0;
+};
+
+struct TimedEv {
+    cudaEvent_t a, b;
+    int kernel;
+};
+
+}  // namespace
+
+struct prenom_ctx {
+    cudaStream_t stream = nullptr;
+    uint64_t seed = 0;
+    int device = 0, n_sm = 0;
+    size_t smem_optin = 0;
+    std::vector<Object> objs;
+    std::string err;
+    float *scratch = nullptr;  // device float receiving losses nobody asked for
+    bool timing = false;
+    std::vector<TimedEv> pending;
+    std::vector<cudaEvent_t> ev_free;
+    double total_ms[PRENOM_N_KERNELS] = {};
+    int64_t count[PRENOM_N_KERNELS] = {};
+    int64_t launches = 0;
+};
+
+namespace {
+
+int fail(prenom_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(prenom_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, PRENOM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Level resolutions of the multiresolution grid (instant-NGP, cited in §III-B):
+// N_l = floor(N_min b^l) with b = exp((ln N_max - ln N_min) / (L - 1)), a 1e-6
+// guard keeping mathematically integral products from rounding down; a level
+// is dense when its (N_l + 1)^3 vertices fit in T entries.
+void level_geometry(const prenom_arch &a, Object &o)
+{
+    const double b = a.L > 1 ? exp((log((double)a.n_max) - log((double)a.n_min)) / (double)(a.L - 1)) : 1.0;
+    const int64_t T = (int64_t)1 << a.log2T;
+    o.res.assign(a.L, 0);
+    o.dense.assign(a.L, 0);
+    o.off.assign(a.L + 1, 0);
+    for (int l = 0; l < a.L; ++l) {
+        const int N = (int)floor((double)a.n_min * pow(b, (double)l) + 1e-6);
+        const int64_t v = (int64_t)(N + 1) * (N + 1) * (N + 1);
+        o.res[l] = N;
+        o.dense[l] = v <= T;
+        o.off[l + 1] = o.off[l] + (o.dense[l] ? v : T) * a.F;
+    }
+    o.n_hash = o.off[a.L];
+    o.IN = a.L * a.F;
+    o.n = o.n_hash + (int64_t)a.width * o.IN + (int64_t)(a.hidden - 1) * a.width * a.width + 4LL * a.width;
+    o.n_pad = (o.n + 63) / 64 * 64;
+}
+
+int check_arch(prenom_ctx *c, const prenom_arch *a)
+{
+    if (!a)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "arch is NULL");
+    if (a->F != 2)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "F = %d: this build supports F = 2", a->F);
+    if (a->L != 4 && a->L != 8 && a->L != 16)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "L = %d: this build supports L in {4, 8, 16}", a->L);
+    if (a->width != 16 && a->width != 32 && a->width != 64)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "width = %d: must be 16, 32 or 64", a->width);
+    if (a->hidden < 1 || a->hidden > 3)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "hidden = %d: must be 1..3", a->hidden);
+    if (a->log2T < 8 || a->log2T > 24)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "log2T = %d: must be 8..24", a->log2T);
+    if (a->n_min < 2 || a->n_max < a->n_min || a->n_max > (1 << 20))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "resolutions %d..%d out of range", a->n_min, a->n_max);
+    if (a->precision != PRENOM_PRECISION_FP32)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "precision %d is not available in this build", a->precision);
+    if (!(a->lambda_d >= 0.f) || !(a->lambda_sigma >= 0.f) || !isfinite(a->lambda_d) || !isfinite(a->lambda_sigma))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "lambda_d and lambda_sigma must be finite and >= 0");
+    return PRENOM_OK;
+}
+
+Object *get_obj(prenom_ctx *c, int32_t obj)
+{
+    if (!c || obj < 0 || obj >= (int32_t)c->objs.size() || !c->objs[obj].alive)
+        return nullptr;
+    return &c->objs[obj];
+}
+
+int check_opts(prenom_ctx *c, const prenom_train_opts *op, bool need_adam)
+{
+    if (!op)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "opts is NULL");
+    if (op->nr < kMinNr || op->nr > kMaxNr)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "nr = %d: must be %d..%d", op->nr, kMinNr, kMaxNr);
+    if (op->nc < 1 || op->nc > kMaxNc)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "nc = %d: must be 1..%d", op->nc, kMaxNc);
+    if (!(op->escape_eps >= 0.f) || !isfinite(op->escape_eps))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "escape_eps must be finite and >= 0");
+    if (!(op->loss_scale_init == 0.f || op->loss_scale_init == 1.f))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "loss scaling is not used by the FP32 path (give 0 or 1)");
+    if (need_adam && !(op->flags & PRENOM_FLAG_NO_ADAM)) {
+        if (!isfinite(op->lr) || !(op->beta1 >= 0.f && op->beta1 < 1.f) || !(op->beta2 >= 0.f && op->beta2 < 1.f) ||
+            !(op->eps >= 0.f) || !isfinite(op->eps))
+            return fail(c, PRENOM_ERR_INVALID_ARG, "Adam constants out of range");
+    }
+    return PRENOM_OK;
+}
+
+int check_batch(prenom_ctx *c, const prenom_ray_batch &b, bool train)
+{
+    Object *o = get_obj(c, b.obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "batch names unknown object %d", b.obj);
+    if (b.n_rays < 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "n_rays = %d < 0", b.n_rays);
+    if (b.n_rays == 0)
+        return PRENOM_OK;
+    if (!b.o || !b.d)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "ray origins and directions are required");
+    if (train && (!b.rgb || !b.depth || !b.is_obj))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "training needs rgb, depth and is_obj");
+    if (!b.t_in && !o->grid)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "object %d has no prior grid and the batch gives no t_in", b.obj);
+    return PRENOM_OK;
+}
+
+void timed_begin(prenom_ctx *c, int kernel, cudaEvent_t *a)
+{
+    *a = nullptr;
+    if (!c->timing)
+        return;
+    if (c->ev_free.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_free.push_back(e);
+    }
+    *a = c->ev_free.back();
+    c->ev_free.pop_back();
+    cudaEventRecord(*a, c->stream);
+    (void)kernel;
+}
+
+void timed_end(prenom_ctx *c, int kernel, cudaEvent_t a)
+{
+    c->launches++;
+    if (!c->timing || !a)
+        return;
+    if (c->ev_free.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_free.push_back(e);
+    }
+    cudaEvent_t b = c->ev_free.back();
+    c->ev_free.pop_back();
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({a, b, kernel});
+}
+
+ObjDesc make_objdesc(const Object &o, float *grad)
+{
+    ObjDesc d{};
+    d.theta = o.theta;
+    d.grad = grad;
+    d.L = o.arch.L;
+    d.IN = o.IN;
+    d.W = o.arch.width;
+    d.H = o.arch.hidden;
+    d.tmask = (uint32_t)((1u << o.arch.log2T) - 1u);
+    d.mlp_off = (uint32_t)o.n_hash;
+    for (int l = 0; l < o.arch.L; ++l) {
+        d.lv[l].res = o.res[l];
+        d.lv[l].offset = (uint32_t)(o.off[l] / o.arch.F);
+        d.lv[l].dense = o.dense[l];
+    }
+    d.grid = o.grid;
+    d.R = o.R;
+    d.lambda_d = o.arch.lambda_d;
+    d.lambda_sigma = o.arch.lambda_sigma;
+    return d;
+}
+
+BatchDesc make_batchdesc(const prenom_ctx *c, const Object &o, const prenom_ray_batch &b, const prenom_train_opts &op,
+                         int mode, int S)
+{
+    BatchDesc d{};
+    d.n_rays = b.n_rays;
+    d.nc = op.nc;
+    d.nr = op.nr;
+    d.rays_per_tile = S / op.nr;
+    d.n_tiles = (b.n_rays + d.rays_per_tile - 1) / d.rays_per_tile;
+    d.mode = mode;
+    d.escape_eps = op.escape_eps;
+    d.inv_r = b.n_rays > 0 ? 1.f / (float)b.n_rays : 0.f;
+    d.o = b.o;
+    d.d = b.d;
+    d.rgb = b.rgb;
+    d.depth = b.depth;
+    d.is_obj = b.is_obj;
+    d.c_rand = b.c_rand;
+    d.u = b.uniforms;
+    d.t_in = b.t_in;
+    d.seed = c->seed;
+    d.step = (uint32_t)o.step;
+    d.obj_id = (uint32_t)b.obj;
+    return d;
+}
+
+int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &bd, int kernel_id)
+{
+    if (bd.n_rays == 0)
+        return PRENOM_OK;
+    const int S = fused_fp32_pick_tile(od.W, od.IN, od.H, c->smem_optin);
+    if (S == 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
+    bd.rays_per_tile = S / bd.nr;
+    bd.n_tiles = (bd.n_rays + bd.rays_per_tile - 1) / bd.rays_per_tile;
+    const int grid = std::min(bd.n_tiles, c->n_sm);
+    cudaEvent_t ev;
+    timed_begin(c, kernel_id, &ev);
+    const cudaError_t e = launch_fused_fp32(od, bd, S, grid, c->stream);
+    timed_end(c, kernel_id, ev);
+    (void)o;
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "fused kernel launch");
+    return PRENOM_OK;
+}
+
+int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train_opts &op)
+{
+    for (size_t first = 0; first < objs.size(); first += kMaxAdamSegs) {
+        AdamArgs a{};
+        a.beta1 = op.beta1;
+        a.beta2 = op.beta2;
+        a.eps = op.eps;
+        const size_t last = std::min(objs.size(), first + kMaxAdamSegs);
+        a.n_segs = (int32_t)(last - first);
+        a.chunk_start[0] = 0;
+        for (size_t i = first; i < last; ++i) {
+            Object &o = c->objs[objs[i]];
+            o.step += 1;
+            const double c1 = 1.0 - pow((double)op.beta1, (double)o.step);
+            const double c2 = 1.0 - pow((double)op.beta2, (double)o.step);
+            AdamSeg &s = a.seg[i - first];
+            s.theta = o.theta;
+            s.grad = o.grad;
+            s.m = o.m;
+            s.v = o.v;
+            s.n = o.n;
+            s.lr_c1 = (float)((double)op.lr / c1);
+            s.inv_c2 = (float)(1.0 / c2);
+            a.chunk_start[i - first + 1] = a.chunk_start[i - first] + (o.n + kAdamChunk - 1) / kAdamChunk;
+        }
+        const int64_t chunks = a.chunk_start[a.n_segs];
+        const int grid = (int)std::min<int64_t>(chunks, (int64_t)c->n_sm * 8);
+        if (grid == 0)
+            continue;
+        cudaEvent_t ev;
+        timed_begin(c, PRENOM_KERNEL_ADAM, &ev);
+        const cudaError_t e = launch_adam(a, grid, c->stream);
+        timed_end(c, PRENOM_KERNEL_ADAM, ev);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "Adam launch");
+    }
+    return PRENOM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prenom_create(prenom_ctx **out, void *cuda_stream, uint64_t seed)
+{
+    if (!out)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    prenom_ctx *c = new (std::nothrow) prenom_ctx();
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_OOM, "host allocation failed");
+    c->stream = (cudaStream_t)cuda_stream;
+    c->seed = seed;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    int optin = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (e == cudaSuccess) {
+        int major = 0;
+        e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+        if (e == cudaSuccess && major < 10) {
+            delete c;
+            return fail(nullptr, PRENOM_ERR_CUDA, "device compute capability %d.x: this library is built for sm_103a",
+                        major);
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->scratch, 64 * sizeof(float));
+    if (e != cudaSuccess) {
+        const int code = (e == cudaErrorMemoryAllocation) ? PRENOM_ERR_OOM : PRENOM_ERR_CUDA;
+        fail(nullptr, code, "context creation: %s", cudaGetErrorString(e));
+        delete c;
+        return code;
+    }
+    c->smem_optin = (size_t)optin;
+    *out = c;
+    return PRENOM_OK;
+}
+
+void prenom_destroy(prenom_ctx *c)
+{
+    if (!c)
+        return;
+    cudaStreamSynchronize(c->stream);
+    for (auto &o : c->objs) {
+        cudaFree(o.arena);
+        cudaFree(o.grid);
+    }
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->ev_free)
+        cudaEventDestroy(e);
+    cudaFree(c->scratch);
+    delete c;
+}
+
+const char *prenom_last_error(const prenom_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+int prenom_create_object(prenom_ctx *c, const prenom_arch *arch, const float *init_params, int32_t *obj_out)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!obj_out)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "obj_out is NULL");
+    int rc = check_arch(c, arch);
+    if (rc)
+        return rc;
+    Object o;
+    o.arch = *arch;
+    level_geometry(*arch, o);
+    cudaError_t e = cudaMalloc(&o.arena, (size_t)o.n_pad * 4 * sizeof(float));
+    if (e != cudaSuccess)
+        return fail(c, PRENOM_ERR_OOM, "object arena of %lld floats: %s", (long long)(o.n_pad * 4),
+                    cudaGetErrorString(e));
+    o.theta = o.arena;
+    o.grad = o.arena + o.n_pad;
+    o.m = o.arena + 2 * o.n_pad;
+    o.v = o.arena + 3 * o.n_pad;
+    e = cudaMemsetAsync(o.grad, 0, (size_t)o.n_pad * 3 * sizeof(float), c->stream);
+    if (e == cudaSuccess) {
+        if (init_params) {
+            e = cudaMemcpyAsync(o.theta, init_params, (size_t)o.n * sizeof(float), cudaMemcpyDefault, c->stream);
+        } else {
+            int32_t shape[8];
+            const int nl = arch->hidden + 1;
+            for (int l = 0; l < nl; ++l) {
+                shape[2 * l] = (l == arch->hidden) ? 4 : arch->width;
+                shape[2 * l + 1] = (l == 0) ? o.IN : arch->width;
+            }
+            cudaEvent_t ev;
+            timed_begin(c, PRENOM_KERNEL_INIT, &ev);
+            e = launch_init_params(o.theta, o.n_hash, shape, nl, c->seed, (uint32_t)c->objs.size(), c->n_sm * 4,
+                                   c->stream);
+            timed_end(c, PRENOM_KERNEL_INIT, ev);
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(o.arena);
+        return cuda_fail(c, e, "object initialisation");
+    }
+    o.alive = true;
+    c->objs.push_back(o);
+    *obj_out = (int32_t)(c->objs.size() - 1);
+    return PRENOM_OK;
+}
+
+int prenom_destroy_object(prenom_ctx *c, int32_t obj)
+{
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(o->arena);
+    cudaFree(o->grid);
+    *o = Object();
+    return PRENOM_OK;
+}
+
+int prenom_param_count(prenom_ctx *c, int32_t obj, size_t *n)
+{
+    Object *o = get_obj(c, obj);
+    if (!o || !n)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d or NULL output", obj);
+    *n = (size_t)o->n;
+    return PRENOM_OK;
+}
+
+int prenom_level_info(prenom_ctx *c, int32_t obj, int32_t *res, int64_t *offset, int32_t *dense)
+{
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    for (int l = 0; l < o->arch.L; ++l) {
+        if (res)
+            res[l] = o->res[l];
+        if (dense)
+            dense[l] = o->dense[l];
+    }
+    if (offset)
+        for (int l = 0; l <= o->arch.L; ++l)
+            offset[l] = o->off[l];
+    return PRENOM_OK;
+}
+
+int prenom_set_prior_grid(prenom_ctx *c, int32_t obj, const float *grid, int32_t res)
+{
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    if (!grid || res < 2 || res > 1024)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "grid must be non-NULL with 2 <= res <= 1024");
+    const size_t bytes = (size_t)res * res * res * sizeof(float);
+    if (o->R != res) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(o->grid);
+        o->grid = nullptr;
+        o->R = 0;
+        const cudaError_t e = cudaMalloc(&o->grid, bytes);
+        if (e != cudaSuccess)
+            return fail(c, PRENOM_ERR_OOM, "prior grid %d^3: %s", res, cudaGetErrorString(e));
+        o->R = res;
+    }
+    const cudaError_t e = cudaMemcpyAsync(o->grid, grid, bytes, cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "prior grid copy");
+    return PRENOM_OK;
+}
+
+int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_batches,
+                      const prenom_train_opts *op, float *loss_dev)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_batches < 0 || (n_batches > 0 && !batches))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "bad batch list");
+    int rc = check_opts(c, op, true);
+    if (rc)
+        return rc;
+    for (int i = 0; i < n_batches; ++i)
+        if ((rc = check_batch(c, batches[i], true)))
+            return rc;
+    if (loss_dev && n_batches > 0) {
+        const cudaError_t e = cudaMemsetAsync(loss_dev, 0, (size_t)n_batches * sizeof(float), c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "loss reset");
+    }
+    std::vector<int32_t> touched;
+    for (int i = 0; i < n_batches; ++i) {
+        const prenom_ray_batch &b = batches[i];
+        Object &o = c->objs[b.obj];
+        ObjDesc od = make_objdesc(o, o.grad);
+        BatchDesc bd = make_batchdesc(c, o, b, *op, kTrain, 128);
+        bd.loss = loss_dev ? loss_dev + i : c->scratch;
+        if ((rc = launch_fused(c, o, od, bd, PRENOM_KERNEL_TRAIN)))
+            return rc;
+        if (std::find(touched.begin(), touched.end(), b.obj) == touched.end())
+            touched.push_back(b.obj);
+    }
+    if ((op->flags & PRENOM_FLAG_CHECK_FINITE) && loss_dev && n_batches > 0) {
+        std::vector<float> h(n_batches);
+        const cudaError_t e = cudaMemcpyAsync(h.data(), loss_dev, h.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                              c->stream);
+        if (e == cudaSuccess)
+            cudaStreamSynchronize(c->stream);
+        for (float v : h)
+            if (!isfinite(v)) {
+                for (int32_t id : touched)
+                    cudaMemsetAsync(c->objs[id].grad, 0, (size_t)c->objs[id].n * sizeof(float), c->stream);
+                return fail(c, PRENOM_ERR_NONFINITE, "non-finite loss; gradients dropped, no Adam step");
+            }
+    }
+    if (op->flags & PRENOM_FLAG_NO_ADAM)
+        return PRENOM_OK;
+    return run_adam(c, touched, *op);
+}
+
+int prenom_render(prenom_ctx *c, const prenom_ray_batch *b, const prenom_train_opts *op, float *rgb, float *depth,
+                  float *acc, int32_t *bins_out, float *t_out)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!b)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "batch is NULL");
+    int rc = check_opts(c, op, false);
+    if (rc || (rc = check_batch(c, *b, false)))
+        return rc;
+    Object &o = c->objs[b->obj];
+    ObjDesc od = make_objdesc(o, nullptr);
+    BatchDesc bd = make_batchdesc(c, o, *b, *op, kRender, 128);
+    bd.out_rgb = rgb;
+    bd.out_depth = depth;
+    bd.out_acc = acc;
+    bd.out_bins = bins_out;
+    bd.out_t = t_out;
+    bd.loss = c->scratch;
+    return launch_fused(c, o, od, bd, PRENOM_KERNEL_RENDER);
+}
+
+int prenom_render_backward(prenom_ctx *c, const prenom_ray_batch *b, const prenom_train_opts *op, const float *d_out,
+                           float *grad)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!b || !grad || (b->n_rays > 0 && !d_out))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "batch, d_out and grad are required");
+    int rc = check_opts(c, op, false);
+    if (rc || (rc = check_batch(c, *b, false)))
+        return rc;
+    Object &o = c->objs[b->obj];
+    ObjDesc od = make_objdesc(o, grad);
+    BatchDesc bd = make_batchdesc(c, o, *b, *op, kRenderBwd, 128);
+    bd.upstream = d_out;
+    bd.loss = c->scratch;
+    return launch_fused(c, o, od, bd, PRENOM_KERNEL_RENDER_BWD);
+}
+
+static float *state_ptr(Object *o, int32_t which)
+{
+    switch (which) {
+    case PRENOM_STATE_THETA: return o->theta;
+    case PRENOM_STATE_GRAD: return o->grad;
+    case PRENOM_STATE_ADAM_M: return o->m;
+    case PRENOM_STATE_ADAM_V: return o->v;
+    default: return nullptr;
+    }
+}
+
+int prenom_get_state(prenom_ctx *c, int32_t obj, int32_t which, float *dst, size_t n)
+{
+    Object *o = get_obj(c, obj);
+    if (!o || !dst || (size_t)o->n != n || !state_ptr(o, which))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "get_state: bad object, buffer, size or selector");
+    cudaError_t e = cudaMemcpyAsync(dst, state_ptr(o, which), n * sizeof(float), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "get_state");
+}
+
+int prenom_set_state(prenom_ctx *c, int32_t obj, int32_t which, const float *src, size_t n)
+{
+    Object *o = get_obj(c, obj);
+    if (!o || !src || (size_t)o->n != n || !state_ptr(o, which))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "set_state: bad object, buffer, size or selector");
+    cudaError_t e = cudaMemcpyAsync(state_ptr(o, which), src, n * sizeof(float), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "set_state");
+}
+
+int prenom_get_step(prenom_ctx *c, int32_t obj, int32_t *step)
+{
+    Object *o = get_obj(c, obj);
+    if (!o || !step)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d or NULL output", obj);
+    *step = o->step;
+    return PRENOM_OK;
+}
+
+int prenom_set_step(prenom_ctx *c, int32_t obj, int32_t step)
+{
+    Object *o = get_obj(c, obj);
+    if (!o || step < 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d or negative step", obj);
+    o->step = step;
+    return PRENOM_OK;
+}
+
+int prenom_zero_grads(prenom_ctx *c, int32_t obj)
+{
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    const cudaError_t e = cudaMemsetAsync(o->grad, 0, (size_t)o->n * sizeof(float), c->stream);
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "zero_grads");
+}
+
+int prenom_sync(prenom_ctx *c)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "stream");
+}
+
+int prenom_enable_timing(prenom_ctx *c, int32_t enable)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    cudaStreamSynchronize(c->stream);
+    for (auto &p : c->pending) {
+        c->ev_free.push_back(p.a);
+        c->ev_free.push_back(p.b);
+    }
+    c->pending.clear();
+    for (int k = 0; k < PRENOM_N_KERNELS; ++k) {
+        c->total_ms[k] = 0.0;
+        c->count[k] = 0;
+    }
+    c->timing = enable != 0;
+    return PRENOM_OK;
+}
+
+int prenom_kernel_time(prenom_ctx *c, int32_t kernel, double *total_ms, int64_t *launches)
+{
+    if (!c || kernel < 0 || kernel >= PRENOM_N_KERNELS)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "bad context or kernel id");
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream");
+    for (auto &p : c->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        c->total_ms[p.kernel] += ms;
+        c->count[p.kernel] += 1;
+        c->ev_free.push_back(p.a);
+        c->ev_free.push_back(p.b);
+    }
+    c->pending.clear();
+    if (total_ms)
+        *total_ms = c->total_ms[kernel];
+    if (launches)
+        *launches = c->count[kernel];
+    return PRENOM_OK;
+}
+
+int prenom_launch_count(prenom_ctx *c, int64_t *launches)
+{
+    if (!c || !launches)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "bad arguments");
+    *launches = c->launches;
+    return PRENOM_OK;
+}
+
+}  // extern "C"

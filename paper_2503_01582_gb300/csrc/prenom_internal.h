@@ -1,0 +1,84 @@
+// Internal descriptors and launchers of the PRENOM CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace prenom {
+
+constexpr int kMaxLevels = 16;
+constexpr int kThreads = 256;   // threads per CTA of the fused kernels
+constexpr int kMaxNc = 256;     // prior probes per ray
+constexpr int kMinNr = 4;       // samples per ray, lower bound (caps rays per tile)
+constexpr int kMaxNr = 128;
+constexpr int kMaxAdamSegs = 128;
+
+// Hash-grid level: resolution N_l, first entry of the level (in F-feature entries), dense flag.
+struct LevelDesc {
+    int32_t res;
+    uint32_t offset;
+    int32_t dense;
+};
+
+// One object's field as the fused kernel sees it.
+struct ObjDesc {
+    const float *theta;  // parameters (hash tables then MLP matrices)
+    float *grad;         // gradient accumulator (atomically added)
+    int32_t L, IN, W, H;
+    uint32_t tmask;      // T - 1 for hashed levels
+    uint32_t mlp_off;    // float offset of W_1 in theta / grad
+    LevelDesc lv[kMaxLevels];
+    const float *grid;   // prior density grid [R][R][R], x fastest
+    int32_t R;
+    float lambda_d, lambda_sigma;
+};
+
+enum Mode : int32_t { kTrain = 0, kRender = 1, kRenderBwd = 2 };
+
+// One batch of rays and what to do with it.
+struct BatchDesc {
+    int32_t n_rays, nc, nr, rays_per_tile, n_tiles;
+    int32_t mode;
+    float escape_eps, inv_r;
+    const float *o, *d, *rgb, *depth;
+    const uint8_t *is_obj;
+    const float *c_rand, *u, *t_in;
+    const float *upstream;  // [n][5] for kRenderBwd
+    float *loss;            // device scalar, accumulated (kTrain)
+    float *out_rgb, *out_depth, *out_acc, *out_t;
+    int32_t *out_bins;
+    uint64_t seed;
+    uint32_t step, obj_id;
+};
+
+// Dynamic shared memory (bytes) of the fused FP32 kernel for (W, IN, H, S).
+size_t fused_fp32_smem(int W, int IN, int H, int S);
+// Largest tile (128 or 64 samples) whose shared memory fits; 0 if none.
+int fused_fp32_pick_tile(int W, int IN, int H, size_t smem_limit);
+// Launches the fused kernel; returns the CUDA error of the launch.
+cudaError_t launch_fused_fp32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
+cudaError_t launch_fused_fp32_w16(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
+cudaError_t launch_fused_fp32_w32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
+cudaError_t launch_fused_fp32_w64(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
+
+// Adam over up to kMaxAdamSegs parameter spans.
+struct AdamSeg {
+    float *theta, *grad, *m, *v;
+    int64_t n;
+    float lr_c1;     // lr / (1 - beta1^t)
+    float inv_c2;    // 1 / (1 - beta2^t)
+};
+struct AdamArgs {
+    int32_t n_segs;
+    float beta1, beta2, eps;
+    int64_t chunk_start[kMaxAdamSegs + 1];  // prefix sums of per-segment chunk counts
+    AdamSeg seg[kMaxAdamSegs];
+};
+constexpr int kAdamChunk = 4096;  // floats per chunk
+cudaError_t launch_adam(const AdamArgs &a, int grid, cudaStream_t st);
+
+// Random initialisation of theta: hash entries U(-1e-4, 1e-4), MLP Xavier-uniform.
+cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_shape /*[2*(H+1)]*/,
+                               int n_layers, uint64_t seed, uint32_t obj, int grid, cudaStream_t st);
+
+}  // namespace prenom

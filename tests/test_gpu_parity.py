@@ -1,0 +1,341 @@
+"""CUDA path against the FP64 oracle, element by element, on seeded synthetic scenes.
+
+Acceptance (per tensor, max |gpu - oracle| / max |oracle|): forward outputs
+(colour, depth, opacity, loss) <= 1e-5, gradients <= 1e-4; sample bins exact
+away from CDF edges (1e-5 margin, either neighbour inside it).
+"""
+
+import numpy as np
+import pytest
+
+from helpers import CFG1, CFG2, bins_match, case, oracle_samples, rel
+
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_01582_gb300 import build
+
+    build.build()
+    import paper_2503_01582_gb300 as p
+
+    return p
+
+
+def _arch(p, d):
+    return p.make_arch(L=d["L"], F=d["F"], log2T=d["log2T"], n_min=d["n_min"], n_max=d["n_max"], width=d["width"],
+                       hidden=d["hidden"], lambda_d=d["lambda_d"], lambda_sigma=d["lambda_sigma"])
+
+
+def _dev(rays, obj, u=None, cr=None, t_in=None):
+    import torch
+
+    b = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
+    b["obj"] = obj
+    if u is not None:
+        b["uniforms"] = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).cuda()
+    if cr is not None:
+        b["c_rand"] = torch.from_numpy(np.ascontiguousarray(cr, dtype=np.float32)).cuda()
+    if t_in is not None:
+        b["t_in"] = torch.from_numpy(np.ascontiguousarray(t_in, dtype=np.float32)).cuda()
+    return b
+
+
+def _setup(pkg, arch, theta, grid):
+    ctx = pkg.Context(seed=7)
+    obj = ctx.create_object(_arch(pkg, arch), theta)
+    ctx.set_prior_grid(obj, grid)
+    return ctx, obj
+
+
+def test_layout_contract(pkg):
+    for arch in (CFG1, CFG2, dict(CFG1, L=4, log2T=12, n_max=32, width=16, hidden=3)):
+        a = orc.Arch(**arch)
+        ctx = pkg.Context()
+        obj = ctx.create_object(_arch(pkg, arch))
+        assert ctx.param_count(obj) == orc.param_count(a)
+        res, off, dense = ctx.level_info(obj)
+        assert res == [orc.level_res(a, l) for l in range(a.L)]
+        assert off == [orc.level_offset(a, l) for l in range(a.L + 1)]
+        assert dense == [orc.level_dense(a, l) for l in range(a.L)]
+        ctx.close()
+
+
+@pytest.mark.parametrize("nc,nr", [(32, 32), (64, 64), (48, 48), (7, 5)])
+def test_sampler_bins_and_depths(pkg, nc, nr):
+    a, theta, grid, rays, u, cr = case(CFG1, 300, nr, nc, seed=3)
+    ctx, obj = _setup(pkg, CFG1, theta, grid)
+    opts = pkg.make_opts(nc=nc, nr=nr)
+    out = ctx.render(_dev(rays, obj, u), opts, want_samples=True)
+    gb = out["bins"].cpu().numpy()
+    gt = out["t"].cpu().numpy().astype(np.float64)
+    want = oracle_samples(grid, rays, u, nc, nr)
+    bad, near = bins_match(gb, want["bins"], want["cdf"], u)
+    assert bad == 0, (bad, near)
+    assert near <= 0.001 * u.size + 2
+    # depths: the FP32 CDF error (a few 1e-7) is divided by the bin mass
+    delta = (want["tf"] - want["tn"]) / nc
+    mass = np.take_along_axis(np.diff(want["cdf"], axis=1), want["bins"], axis=1)
+    tol = delta[:, None] * 2e-6 / np.maximum(mass, 1e-30) + 1e-6 * np.abs(want["t"]) + 1e-7
+    ok = (gb == want["bins"])
+    assert np.all(np.abs(gt - want["t"])[ok] <= tol[ok])
+    ctx.close()
+
+
+def test_sampler_special_cases(pkg):
+    import torch
+
+    R = 16
+    o = np.array([[-1.0, 0.5, 0.5], [-1.0, 0.31, 0.52], [0.5, 0.5, 0.5]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]], np.float32)
+    rays = dict(o=o, d=d)
+    nc, nr = 32, 32
+    u = np.sort(np.random.default_rng(0).random((3, nr)).astype(np.float32), axis=1)
+    a = orc.Arch(**CFG1)
+    theta = np.zeros(orc.param_count(a), np.float32)
+    for name, grid in [("escape", np.zeros((R, R, R), np.float32)),
+                       ("one-hot", np.where(np.arange(R)[None, None, :] >= 10, 1e30, 0.0).repeat(R, 0).repeat(R, 1)
+                        .astype(np.float32)),
+                       ("constant", np.full((R, R, R), 3.0, np.float32))]:
+        grid = np.ascontiguousarray(np.broadcast_to(grid, (R, R, R)), dtype=np.float32)
+        ctx, obj = _setup(pkg, CFG1, theta, grid)
+        out = ctx.render(_dev(rays, obj, u), pkg.make_opts(nc=nc, nr=nr), want_samples=True)
+        gb = out["bins"].cpu().numpy()
+        want = oracle_samples(grid, rays, u, nc, nr)
+        bad, near = bins_match(gb, want["bins"], want["cdf"], u)
+        assert bad == 0, name
+        if name == "escape":
+            assert want["escape"].all()
+            np.testing.assert_array_equal(gb, np.floor(u * nc).astype(np.int32))
+        if name == "one-hot":
+            assert np.all(gb[0] == gb[0, 0]) and np.all(gb[1] == gb[1, 0])
+        ctx.close()
+    torch.cuda.synchronize()
+
+
+def test_forward_given_samples(pkg):
+    """Encoding, MLP, compositing on the oracle's own sample depths (rounded to FP32)."""
+    a, theta, grid, rays, u, cr = case(CFG1, 256, 32, 32, seed=5, hash_range=0.5)
+    want_s = oracle_samples(grid, rays, u, 32, 32)
+    t_in = want_s["t"].astype(np.float32)
+    want = orc.batch(a, theta, grid, rays, 32, 32, t_in=t_in, c_rand=cr)
+    ctx, obj = _setup(pkg, CFG1, theta, grid)
+    out = ctx.render(_dev(rays, obj, t_in=t_in), pkg.make_opts(nc=32, nr=32), want_samples=True)
+    np.testing.assert_array_equal(out["t"].cpu().numpy(), t_in)
+    for k in ("rgb", "depth", "acc"):
+        e = rel(out[k].cpu().numpy(), want[k])
+        assert e <= FWD_TOL, (k, e)
+    ctx.close()
+
+
+@pytest.mark.parametrize("arch", [CFG1, dict(CFG1, lambda_sigma=1e-2), dict(CFG1, L=4, log2T=12, n_max=64, width=16,
+                                                                             hidden=3)])
+def test_forward_and_gradients_from_uniforms(pkg, arch):
+    import torch
+
+    a, theta, grid, rays, u, cr = case(arch, 200, 32, 32, seed=11, hash_range=0.5)
+    want = orc.batch(a, theta, grid, rays, 32, 32, u=u, c_rand=cr, want_grad=True)
+    ctx, obj = _setup(pkg, arch, theta, grid)
+    b = _dev(rays, obj, u, cr)
+    out = ctx.render(b, pkg.make_opts(nc=32, nr=32))
+    for k in ("rgb", "depth", "acc"):
+        e = rel(out[k].cpu().numpy(), want[k])
+        assert e <= FWD_TOL, (k, e)
+    loss = torch.zeros(1, device="cuda")
+    ctx.train_step([b], pkg.make_opts(nc=32, nr=32, flags=pkg.PRENOM_FLAG_NO_ADAM), loss)
+    assert abs(loss.item() - want["loss"]) <= FWD_TOL * abs(want["loss"])
+    g = ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy()
+    nh = orc.n_hash_params(a)
+    # per level and per layer blocks
+    for l in range(a.L):
+        lo, hi = orc.level_offset(a, l), orc.level_offset(a, l + 1)
+        assert rel(g[lo:hi], want["grad"][lo:hi]) <= GRAD_TOL, ("level", l)
+    for layer in range(a.hidden + 1):
+        lo, hi = orc.mlp_offset(a, layer), orc.mlp_offset(a, layer + 1)
+        assert rel(g[lo:hi], want["grad"][lo:hi]) <= GRAD_TOL, ("layer", layer)
+    assert np.all(g[:nh][want["grad"][:nh] == 0] == 0)  # untouched entries stay exactly zero
+    ctx.close()
+
+
+def test_adam_one_step_and_trajectory(pkg):
+    import torch
+
+    a, theta, grid, rays0, u0, cr0 = case(CFG1, 256, 32, 32, seed=21)
+    ob = orc.OracleObject(a, theta, grid)
+    ctx, obj = _setup(pkg, CFG1, theta, grid)
+    from helpers import pool_cfg1
+    from synth import random_colours, sample_batch, stratified_uniforms
+
+    _, pool = pool_cfg1()
+    losses_g, losses_o = [], []
+    loss = torch.zeros(1, device="cuda")
+    for step in range(20):
+        rays = sample_batch(pool, 256, 100 + step)
+        u = stratified_uniforms(256, 32, 200 + step)
+        cr = random_colours(256, 300 + step)
+        losses_o.append(ob.train_step(rays, 32, 32, u=u, c_rand=cr, lr=1e-2))
+        ctx.train_step([_dev(rays, obj, u, cr)], pkg.make_opts(nc=32, nr=32, lr=1e-2), loss)
+        losses_g.append(loss.item())
+        if step == 0:
+            th = ctx.get_state(obj, pkg.PRENOM_STATE_THETA).cpu().numpy()
+            g_o = orc.batch(a, theta, grid, rays, 32, 32, u=u, c_rand=cr, want_grad=True)["grad"]
+            # Adam normalises each gradient entry: where the oracle gradient is
+            # below the FP32 noise floor the sign of the first step is arbitrary
+            sure = np.abs(g_o) > 1e-5 * np.abs(g_o).max()
+            d = np.abs(th - ob.theta)
+            assert np.max(d[sure]) <= GRAD_TOL * np.abs(ob.theta).max()
+            assert np.max(d[~sure], initial=0.0) <= 2.01e-2
+    lg, lo = np.array(losses_g), np.array(losses_o)
+    assert np.all(np.abs(lg - lo) <= GRAD_TOL * np.abs(lo)), np.abs(lg - lo) / np.abs(lo)
+    assert ctx.get_step(obj) == 20
+    ctx.close()
+
+
+def test_edge_cases(pkg):
+    import torch
+
+    a, theta, grid, rays, u, cr = case(CFG1, 37, 48, 16, seed=31)
+    ctx, obj = _setup(pkg, CFG1, theta, grid)
+    opts = pkg.make_opts(nc=16, nr=48, flags=pkg.PRENOM_FLAG_NO_ADAM)
+    # empty batch: no work, loss 0
+    loss = torch.ones(1, device="cuda")
+    empty = {k: v[:0] for k, v in _dev(rays, obj, u, cr).items() if k != "obj"}
+    empty["obj"] = obj
+    ctx.train_step([empty], opts, loss)
+    assert loss.item() == 0.0
+    # ragged: 37 rays of 48 samples (2 rays per 128-sample tile, 1 in the last)
+    want = orc.batch(a, theta, grid, rays, 16, 48, u=u, c_rand=cr, want_grad=True)
+    ctx.train_step([_dev(rays, obj, u, cr)], opts, loss)
+    assert abs(loss.item() - want["loss"]) <= FWD_TOL * abs(want["loss"])
+    g = ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy()
+    assert rel(g, want["grad"]) <= GRAD_TOL
+    # rays that miss the cube and rays starting inside it
+    miss = dict(o=np.array([[-1, 2, 0.5], [0.5, 0.5, 0.5], [0.2, 0.9, 0.1]], np.float32),
+                d=np.array([[1, 0, 0], [0, 0.6, 0.8], [0.6, -0.8, 0.0]], np.float32),
+                rgb=np.full((3, 3), 0.5, np.float32), depth=np.ones(3, np.float32),
+                is_obj=np.array([1, 1, 0], np.uint8))
+    um = u[:3]
+    want = orc.batch(a, theta, grid, miss, 16, 48, u=um, c_rand=cr[:3])
+    out = ctx.render(_dev(miss, obj, um, cr[:3]), opts)
+    for k in ("rgb", "depth", "acc"):
+        assert rel(out[k].cpu().numpy(), want[k]) <= FWD_TOL, k
+    assert out["acc"][0].item() == 0.0
+    ctx.close()
+
+
+def test_render_backward_matches_oracle(pkg):
+    import torch
+
+    a, theta, grid, rays, u, cr = case(CFG1, 128, 32, 32, seed=41, hash_range=0.5)
+    up = np.random.default_rng(1).normal(size=(128, 5))
+    want = orc.batch(a, theta, grid, rays, 32, 32, u=u, upstream=up, want_grad=True)
+    ctx, obj = _setup(pkg, CFG1, theta, grid)
+    grad = torch.zeros(ctx.param_count(obj), device="cuda")
+    ctx.render_backward(_dev(rays, obj, u), pkg.make_opts(nc=32, nr=32),
+                        torch.from_numpy(up.astype(np.float32)).cuda(), grad)
+    assert rel(grad.cpu().numpy(), want["grad"]) <= GRAD_TOL
+    # through torch.autograd
+    from paper_2503_01582_gb300.autograd import render
+
+    th = torch.from_numpy(theta).cuda().requires_grad_(True)
+    rgb, depth, acc = render(ctx, obj, th, _dev(rays, obj, u), pkg.make_opts(nc=32, nr=32))
+    upt = torch.from_numpy(up.astype(np.float32)).cuda()
+    (rgb * upt[:, :3]).sum().add((depth * upt[:, 3]).sum()).add((acc * upt[:, 4]).sum()).backward()
+    assert rel(th.grad.cpu().numpy(), want["grad"]) <= GRAD_TOL
+    ctx.close()
+
+
+def test_philox_draws_match_oracle(pkg):
+    import torch
+
+    a, theta, grid, rays, u, cr = case(CFG1, 96, 32, 32, seed=51)
+    ctx = pkg.Context(seed=0x1234567890AB)
+    obj = ctx.create_object(_arch(pkg, CFG1), theta)
+    ctx.set_prior_grid(obj, grid)
+    ctx.set_step(obj, 5)
+    out = ctx.render(_dev(rays, obj), pkg.make_opts(nc=32, nr=32), want_samples=True)
+    uu = orc.philox_uniforms(0x1234567890AB, 5, obj, 96, 32)
+    want = oracle_samples(grid, rays, uu, 32, 32)
+    bad, _ = bins_match(out["bins"].cpu().numpy(), want["bins"], want["cdf"], uu)
+    assert bad == 0
+    crr = orc.philox_colours(0x1234567890AB, 5, obj, 96)
+    w = orc.batch(a, theta, grid, rays, 32, 32, u=uu, c_rand=crr)
+    loss = torch.zeros(1, device="cuda")
+    ctx.train_step([_dev(rays, obj)], pkg.make_opts(nc=32, nr=32, flags=pkg.PRENOM_FLAG_NO_ADAM), loss)
+    assert abs(loss.item() - w["loss"]) <= FWD_TOL * abs(w["loss"])
+    ctx.close()
+
+
+def test_random_init_and_errors(pkg):
+    import torch
+
+    ctx = pkg.Context(seed=3)
+    obj = ctx.create_object(_arch(pkg, CFG1))
+    th = ctx.get_state(obj).cpu().numpy()
+    a = orc.Arch(**CFG1)
+    nh = orc.n_hash_params(a)
+    assert np.abs(th[:nh]).max() <= 1e-4 and np.abs(th[:nh]).max() > 0.9e-4
+    assert abs(th[:nh].mean()) < 1e-6
+    lim = np.sqrt(6.0 / (16 + 32))
+    w1 = th[nh:nh + 32 * 16]
+    assert np.abs(w1).max() <= lim and np.abs(w1).max() > 0.9 * lim
+    with pytest.raises(pkg.PrenomError) as e:
+        ctx.create_object(_arch(pkg, dict(CFG1, width=48)))
+    assert e.value.code == -1
+    with pytest.raises(pkg.PrenomError) as e:  # no prior grid
+        ctx.render(dict(obj=obj, o=torch.zeros((4, 3), device="cuda"), d=torch.ones((4, 3), device="cuda")),
+                   pkg.make_opts())
+    assert e.value.code == -1
+    with pytest.raises(pkg.PrenomError):
+        ctx.train_step([dict(obj=99, o=torch.zeros((4, 3), device="cuda"), d=torch.ones((4, 3), device="cuda"))],
+                       pkg.make_opts())
+    with pytest.raises(pkg.PrenomError):
+        ctx.render(dict(obj=obj, o=torch.zeros((4, 3), device="cuda"), d=torch.ones((4, 3), device="cuda")),
+                   pkg.make_opts(nr=200))
+    ctx.close()
+
+
+def test_full_size_config_sampled(pkg):
+    """The 16-level, 2^19-entry, 2x64 MLP object at 4096 rays x 64 samples in the
+    launch configuration the benchmark times; the oracle checks sampled rays'
+    outputs, and the full batch's loss and MLP gradients on a ray subset."""
+    import torch
+
+    arch = CFG2
+    a = orc.Arch(**arch)
+    from helpers import pool_cfg2
+    from synth import init_params, prior_grid, random_colours, sample_batch, stratified_uniforms
+
+    sc, pool = pool_cfg2()
+    rays = sample_batch(pool, 4096, 0)
+    u = stratified_uniforms(4096, 64, 1)
+    cr = random_colours(4096, 2)
+    grid = prior_grid(sc, 64, 0)
+    theta = init_params(orc.n_hash_params(a), a.mlp_shapes(), 3, hash_range=0.5)
+    ctx, obj = _setup(pkg, arch, theta, grid)
+    b = _dev(rays, obj, u, cr)
+    out = ctx.render(b, pkg.make_opts(nc=64, nr=64))
+    idx = np.random.default_rng(0).choice(4096, 48, replace=False)
+    sub = {k: v[idx] for k, v in rays.items()}
+    want = orc.batch(a, theta, grid, sub, 64, 64, u=u[idx], c_rand=cr[idx])
+    for k in ("rgb", "depth", "acc"):
+        assert rel(out[k].cpu().numpy()[idx], want[k]) <= FWD_TOL, k
+    # gradients of a 64-ray batch at full architecture size
+    sub = {k: v[:64] for k, v in rays.items()}
+    want = orc.batch(a, theta, grid, sub, 64, 64, u=u[:64], c_rand=cr[:64], want_grad=True)
+    loss = torch.zeros(1, device="cuda")
+    ctx.train_step([_dev(sub, obj, u[:64], cr[:64])], pkg.make_opts(nc=64, nr=64, flags=pkg.PRENOM_FLAG_NO_ADAM),
+                   loss)
+    assert abs(loss.item() - want["loss"]) <= FWD_TOL * abs(want["loss"])
+    g = ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy()
+    assert rel(g, want["grad"]) <= GRAD_TOL
+    ctx.close()
