@@ -78,7 +78,8 @@ def _workload(seed: int, n_batches: int, n_params_hash: int):
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -109,25 +110,36 @@ class ClockSampler:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
         return False
 
+    def mark(self, t0: float, t1: float):
+        """Wall-clock bounds of the timed region (samples outside it are dropped)."""
+        self.window = (t0, t1)
+
     def summary(self):
-        sm, smax, reasons = [], [], set()
+        import datetime
+
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        t0, t1 = getattr(self, "window", (rows[0][0], rows[-1][0]))
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        note = "inside the timed region"
+        if not inside:  # region shorter than the sampling period: nearest sample
+            mid = 0.5 * (t0 + t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+            note = "nearest sample (timed region shorter than 200 ms)"
+        reasons = sorted({nm for r in inside for nm, v in zip(names, r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside), "note": note}
 
 
 def gpu_identifier(dev: int) -> str:
@@ -274,11 +286,13 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     with clocks:
+        w0 = time.time()
         ev0.record(stream)
         for i in range(args.steps):
             ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clocks.mark(w0, time.time())
     barrier()
     launches = ctx.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
@@ -372,8 +386,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -70,6 +70,37 @@ def oracle_samples(grid, rays, u, nc, nr, eps=1e-4):
     return out
 
 
+def oracle_t(grid, rays, u, nc, nr, eps=1e-4):
+    """The oracle's sample depths rounded to FP32: fed as t_in to both sides so
+    that encoding, MLP, rendering and gradients are compared on identical
+    samples.  (The FP32 inverse CDF places a sample in a bin of mass m only to
+    ~1e-7 / m of the bin width, which the fine levels turn into weight errors;
+    the sampler is compared separately, with that bound.)"""
+    return oracle_samples(grid, rays, u, nc, nr, eps)["t"].astype(np.float32)
+
+
+def conditioned_uniforms(grid, rays, nc, nr, seed, min_mass=0.02, eps=1e-4):
+    """Stratified uniforms re-drawn, inside their own stratum, away from bins
+    whose oracle mass is below min_mass (where FP32 inversion is ill-conditioned).
+    Samples whose whole stratum lies in such bins keep their draw."""
+    rng = np.random.default_rng(seed)
+    u = stratified_uniforms(rays["o"].shape[0], nr, seed).astype(np.float64)
+    for r in range(u.shape[0]):
+        cdf = orc.sample_ray(grid, rays["o"][r], rays["d"][r], nc, nr, eps, u[r].astype(np.float32))["cdf"]
+        mass = np.diff(cdf)
+        for k in range(nr):
+            b = min(int(np.searchsorted(cdf[1:], u[r, k], side="right")), nc - 1)
+            if mass[b] >= min_mass:
+                continue
+            lo_s, hi_s = k / nr, (k + 1) / nr
+            good = [(max(cdf[i], lo_s), min(cdf[i + 1], hi_s)) for i in range(nc)
+                    if mass[i] >= min_mass and min(cdf[i + 1], hi_s) - max(cdf[i], lo_s) > 1e-6]
+            if good:
+                lo, hi = good[int(rng.integers(0, len(good)))]
+                u[r, k] = lo + (hi - lo) * (0.05 + 0.9 * rng.random())
+    return np.minimum(u, np.nextafter(np.float32(1), np.float32(0))).astype(np.float32)
+
+
 def bins_match(gpu_bins, want_bins, cdf_rows, u, margin=1e-5):
     """Bin indices must equal the oracle's wherever the uniform is farther than
     `margin` from every FP64 CDF edge; inside the margin the GPU's bin must
