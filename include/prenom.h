@@ -212,6 +212,46 @@ PRENOM_API int prenom_sync(prenom_ctx *ctx);
 PRENOM_API int prenom_enable_timing(prenom_ctx *ctx, int32_t enable);
 PRENOM_API int prenom_kernel_time(prenom_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
 
+/* ------------------------------------------------- allocation-free step
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they train: a mapping front end
+ * that reserved the GPU's whole memory budget for its own buffers up front, a
+ * host framework whose caching allocator owns the device pool, or a real-time
+ * thread that cannot afford cudaMalloc's implicit device synchronisation.
+ *
+ * prenom_train_step_noalloc() runs the same training step as
+ * prenom_train_step() for one object whose state the caller owns, and calls
+ * no cudaMalloc, cudaFree or other allocating routine.  Its only extra device
+ * memory is a gradient accumulator of PRENOM_NOALLOC_MAX_PARAMS floats
+ * (16 MiB) compiled into the library as a static device array, which every
+ * GPU that loads the library holds until the process exits.
+ *   arch       architecture (same rules as prenom_create_object); objects with
+ *              more than PRENOM_NOALLOC_MAX_PARAMS parameters are rejected
+ *              with PRENOM_ERR_INVALID_ARG
+ *   theta      device, param_count floats, updated in place (layout above)
+ *   adam_m, adam_v  device, param_count floats each, updated in place (zero
+ *              before the first step)
+ *   step       Adam steps already taken (this call performs step + 1)
+ *   grid, res  prior density grid as in prenom_set_prior_grid (device; may be
+ *              NULL when the batch gives t_in)
+ *   batch      rays as for prenom_train_step (batch->obj only keys the Philox
+ *              draws when uniforms or c_rand are NULL)
+ *   loss_dev   device float receiving the batch's loss, or NULL
+ *   cuda_stream, seed  stream of all work; Philox seed
+ * Errors are reported by the return code; the message is available from
+ * prenom_last_error(NULL).
+ * The first call on each device looks up the array's device address (set-up
+ * done once per device, with that device current): make that first call
+ * before any stream capture.  Every call on a device shares the array and
+ * clears the part it uses before use, so calls whose work overlaps on the GPU
+ * (for example on two streams at once) race and must be avoided. */
+#define PRENOM_NOALLOC_MAX_PARAMS (1 << 22)
+
+PRENOM_API int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, float *adam_m, float *adam_v,
+                                         int32_t step, const float *grid, int32_t res,
+                                         const prenom_ray_batch *batch, const prenom_train_opts *opts,
+                                         float *loss_dev, void *cuda_stream, uint64_t seed);
+
 /* Total kernel launches made by the library on this context. */
 PRENOM_API int prenom_launch_count(prenom_ctx *ctx, int64_t *launches);
 

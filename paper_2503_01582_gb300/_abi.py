@@ -86,7 +86,12 @@ _SIGS = {
     "prenom_enable_timing": (C.c_int, [_CTX, C.c_int32]),
     "prenom_kernel_time": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "prenom_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
+    "prenom_train_step_noalloc": (C.c_int, [C.POINTER(prenom_arch), _P, _P, _P, C.c_int32, _P, C.c_int32,
+                                            C.POINTER(prenom_ray_batch), C.POINTER(prenom_train_opts), _P, _P,
+                                            C.c_uint64]),
 }
+
+PRENOM_NOALLOC_MAX_PARAMS = 1 << 22
 
 _lib = None
 
@@ -224,3 +229,12 @@ def prenom_launch_count(ctx) -> int:
     n = C.c_int64()
     check(lib().prenom_launch_count(ctx, C.byref(n)), ctx)
     return n.value
+
+
+def prenom_train_step_noalloc(arch: prenom_arch, theta_ptr: int, m_ptr: int, v_ptr: int, step: int, grid_ptr: int,
+                              res: int, batch: prenom_ray_batch, opts: prenom_train_opts, loss_ptr: int = 0,
+                              stream: int = 0, seed: int = 0):
+    """Training step on caller-owned theta / Adam moments that allocates no device memory."""
+    check(lib().prenom_train_step_noalloc(C.byref(arch), _P(theta_ptr), _P(m_ptr), _P(v_ptr), step,
+                                          _P(grid_ptr or None), res, C.byref(batch), C.byref(opts),
+                                          _P(loss_ptr or None), _P(stream or None), seed))

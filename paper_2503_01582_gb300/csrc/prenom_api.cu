@@ -309,6 +309,35 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
 
 }  // namespace
 
+namespace prenom {
+
+// Field descriptor for parameters held in caller-owned buffers (used by the
+// allocation-free training step).  Validates the architecture with the same
+// rules as prenom_create_object; failures set the context-free last error.
+int describe_caller_field(const prenom_arch *arch, const float *theta, float *grad, const float *grid, int32_t R,
+                          ObjDesc *od, int64_t *n_params)
+{
+    const int rc = check_arch(nullptr, arch);
+    if (rc)
+        return rc;
+    Object o;
+    o.arch = *arch;
+    level_geometry(*arch, o);
+    o.theta = const_cast<float *>(theta);
+    o.grid = const_cast<float *>(grid);
+    o.R = R;
+    *od = make_objdesc(o, grad);
+    *n_params = o.n;
+    return PRENOM_OK;
+}
+
+int set_context_free_error(int code, const char *msg)
+{
+    return fail(nullptr, code, "%s", msg);
+}
+
+}  // namespace prenom
+
 extern "C" {
 
 int prenom_create(prenom_ctx **out, void *cuda_stream, uint64_t seed)
