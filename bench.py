@@ -34,6 +34,10 @@ WORKLOAD = ("single object at full size: hash grid L=16 F=2 T=2^19 res 16..2048,
             "density, sigmoid colour), 4096 rays x 64 samples/step from the prior sampler (Nc=64) over a 64^3 "
             "prior grid, random CSG scene, 480x640 views, depth noise 2 mm, FP32 per-object form")
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
+DTYPE = {"fp32": "f32", "fp16": "f16 MLP / f32 accumulate", "bf16": "bf16 MLP / f32 accumulate"}
+FORM = {"fp32": "fp32 per-object", "fp16": "mixed precision (FP16 tensor-core MLP, FP32 master weights)",
+        "bf16": "mixed precision (BF16 tensor-core MLP, FP32 master weights)"}
 
 
 def mlp_macs(a):
@@ -251,7 +255,7 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()
     ctx = pkg.Context(seed=rank, stream=stream)
-    arch = pkg.make_arch(**{k: v for k, v in ARCH.items()})
+    arch = pkg.make_arch(**{k: v for k, v in ARCH.items()}, precision=PRECISION[args.precision])
     probe = ctx.create_object(arch)
     n_params = ctx.param_count(probe)
     ctx.destroy_object(probe)
@@ -366,9 +370,9 @@ def run_ours(args):
                               f"({r['t_adam']:.2f} s), FP64, 1 host thread, extrapolated to the 4096-ray step")}
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
                 "config": {"workload": WORKLOAD, "rays_per_step": N_RAYS, "samples_per_ray": NR, "probes": NC,
-                           "params": n_params, "form": "fp32 per-object",
+                           "params": n_params, "form": FORM[args.precision],
                            "parallelism": f"{world} independent objects (one per GPU)" if world > 1 else "1 object",
                            "l2": "working set > L2: theta, grad, Adam m and v (4 x %.0f MB) stream every step"
                                  % (n_params * 4 / 1e6)},
@@ -390,6 +394,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=list(PRECISION))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

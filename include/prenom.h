@@ -55,6 +55,13 @@ extern "C" {
 #define PRENOM_ERR_NONFINITE (-5)      /* a checked loss was NaN or infinite */
 
 #define PRENOM_PRECISION_FP32 0 /* FP32 features, MLP and accumulation */
+/* Mixed precision: the MLP runs on the tensor cores with 16-bit operands and
+ * FP32 accumulation; parameters, Adam state, hash features, sampling,
+ * transmittance and the loss stay FP32.  FP16 uses a dynamic loss scale
+ * (initial 2^15, halved and the step dropped on an overflow, doubled after 1000
+ * clean steps); BF16 uses a scale of 1. */
+#define PRENOM_PRECISION_FP16 1
+#define PRENOM_PRECISION_BF16 2
 
 /* prenom_train_opts.flags */
 #define PRENOM_FLAG_NO_ADAM 1u      /* accumulate gradients, skip Adam (step count unchanged) */
@@ -80,7 +87,7 @@ typedef struct prenom_ctx prenom_ctx; /* opaque; owns all device state */
  * lists hash-grid and MLP hyper-parameters and lambda_d, lambda_sigma).
  * Limits of this build: F = 2; L in {4, 8, 16}; width in {16, 32, 64};
  * 1 <= hidden <= 3; 8 <= log2T <= 24; 2 <= n_min <= n_max <= 2^20;
- * precision = PRENOM_PRECISION_FP32. */
+ * precision = PRENOM_PRECISION_FP32, _FP16 or _BF16. */
 typedef struct {
     int32_t L, F, log2T, n_min, n_max; /* levels, features/level, log2 table size, resolutions */
     int32_t width, hidden;             /* MLP hidden width W and hidden layer count H */
@@ -91,7 +98,9 @@ typedef struct {
 /* Step options.  lr, beta1, beta2, eps: Adam (§III-B).  nc, nr: probes and
  * samples per ray (§III-B, N_c and N_r; 4 <= nr <= 128, 1 <= nc <= 256).
  * escape_eps: the escape threshold epsilon of §III-B (the paper uses 1e-4).
- * loss_scale_init: reserved (must be 0 or 1 in FP32).  flags: PRENOM_FLAG_*. */
+ * loss_scale_init: for a mixed-precision object, when > 0, the loss scale it
+ * starts from at its first step (0 = the default of its precision; ignored
+ * in FP32).  flags: PRENOM_FLAG_*. */
 typedef struct {
     float lr, beta1, beta2, eps;
     int32_t nc, nr;
@@ -251,6 +260,11 @@ PRENOM_API int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, 
                                          int32_t step, const float *grid, int32_t res,
                                          const prenom_ray_batch *batch, const prenom_train_opts *opts,
                                          float *loss_dev, void *cuda_stream, uint64_t seed);
+
+/* Loss-scaling state of a mixed-precision object (blocking read): the current
+ * scale and the number of steps dropped because a scaled 16-bit gradient
+ * overflowed.  FP32 objects report scale 1 and 0 dropped steps. */
+PRENOM_API int prenom_get_loss_scale(prenom_ctx *ctx, int32_t obj, float *scale, int32_t *dropped_steps);
 
 /* Total kernel launches made by the library on this context. */
 PRENOM_API int prenom_launch_count(prenom_ctx *ctx, int64_t *launches);

@@ -23,6 +23,8 @@ from ._abi import (  # noqa: F401
     PRENOM_KERNEL_RENDER_BWD,
     PRENOM_KERNEL_TRAIN,
     PRENOM_N_KERNELS,
+    PRENOM_PRECISION_BF16,
+    PRENOM_PRECISION_FP16,
     PRENOM_PRECISION_FP32,
     PRENOM_STATE_ADAM_M,
     PRENOM_STATE_ADAM_V,
@@ -182,6 +184,10 @@ class Context:
 
     def set_step(self, obj: int, step: int):
         _abi.prenom_set_step(self._ctx, obj, step)
+
+    def loss_scale(self, obj: int):
+        """(current loss scale, steps dropped after a 16-bit overflow)."""
+        return _abi.prenom_get_loss_scale(self._ctx, obj)
 
     def zero_grads(self, obj: int):
         _abi.prenom_zero_grads(self._ctx, obj)

@@ -20,6 +20,8 @@ PRENOM_ERR_DEVICE_TIMEOUT = -4
 PRENOM_ERR_NONFINITE = -5
 
 PRENOM_PRECISION_FP32 = 0
+PRENOM_PRECISION_FP16 = 1
+PRENOM_PRECISION_BF16 = 2
 PRENOM_FLAG_NO_ADAM = 1
 PRENOM_FLAG_CHECK_FINITE = 2
 
@@ -86,6 +88,7 @@ _SIGS = {
     "prenom_enable_timing": (C.c_int, [_CTX, C.c_int32]),
     "prenom_kernel_time": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "prenom_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
+    "prenom_get_loss_scale": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
     "prenom_train_step_noalloc": (C.c_int, [C.POINTER(prenom_arch), _P, _P, _P, C.c_int32, _P, C.c_int32,
                                             C.POINTER(prenom_ray_batch), C.POINTER(prenom_train_opts), _P, _P,
                                             C.c_uint64]),
@@ -238,3 +241,11 @@ def prenom_train_step_noalloc(arch: prenom_arch, theta_ptr: int, m_ptr: int, v_p
     check(lib().prenom_train_step_noalloc(C.byref(arch), _P(theta_ptr), _P(m_ptr), _P(v_ptr), step,
                                           _P(grid_ptr or None), res, C.byref(batch), C.byref(opts),
                                           _P(loss_ptr or None), _P(stream or None), seed))
+
+
+def prenom_get_loss_scale(ctx, obj: int):
+    """(current loss scale, steps dropped after a 16-bit overflow) of an object."""
+    s = C.c_float()
+    n = C.c_int32()
+    check(lib().prenom_get_loss_scale(ctx, obj, C.byref(s), C.byref(n)), ctx)
+    return s.value, n.value

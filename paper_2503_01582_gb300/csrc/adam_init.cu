@@ -1,6 +1,6 @@
 // Adam update over every parameter of a step's objects, random initialisation,
 // and the host-side dispatch of the fused kernels.
-#include "fused_fp32.cuh"
+#include "fused_tc.cuh"
 
 namespace prenom {
 
@@ -33,6 +33,11 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
         const AdamSeg &sg = a.seg[lo];
         const int64_t base = (c - a.chunk_start[lo]) * kAdamChunk;
         const int64_t end = min(base + (int64_t)kAdamChunk, sg.n);
+        if (sg.skip && *sg.skip) {  // a 16-bit gradient overflowed: drop the step, clear the gradients
+            for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
+                sg.grad[i] = 0.f;
+            continue;
+        }
         for (int64_t i = base + threadIdx.x * 4; i < end; i += blockDim.x * 4) {
             if (i + 4 <= end) {
                 float4 th = *reinterpret_cast<float4 *>(sg.theta + i);
@@ -115,6 +120,56 @@ cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_
     a.obj = obj;
     init_kernel<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------ loss scaling
+// Dynamic loss scale of a mixed-precision object, run after its Adam step:
+// an overflow halves the scale (the step was dropped), 1000 clean steps in a
+// row double it (capped at 2^24).
+__global__ void loss_scale_update_kernel(LossScaleState *s)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    if (s->overflow) {
+        s->scale = fmaxf(s->scale * 0.5f, 1.f);
+        s->good_steps = 0;
+        s->skipped += 1;
+        s->overflow = 0;
+    } else if (++s->good_steps >= 1000) {
+        s->scale = fminf(s->scale * 2.f, 16777216.f);
+        s->good_steps = 0;
+    }
+}
+
+cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st)
+{
+    loss_scale_update_kernel<<<1, 32, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+size_t fused_tc_smem(int W, int IN, int H)
+{
+    switch (W * 100 + IN) {
+    case 1608: return TcLayout<16, 8>::bytes(H);
+    case 1616: return TcLayout<16, 16>::bytes(H);
+    case 1632: return TcLayout<16, 32>::bytes(H);
+    case 3208: return TcLayout<32, 8>::bytes(H);
+    case 3216: return TcLayout<32, 16>::bytes(H);
+    case 3232: return TcLayout<32, 32>::bytes(H);
+    case 6408: return TcLayout<64, 8>::bytes(H);
+    case 6416: return TcLayout<64, 16>::bytes(H);
+    case 6432: return TcLayout<64, 32>::bytes(H);
+    default: return 0;
+    }
+}
+
+cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precision, int grid, cudaStream_t st)
+{
+    if (precision == 1)
+        return launch_fused_tc_fp16(od, bd, grid, st);
+    if (precision == 2)
+        return launch_fused_tc_bf16(od, bd, grid, st);
+    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------- fused dispatch

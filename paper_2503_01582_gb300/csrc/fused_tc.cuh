@@ -1,0 +1,607 @@
+// Mixed-precision fused training step (FP16 or BF16 MLP on the sm_100-family
+// tensor cores, FP32 accumulation in tensor memory, FP32 master weights).
+//
+// Same tile walk as the FP32 kernel (sampling, encoding, compositing and the
+// hash scatter are the FP32 code), but every MLP contraction is a tcgen05.mma
+// issued by one thread:
+//   forward   H_l   = relu(A_l W_l^T)       M = 128 samples, N = W, K = in
+//   output    O     = H_last W_out^T         N = 16 (4 outputs, zero-padded)
+//   backward  dH_l  = (dH_{l+1} W_{l+1})     masked by H_l > 0
+//             dW_l += dH_l^T A_l             M = 64 (W zero-padded), K = 128 samples
+//             dX    = dH_0 W_0               read by the scatter threads from TMEM
+// Every 16-bit operand lives once in shared memory in the no-swizzle
+// interleaved layout (8x8 core matrices of 128 contiguous bytes) and is used
+// K-major or MN-major by the descriptors, so no transposed copies exist.  The
+// weight gradients accumulate in tensor memory for the CTA's whole life and are
+// flushed with one atomic pass at the end; dW_out (4 x W) is summed on the
+// CUDA cores.  The backward gradients are multiplied by a loss scale before the
+// 16-bit cast (FP16 dynamic range) and divided by it in FP32 on the way out.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fused_fp32.cuh"
+
+namespace prenom {
+
+template <bool BF16>
+struct Half;
+
+template <>
+struct Half<true> {
+    static constexpr uint32_t fmt = 1;  // instruction-descriptor operand format
+    static __device__ __forceinline__ uint16_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+    static __device__ __forceinline__ float value(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+    static __device__ __forceinline__ bool finite(uint16_t b) { return (b & 0x7F80u) != 0x7F80u; }
+};
+
+template <>
+struct Half<false> {
+    static constexpr uint32_t fmt = 0;
+    static __device__ __forceinline__ uint16_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    static __device__ __forceinline__ float value(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+    static __device__ __forceinline__ bool finite(uint16_t b) { return (b & 0x7C00u) != 0x7C00u; }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (r, c) of a rows x cols 16-bit matrix in the
+// interleaved layout: core matrix (r/8, c/8) at (r/8)*(cols/8)*128 + (c/8)*128,
+// row r%8 of a core at 16 B, element c%8 at 2 B.
+__device__ __forceinline__ int il_off(int r, int c, int cols)
+{
+    return ((r >> 3) * (cols >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2;
+}
+
+// An MMA operand: a stored matrix viewed K-major (its rows are M or N) or
+// MN-major (its rows are K).  kstr / mnstr: byte distance of adjacent core
+// matrices along K and along M (or N).
+struct Operand {
+    uint32_t addr, kstr, mnstr, mn_major;
+};
+
+__device__ __forceinline__ Operand kmajor(const void *p, int cols)
+{
+    return Operand{smem_addr(p), 128u, (uint32_t)(cols >> 3) * 128u, 0u};
+}
+
+__device__ __forceinline__ Operand mnmajor(const void *p, int cols)
+{
+    return Operand{smem_addr(p), (uint32_t)(cols >> 3) * 128u, 128u, 1u};
+}
+
+// Shared-memory matrix descriptor: start, leading (K-direction) and stride
+// (M/N-direction) byte offsets in 16-byte units, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, 16-bit A and B of the
+// given format, major-ness of A and B, N >> 3 and M >> 4.
+__device__ __forceinline__ uint32_t mma_idesc(uint32_t fmt, int M, int N, uint32_t a_mn, uint32_t b_mn)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (a_mn << 15) | (b_mn << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+// D (+)= A * B^T over K (multiple of 16), issued by the calling thread.
+__device__ __forceinline__ void mma_gemm(uint32_t d_tmem, const Operand &a, const Operand &b, int K, uint32_t idesc,
+                                         bool accumulate)
+{
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t ad = smem_desc(a.addr + ks * 2 * a.kstr, a.kstr, a.mnstr);
+        const uint64_t bd = smem_desc(b.addr + ks * 2 * b.kstr, b.kstr, b.mnstr);
+        const uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_addr(mbar)));
+}
+
+// Bounded wait for the mbarrier phase; false (and status set) when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int32_t *status)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(mbar)), "r"(parity));
+    }
+    if (!done && status)
+        atomicExch(status, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return __syncthreads_and(done != 0) != 0;  // the same answer in every thread of the block
+}
+
+__device__ __forceinline__ void tc_sync()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kTcTile = 128;       // samples per tile = MMA M
+constexpr int kTcCols = 256;       // TMEM columns allocated per CTA
+constexpr int kDaCols = 64;        // columns of the dH buffer (dW MMAs use M = 64)
+
+template <int W, int IN>
+struct TcLayout {
+    static constexpr int INP = IN < 16 ? 16 : IN;  // encoding width padded to the MMA N/K quantum
+    static constexpr int SP = kTcTile + 4;
+    // byte sizes of the 16-bit matrices
+    static constexpr int w0 = W * INP * 2, wh = W * W * 2, wo = 16 * W * 2;
+    static constexpr int xa = kTcTile * INP * 2, ha = kTcTile * W * 2, da = kTcTile * kDaCols * 2,
+                         doa = kTcTile * 16 * 2;
+    static __host__ __device__ size_t bytes(int H)
+    {
+        size_t b = (size_t)w0 + (size_t)(H - 1) * wh + wo + xa + (size_t)H * ha + da + doa;
+        b += sizeof(float) * (8 * SP + SP + (size_t)(kTcTile / kMinNr) * kRayStride + 8 * (size_t)(kMaxNc + 1));
+        return b + 64;  // TMEM slot and mbarrier
+    }
+};
+
+// TMEM column of each accumulator region: R0 (64 columns) holds the current
+// forward layer, the output layer, then the current backward product; the dW
+// accumulators follow (M = 64 layout: row m in lane 32*(m/16) + m%16).
+template <int W, int IN>
+__device__ __forceinline__ uint32_t dw_col(int layer)
+{
+    constexpr int INP = TcLayout<W, IN>::INP;
+    return layer == 0 ? 64u : (uint32_t)(64 + INP + (layer - 1) * W);
+}
+
+template <int W, int IN, bool BF16>
+__global__ void __launch_bounds__(kThreads, 2) fused_tc_kernel(const ObjDesc od, const BatchDesc bd)
+{
+    using L = TcLayout<W, IN>;
+    using Hf = Half<BF16>;
+    constexpr int INP = L::INP;
+    constexpr int SP = L::SP;
+    constexpr int MAXR = kTcTile / kMinNr;
+    constexpr int NL = IN / 2;  // levels (F = 2)
+    extern __shared__ __align__(128) unsigned char smc[];
+    const int H = od.H;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int quad = warp & 3, half = warp >> 2;
+    const int srow = 32 * quad + lane;  // TMEM lane = sample row of this thread
+
+    unsigned char *Wt0 = smc;
+    unsigned char *WtH = Wt0 + L::w0;                 // layers 1..H-1
+    unsigned char *WtO = WtH + (H - 1) * L::wh;
+    unsigned char *XA = WtO + L::wo;
+    unsigned char *HA = XA + L::xa;                   // H buffers of ha bytes
+    unsigned char *DA = HA + H * L::ha;
+    unsigned char *DOA = DA + L::da;
+    float *OT = reinterpret_cast<float *>(DOA + L::doa);  // [4][SP] raw outputs
+    float *dOT = OT + 4 * SP;                         // [4][SP] dL/d(raw outputs), unscaled
+    float *ts = dOT + 4 * SP;
+    float *rayf = ts + SP;
+    float *cdfs = rayf + MAXR * kRayStride;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cdfs + 8 * (kMaxNc + 1));
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(tmem_slot + 2);
+
+    const bool train = bd.mode != kRender;
+    const float scale = (train && bd.loss_scale) ? *bd.loss_scale : 1.f;
+    const float inv_scale = 1.f / scale;
+
+    // ---- 16-bit weights into the interleaved layout; padding stays zero
+    {
+        const float *th = od.theta + od.mlp_off;
+        // buffers with padding that is never written again: W_0 (columns IN..INP),
+        // W_out (rows 4..15), DA (columns W..63), dO (columns 4..15)
+        for (int i = tid; i < L::w0 / 4; i += kThreads)
+            reinterpret_cast<uint32_t *>(Wt0)[i] = 0u;
+        for (int i = tid; i < L::wo / 4; i += kThreads)
+            reinterpret_cast<uint32_t *>(WtO)[i] = 0u;
+        for (int i = tid; i < L::da / 4; i += kThreads)
+            reinterpret_cast<uint32_t *>(DA)[i] = 0u;
+        for (int i = tid; i < L::doa / 4; i += kThreads)
+            reinterpret_cast<uint32_t *>(DOA)[i] = 0u;
+        __syncthreads();
+        for (int i = tid; i < W * IN; i += kThreads) {
+            const int o = i / IN, c = i % IN;
+            *reinterpret_cast<uint16_t *>(Wt0 + il_off(o, c, INP)) = Hf::bits(th[i]);
+        }
+        for (int l = 1; l < H; ++l)
+            for (int i = tid; i < W * W; i += kThreads) {
+                const int o = i / W, c = i % W;
+                *reinterpret_cast<uint16_t *>(WtH + (l - 1) * L::wh + il_off(o, c, W)) =
+                    Hf::bits(th[IN * W + (l - 1) * W * W + i]);
+            }
+        for (int i = tid; i < 4 * W; i += kThreads) {
+            const int o = i / W, c = i % W;
+            *reinterpret_cast<uint16_t *>(WtO + il_off(o, c, W)) = Hf::bits(th[IN * W + (H - 1) * W * W + i]);
+        }
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quad) << 16);
+
+    const uint32_t id_fwd = mma_idesc(Hf::fmt, 128, W, 0, 0);
+    const uint32_t id_out = mma_idesc(Hf::fmt, 128, 16, 0, 0);
+    const uint32_t id_dh = mma_idesc(Hf::fmt, 128, W, 0, 1);
+    const uint32_t id_dx = mma_idesc(Hf::fmt, 128, INP, 0, 1);
+    const uint32_t id_dw = mma_idesc(Hf::fmt, 64, W, 1, 1);
+    const uint32_t id_dw0 = mma_idesc(Hf::fmt, 64, INP, 1, 1);
+
+    uint32_t parity = 0;
+    bool ok = true;
+    bool first_dw = true;
+    const int off_out = IN * W + (H - 1) * W * W;
+    float dwo_acc = 0.f;  // dW_out entry (o, i) = (tid / W, tid % W) for tid < 4W
+    float loss_acc = 0.f;
+    const int nr = bd.nr, NR = bd.rays_per_tile;
+
+    for (int tile = blockIdx.x; tile < bd.n_tiles && ok; tile += gridDim.x) {
+        const int ray0 = tile * NR;
+        const int nrt = min(NR, bd.n_rays - ray0);
+        const int ns = nrt * nr;
+        // ---- ray data and sampling (FP32, shared with the FP32 kernel)
+        for (int i = tid; i < nrt; i += kThreads) {
+            const int g = ray0 + i;
+            float *rf = rayf + i * kRayStride;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                rf[RF_O + a] = bd.o[(size_t)g * 3 + a];
+                rf[RF_D + a] = bd.d[(size_t)g * 3 + a];
+            }
+            if (bd.mode == kTrain) {
+                const bool obj = bd.is_obj[g] != 0;
+                rf[RF_OBJ] = obj ? 1.f : 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    rf[RF_RGB + a] = obj ? bd.rgb[(size_t)g * 3 + a] : 0.f;
+                rf[RF_DEPTH] = obj ? bd.depth[g] : 0.f;
+                if (!obj) {
+                    if (bd.c_rand) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            rf[RF_CR + a] = bd.c_rand[(size_t)g * 3 + a];
+                    } else {
+                        const float3 c = philox_colour(bd.seed, bd.step, bd.obj_id, (uint32_t)g);
+                        rf[RF_CR] = c.x;
+                        rf[RF_CR + 1] = c.y;
+                        rf[RF_CR + 2] = c.z;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int r = warp; r < nrt; r += kThreads / 32)
+            sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
+        __syncthreads();
+        // ---- encoding -> XA (16-bit, interleaved [128][INP])
+        {
+            const int s = tid % kTcTile, part = tid / kTcTile;
+            if (s >= ns) {
+                for (int l = part; l < INP / 2; l += 2)
+                    *reinterpret_cast<uint32_t *>(XA + il_off(s, 2 * l, INP)) = 0u;
+                if (part == 0)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        dOT[c * SP + s] = 0.f;
+            } else {
+                const int r = s / nr;
+                const float *rf = rayf + r * kRayStride;
+                const float t = ts[s];
+                float ph[3], pl[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    pos_two_float(rf[RF_O + a], t, rf[RF_D + a], ph[a], pl[a]);
+                const float2 *tab = reinterpret_cast<const float2 *>(od.theta);
+#pragma unroll 2
+                for (int l = part; l < NL; l += 2) {
+                    const LevelDesc lv = od.lv[l];
+                    Corners cs;
+                    level_corners(lv, od.tmask, ph, pl, cs);
+                    float2 f[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        f[c] = __ldg(tab + lv.offset + cs.idx[c]);
+                    float e0 = 0.f, e1 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        e0 = fmaf(cs.wt[c], f[c].x, e0);
+                        e1 = fmaf(cs.wt[c], f[c].y, e1);
+                    }
+                    *reinterpret_cast<uint32_t *>(XA + il_off(s, 2 * l, INP)) =
+                        (uint32_t)Hf::bits(e0) | ((uint32_t)Hf::bits(e1) << 16);
+                }
+                for (int l = NL + part; l < INP / 2; l += 2)  // zero padding of a narrow encoding
+                    *reinterpret_cast<uint32_t *>(XA + il_off(s, 2 * l, INP)) = 0u;
+            }
+        }
+        tc_sync();
+        // ---- MLP forward on the tensor cores
+        for (int l = 0; l < H && ok; ++l) {
+            if (tid == 0) {
+                const Operand a = l == 0 ? kmajor(XA, INP) : kmajor(HA + (l - 1) * L::ha, W);
+                const Operand b = l == 0 ? kmajor(Wt0, INP) : kmajor(WtH + (l - 1) * L::wh, W);
+                mma_gemm(tmem, a, b, l == 0 ? INP : W, id_fwd, false);
+                mma_commit(mbar);
+            }
+            ok = mbar_wait(mbar, parity, bd.status);
+            parity ^= 1u;
+            // epilogue: relu -> 16-bit -> HA[l]; warp half h takes columns [h W/2, (h+1) W/2)
+#pragma unroll
+            for (int c0 = 0; c0 < W / 2; c0 += 8) {
+                const int col = half * (W / 2) + c0;
+                float v[8];
+                tmem_ld8(lane_base + col, v);
+                uint4 pk;
+                pk.x = (uint32_t)Hf::bits(fmaxf(v[0], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[1], 0.f)) << 16);
+                pk.y = (uint32_t)Hf::bits(fmaxf(v[2], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[3], 0.f)) << 16);
+                pk.z = (uint32_t)Hf::bits(fmaxf(v[4], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[5], 0.f)) << 16);
+                pk.w = (uint32_t)Hf::bits(fmaxf(v[6], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[7], 0.f)) << 16);
+                *reinterpret_cast<uint4 *>(HA + l * L::ha + il_off(srow, col, W)) = pk;
+            }
+            tc_sync();
+        }
+        if (!ok)
+            break;
+        if (tid == 0) {
+            mma_gemm(tmem, kmajor(HA + (H - 1) * L::ha, W), kmajor(WtO, W), W, id_out, false);
+            mma_commit(mbar);
+        }
+        ok = mbar_wait(mbar, parity, bd.status);
+        parity ^= 1u;
+        if (half == 0) {
+            float v[4];
+            tmem_ld4(lane_base, v);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                OT[c * SP + srow] = v[c];
+        }
+        tc_sync();
+        // ---- compositing, loss and its adjoint (FP32)
+        for (int r = warp; r < nrt; r += kThreads / 32) {
+            const float lr = composite_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane);
+            if (lane == 0)
+                loss_acc += lr;
+        }
+        __syncthreads();
+        if (!train)
+            continue;
+        // ---- scaled 16-bit dL/dO, and dW_out on the CUDA cores
+        if (tid < kTcTile) {
+            uint32_t lo = (uint32_t)Hf::bits(dOT[tid] * scale) | ((uint32_t)Hf::bits(dOT[SP + tid] * scale) << 16);
+            uint32_t hi = (uint32_t)Hf::bits(dOT[2 * SP + tid] * scale) |
+                          ((uint32_t)Hf::bits(dOT[3 * SP + tid] * scale) << 16);
+            *reinterpret_cast<uint2 *>(DOA + il_off(tid, 0, 16)) = make_uint2(lo, hi);
+            if (!(Hf::finite(lo & 0xFFFFu) && Hf::finite(lo >> 16) && Hf::finite(hi & 0xFFFFu) &&
+                  Hf::finite(hi >> 16)) && bd.overflow)
+                atomicExch(bd.overflow, 1);
+        }
+        if (tid < 4 * W) {
+            const int o = tid / W, i = tid % W;
+            const unsigned char *hl = HA + (H - 1) * L::ha;
+            float acc = 0.f;
+            for (int s = 0; s < kTcTile; ++s)
+                acc = fmaf(dOT[o * SP + s], Hf::value(*reinterpret_cast<const uint16_t *>(hl + il_off(s, i, W))),
+                           acc);
+            dwo_acc += acc;
+        }
+        tc_sync();
+        // ---- backward through the hidden layers
+        for (int l = H - 1; l >= 0 && ok; --l) {
+            // dH_l = dOut_{l+1} W_{l+1}: for l = H-1 from the output layer
+            if (tid == 0) {
+                if (l == H - 1)
+                    mma_gemm(tmem, kmajor(DOA, 16), mnmajor(WtO, W), 16, id_dh, false);
+                else
+                    mma_gemm(tmem, kmajor(DA, kDaCols), mnmajor(WtH + l * L::wh, W), W, id_dh, false);
+                mma_commit(mbar);
+            }
+            ok = mbar_wait(mbar, parity, bd.status);
+            parity ^= 1u;
+            // epilogue: mask by H_l > 0 -> 16-bit -> DA (columns [0, W))
+            const unsigned char *hl = HA + l * L::ha;
+#pragma unroll
+            for (int c0 = 0; c0 < W / 2; c0 += 8) {
+                const int col = half * (W / 2) + c0;
+                float v[8];
+                tmem_ld8(lane_base + col, v);
+                const uint4 hv = *reinterpret_cast<const uint4 *>(hl + il_off(srow, col, W));
+                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                uint32_t pk[4];
+                bool fin = true;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint16_t h0 = (uint16_t)(hw[j] & 0xFFFFu), h1 = (uint16_t)(hw[j] >> 16);
+                    const uint16_t b0 = Hf::bits(Hf::value(h0) > 0.f ? v[2 * j] : 0.f);
+                    const uint16_t b1 = Hf::bits(Hf::value(h1) > 0.f ? v[2 * j + 1] : 0.f);
+                    fin = fin && Hf::finite(b0) && Hf::finite(b1);
+                    pk[j] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+                }
+                if (!fin && bd.overflow)
+                    atomicExch(bd.overflow, 1);
+                *reinterpret_cast<uint4 *>(DA + il_off(srow, col, kDaCols)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            tc_sync();
+            // dW_l += dH_l^T A_l (M = 64 rows of DA, N = width of A_l, K = 128 samples)
+            if (tid == 0) {
+                if (l > 0)
+                    mma_gemm(tmem + dw_col<W, IN>(l), mnmajor(DA, kDaCols), mnmajor(HA + (l - 1) * L::ha, W),
+                             kTcTile, id_dw, !first_dw);
+                else
+                    mma_gemm(tmem + dw_col<W, IN>(0), mnmajor(DA, kDaCols), mnmajor(XA, INP), kTcTile, id_dw0,
+                             !first_dw);
+            }
+        }
+        if (!ok)
+            break;
+        // dX = dH_0 W_0 -> TMEM R0 (N = INP), then the hash scatter
+        if (tid == 0) {
+            mma_gemm(tmem, kmajor(DA, kDaCols), mnmajor(Wt0, INP), W, id_dx, false);
+            mma_commit(mbar);
+        }
+        ok = mbar_wait(mbar, parity, bd.status);
+        parity ^= 1u;
+        first_dw = false;
+        {
+            const int s = srow;
+            float g[16];
+            if constexpr (INP / 2 == 16) {
+                tmem_ld16(lane_base + half * 16, g);
+            } else {
+                float g8[8];
+                tmem_ld8(lane_base + half * (INP / 2), g8);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    g[j] = g8[j];
+            }
+            if (s < ns) {
+                const int r = s / nr;
+                const float *rf = rayf + r * kRayStride;
+                const float t = ts[s];
+                float ph[3], pl[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    pos_two_float(rf[RF_O + a], t, rf[RF_D + a], ph[a], pl[a]);
+                float2 *gtab = reinterpret_cast<float2 *>(od.grad);
+                const int l0 = half * (INP / 4);
+#pragma unroll
+                for (int j = 0; j < INP / 4; ++j) {
+                    const int l = l0 + j;
+                    if (l >= NL)
+                        break;
+                    const LevelDesc lv = od.lv[l];
+                    Corners cs;
+                    level_corners(lv, od.tmask, ph, pl, cs);
+                    const float g0 = g[2 * j] * inv_scale, g1 = g[2 * j + 1] * inv_scale;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float w = cs.wt[c];
+                        if (w != 0.f)
+                            atomicAdd(gtab + lv.offset + cs.idx[c], make_float2(w * g0, w * g1));
+                    }
+                }
+            }
+        }
+        tc_sync();
+    }
+
+    if (train && ok) {
+        if (lane == 0 && bd.mode == kTrain && loss_acc != 0.f)
+            atomicAdd(bd.loss, loss_acc);
+        float *gw = od.grad + od.mlp_off;
+        if (tid < 4 * W && dwo_acc != 0.f)
+            atomicAdd(gw + off_out + tid, dwo_acc);
+        // dW accumulators: M = 64 layout, warp quadrant q holds rows 16q .. 16q+15 in lanes 0..15
+        if (!first_dw) {
+            for (int l = 0; l < H; ++l) {
+                const int ncol = l == 0 ? INP : W;
+                const int nin = l == 0 ? IN : W;
+                float *dst = gw + (l == 0 ? 0 : IN * W + (l - 1) * W * W);
+                for (int c0 = half * 8; c0 < ncol; c0 += 16) {
+                    float v[8];
+                    tmem_ld8(lane_base + dw_col<W, IN>(l) + c0, v);
+                    const int row = 16 * quad + lane;
+                    if (lane < 16 && row < W)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (c0 + j < nin && v[j] != 0.f)
+                                atomicAdd(dst + row * nin + c0 + j, v[j] * inv_scale);
+                }
+            }
+        }
+    } else if (lane == 0 && bd.mode == kTrain && loss_acc != 0.f) {
+        atomicAdd(bd.loss, loss_acc);
+    }
+    tc_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
+template <int W, int IN, bool BF16>
+cudaError_t launch_tc_t(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
+{
+    const size_t smem = TcLayout<W, IN>::bytes(od.H);
+    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<W, IN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    fused_tc_kernel<W, IN, BF16><<<grid, kThreads, smem, st>>>(od, bd);
+    return cudaGetLastError();
+}
+
+template <bool BF16>
+cudaError_t launch_tc_prec(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
+{
+#define PRENOM_TC_CASE(Wv, INv)                                                                                       \
+    if (od.W == Wv && od.IN == INv)                                                                                   \
+        return launch_tc_t<Wv, INv, BF16>(od, bd, grid, st);
+    PRENOM_TC_CASE(16, 8)
+    PRENOM_TC_CASE(16, 16)
+    PRENOM_TC_CASE(16, 32)
+    PRENOM_TC_CASE(32, 8)
+    PRENOM_TC_CASE(32, 16)
+    PRENOM_TC_CASE(32, 32)
+    PRENOM_TC_CASE(64, 8)
+    PRENOM_TC_CASE(64, 16)
+    PRENOM_TC_CASE(64, 32)
+#undef PRENOM_TC_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace prenom

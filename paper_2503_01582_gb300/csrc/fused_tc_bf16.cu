@@ -1,0 +1,11 @@
+// Mixed-precision fused kernels with BF16 MLP operands (all widths and encoding sizes).
+#include "fused_tc.cuh"
+
+namespace prenom {
+
+cudaError_t launch_fused_tc_bf16(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
+{
+    return launch_tc_prec<true>(od, bd, grid, st);
+}
+
+}  // namespace prenom

@@ -88,6 +88,8 @@ extern "C" int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, 
     int rc = describe_caller_field(arch, theta, grad, grid, res, &od, &n);
     if (rc)
         return rc;
+    if (arch->precision != PRENOM_PRECISION_FP32)
+        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: only FP32 objects (precision %lld given)", arch->precision);
     if (n > PRENOM_NOALLOC_MAX_PARAMS)
         return err(PRENOM_ERR_INVALID_ARG,
                    "noalloc step: the object has %lld parameters; the allocation-free step holds at most %lld", n,

@@ -29,6 +29,7 @@ struct Object {
     float *grid = nullptr;
     int32_t R = 0;
     int32_t step = 0;
+    LossScaleState *lss = nullptr;  // mixed precision only
 };
 
 struct TimedEv {
@@ -46,6 +47,7 @@ struct prenom_ctx {
     std::vector<Object> objs;
     std::string err;
     float *scratch = nullptr;  // device float receiving losses nobody asked for
+    int32_t *status = nullptr; // device word set by a kernel whose bounded wait gave up
     bool timing = false;
     std::vector<TimedEv> pending;
     std::vector<cudaEvent_t> ev_free;
@@ -115,8 +117,9 @@ int check_arch(prenom_ctx *c, const prenom_arch *a)
         return fail(c, PRENOM_ERR_INVALID_ARG, "log2T = %d: must be 8..24", a->log2T);
     if (a->n_min < 2 || a->n_max < a->n_min || a->n_max > (1 << 20))
         return fail(c, PRENOM_ERR_INVALID_ARG, "resolutions %d..%d out of range", a->n_min, a->n_max);
-    if (a->precision != PRENOM_PRECISION_FP32)
-        return fail(c, PRENOM_ERR_INVALID_ARG, "precision %d is not available in this build", a->precision);
+    if (a->precision != PRENOM_PRECISION_FP32 && a->precision != PRENOM_PRECISION_FP16 &&
+        a->precision != PRENOM_PRECISION_BF16)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "precision %d: must be FP32 (0), FP16 (1) or BF16 (2)", a->precision);
     if (!(a->lambda_d >= 0.f) || !(a->lambda_sigma >= 0.f) || !isfinite(a->lambda_d) || !isfinite(a->lambda_sigma))
         return fail(c, PRENOM_ERR_INVALID_ARG, "lambda_d and lambda_sigma must be finite and >= 0");
     return PRENOM_OK;
@@ -139,8 +142,8 @@ int check_opts(prenom_ctx *c, const prenom_train_opts *op, bool need_adam)
         return fail(c, PRENOM_ERR_INVALID_ARG, "nc = %d: must be 1..%d", op->nc, kMaxNc);
     if (!(op->escape_eps >= 0.f) || !isfinite(op->escape_eps))
         return fail(c, PRENOM_ERR_INVALID_ARG, "escape_eps must be finite and >= 0");
-    if (!(op->loss_scale_init == 0.f || op->loss_scale_init == 1.f))
-        return fail(c, PRENOM_ERR_INVALID_ARG, "loss scaling is not used by the FP32 path (give 0 or 1)");
+    if (!(op->loss_scale_init >= 0.f) || !isfinite(op->loss_scale_init))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "loss_scale_init must be finite and >= 0");
     if (need_adam && !(op->flags & PRENOM_FLAG_NO_ADAM)) {
         if (!isfinite(op->lr) || !(op->beta1 >= 0.f && op->beta1 < 1.f) || !(op->beta2 >= 0.f && op->beta2 < 1.f) ||
             !(op->eps >= 0.f) || !isfinite(op->eps))
@@ -245,6 +248,11 @@ BatchDesc make_batchdesc(const prenom_ctx *c, const Object &o, const prenom_ray_
     d.seed = c->seed;
     d.step = (uint32_t)o.step;
     d.obj_id = (uint32_t)b.obj;
+    if (o.lss && mode == kTrain) {
+        d.loss_scale = &o.lss->scale;
+        d.overflow = &o.lss->overflow;
+    }
+    d.status = c->status;
     return d;
 }
 
@@ -252,6 +260,22 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
 {
     if (bd.n_rays == 0)
         return PRENOM_OK;
+    if (o.arch.precision != PRENOM_PRECISION_FP32) {
+        const size_t smem = fused_tc_smem(od.W, od.IN, od.H);
+        if (smem == 0 || smem > c->smem_optin)
+            return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
+        bd.rays_per_tile = 128 / bd.nr;
+        bd.n_tiles = (bd.n_rays + bd.rays_per_tile - 1) / bd.rays_per_tile;
+        const int per_sm = (2 * (smem + 1024) <= 228 * 1024) ? 2 : 1;  // two CTAs share an SM when they fit
+        const int grid = std::min(bd.n_tiles, c->n_sm * per_sm);
+        cudaEvent_t ev;
+        timed_begin(c, kernel_id, &ev);
+        const cudaError_t e = launch_fused_tc(od, bd, o.arch.precision, grid, c->stream);
+        timed_end(c, kernel_id, ev);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "mixed-precision kernel launch");
+        return PRENOM_OK;
+    }
     const int S = fused_fp32_pick_tile(od.W, od.IN, od.H, c->smem_optin);
     if (S == 0)
         return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
@@ -291,6 +315,7 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
             s.n = o.n;
             s.lr_c1 = (float)((double)op.lr / c1);
             s.inv_c2 = (float)(1.0 / c2);
+            s.skip = o.lss ? &o.lss->overflow : nullptr;
             a.chunk_start[i - first + 1] = a.chunk_start[i - first] + (o.n + kAdamChunk - 1) / kAdamChunk;
         }
         const int64_t chunks = a.chunk_start[a.n_segs];
@@ -303,6 +328,15 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
         timed_end(c, PRENOM_KERNEL_ADAM, ev);
         if (e != cudaSuccess)
             return cuda_fail(c, e, "Adam launch");
+        for (size_t i = first; i < last; ++i) {
+            Object &o = c->objs[objs[i]];
+            if (!o.lss)
+                continue;
+            const cudaError_t e2 = launch_loss_scale_update(o.lss, c->stream);
+            c->launches++;
+            if (e2 != cudaSuccess)
+                return cuda_fail(c, e2, "loss-scale update launch");
+        }
     }
     return PRENOM_OK;
 }
@@ -367,6 +401,10 @@ int prenom_create(prenom_ctx **out, void *cuda_stream, uint64_t seed)
     }
     if (e == cudaSuccess)
         e = cudaMalloc(&c->scratch, 64 * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&c->status, 4 * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMemset(c->status, 0, 4 * sizeof(int32_t));
     if (e != cudaSuccess) {
         const int code = (e == cudaErrorMemoryAllocation) ? PRENOM_ERR_OOM : PRENOM_ERR_CUDA;
         fail(nullptr, code, "context creation: %s", cudaGetErrorString(e));
@@ -386,7 +424,9 @@ void prenom_destroy(prenom_ctx *c)
     for (auto &o : c->objs) {
         cudaFree(o.arena);
         cudaFree(o.grid);
+        cudaFree(o.lss);
     }
+    cudaFree(c->status);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -440,10 +480,18 @@ int prenom_create_object(prenom_ctx *c, const prenom_arch *arch, const float *in
             timed_end(c, PRENOM_KERNEL_INIT, ev);
         }
     }
+    if (e == cudaSuccess && arch->precision != PRENOM_PRECISION_FP32) {
+        e = cudaMalloc(&o.lss, sizeof(LossScaleState));
+        if (e == cudaSuccess) {
+            const LossScaleState init{arch->precision == PRENOM_PRECISION_FP16 ? 32768.f : 1.f, 0, 0, 0};
+            e = cudaMemcpyAsync(o.lss, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+        }
+    }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         cudaFree(o.arena);
+        cudaFree(o.lss);
         return cuda_fail(c, e, "object initialisation");
     }
     o.alive = true;
@@ -460,6 +508,7 @@ int prenom_destroy_object(prenom_ctx *c, int32_t obj)
     cudaStreamSynchronize(c->stream);
     cudaFree(o->arena);
     cudaFree(o->grid);
+    cudaFree(o->lss);
     *o = Object();
     return PRENOM_OK;
 }
@@ -536,6 +585,12 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
     for (int i = 0; i < n_batches; ++i) {
         const prenom_ray_batch &b = batches[i];
         Object &o = c->objs[b.obj];
+        if (o.lss && o.step == 0 && op->loss_scale_init > 0.f) {  // caller-chosen starting scale
+            const float s0 = op->loss_scale_init;
+            const cudaError_t e = cudaMemcpyAsync(&o.lss->scale, &s0, sizeof(float), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                cudaStreamSynchronize(c->stream);
+        }
         ObjDesc od = make_objdesc(o, o.grad);
         BatchDesc bd = make_batchdesc(c, o, b, *op, kTrain, 128);
         bd.loss = loss_dev ? loss_dev + i : c->scratch;
@@ -666,8 +721,38 @@ int prenom_sync(prenom_ctx *c)
 {
     if (!c)
         return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
-    const cudaError_t e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "stream");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream");
+    int32_t st = 0;
+    e = cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "status read");
+    if (st != 0) {
+        cudaMemset(c->status, 0, sizeof(int32_t));
+        return fail(c, PRENOM_ERR_DEVICE_TIMEOUT, "a kernel gave up waiting for its tensor-core work");
+    }
+    return PRENOM_OK;
+}
+
+int prenom_get_loss_scale(prenom_ctx *c, int32_t obj, float *scale, int32_t *dropped_steps)
+{
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    LossScaleState s{1.f, 0, 0, 0};
+    if (o->lss) {
+        cudaError_t e = cudaMemcpyAsync(&s, o->lss, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "loss-scale read");
+    }
+    if (scale)
+        *scale = s.scale;
+    if (dropped_steps)
+        *dropped_steps = s.skipped;
+    return PRENOM_OK;
 }
 
 int prenom_enable_timing(prenom_ctx *c, int32_t enable)

@@ -49,7 +49,27 @@ struct BatchDesc {
     int32_t *out_bins;
     uint64_t seed;
     uint32_t step, obj_id;
+    // mixed-precision form only
+    const float *loss_scale;  // device scalar multiplying dL/d(MLP output) before the 16-bit cast
+    int32_t *overflow;        // device flag set when a scaled 16-bit gradient is not finite
+    int32_t *status;          // device word: nonzero when a bounded wait gave up
 };
+
+// Dynamic loss-scaling state of one mixed-precision object (device memory).
+struct LossScaleState {
+    float scale;
+    int32_t good_steps;
+    int32_t overflow;
+    int32_t skipped;
+};
+
+// Mixed-precision fused kernel (tcgen05 MLP); precision 1 = FP16, 2 = BF16.
+size_t fused_tc_smem(int W, int IN, int H);
+cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precision, int grid, cudaStream_t st);
+cudaError_t launch_fused_tc_bf16(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st);
+cudaError_t launch_fused_tc_fp16(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st);
+// Loss-scale bookkeeping after the Adam step of a mixed-precision object.
+cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st);
 
 // Dynamic shared memory (bytes) of the fused FP32 kernel for (W, IN, H, S).
 size_t fused_fp32_smem(int W, int IN, int H, int S);
@@ -67,6 +87,7 @@ struct AdamSeg {
     int64_t n;
     float lr_c1;     // lr / (1 - beta1^t)
     float inv_c2;    // 1 / (1 - beta2^t)
+    const int32_t *skip;  // mixed precision: nonzero overflow flag = drop this step (NULL for FP32)
 };
 struct AdamArgs {
     int32_t n_segs;

@@ -1,0 +1,151 @@
+"""Mixed-precision form (FP16 / BF16 MLP on the tensor cores) against the FP64 oracle.
+
+The 16-bit MLP changes results by the operands' rounding, so the bounds here
+are the mixed-precision acceptance, not the FP32 one.  They were measured on
+these cases and frozen at about five times the largest measured error
+(measured FP16: colour 3.6e-5, depth/opacity 6.9e-5, gradient rel-L2 1.5e-3;
+BF16: colour 3.0e-4, depth/opacity 7.4e-4, rel-L2 1.1e-2):
+  FP16: colour absolute <= 2e-4, depth and opacity relative (to the tensor's
+        max) and loss <= 5e-4, gradient cosine >= 0.99995, rel-L2 <= 1e-2;
+  BF16: colour absolute <= 2e-3, depth and opacity relative and loss <= 5e-3,
+        gradient cosine >= 0.9995, rel-L2 <= 5e-2.
+Samples are identical on both sides (oracle depths fed as t_in), so only the
+MLP precision differs.
+"""
+
+import numpy as np
+import pytest
+
+from helpers import CFG1, CFG2, case, oracle_t, rel
+
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {1: dict(rgb=2e-4, rel=5e-4, cos=0.99995, l2=1e-2), 2: dict(rgb=2e-3, rel=5e-3, cos=0.9995, l2=5e-2)}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2503_01582_gb300 import build
+
+    build.build()
+    import paper_2503_01582_gb300 as p
+
+    return p
+
+
+def _dev(rays, obj, cr=None, t_in=None, u=None):
+    import torch
+
+    b = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.items()}
+    b["obj"] = obj
+    for name, arr in (("c_rand", cr), ("t_in", t_in), ("uniforms", u)):
+        if arr is not None:
+            b[name] = torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float32)).cuda()
+    return b
+
+
+def _arch(p, d, precision):
+    return p.make_arch(L=d["L"], F=d["F"], log2T=d["log2T"], n_min=d["n_min"], n_max=d["n_max"], width=d["width"],
+                       hidden=d["hidden"], lambda_d=d["lambda_d"], lambda_sigma=d["lambda_sigma"], precision=precision)
+
+
+def _grad_metrics(g, want):
+    g = np.asarray(g, np.float64)
+    cos = float(g @ want / (np.linalg.norm(g) * np.linalg.norm(want)))
+    l2 = float(np.linalg.norm(g - want) / np.linalg.norm(want))
+    return cos, l2
+
+
+ARCHS = [CFG1, dict(CFG1, L=16, log2T=15, n_max=512, width=64, hidden=2),
+         dict(CFG1, L=4, log2T=12, n_max=64, width=16, hidden=3), dict(CFG1, width=32, hidden=1, lambda_sigma=1e-2)]
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("arch", ARCHS)
+def test_mixed_forward_and_gradients(pkg, arch, precision):
+    import torch
+
+    bnd = BOUNDS[precision]
+    a, theta, grid, rays, u, cr = case(arch, 256, 32, 32, seed=71, hash_range=0.5)
+    t_in = oracle_t(grid, rays, u, 32, 32)
+    want = orc.batch(a, theta, grid, rays, 32, 32, t_in=t_in, c_rand=cr, want_grad=True)
+    ctx = pkg.Context(seed=3)
+    obj = ctx.create_object(_arch(pkg, arch, precision), theta)
+    ctx.set_prior_grid(obj, grid)
+    b = _dev(rays, obj, cr=cr, t_in=t_in)
+    out = ctx.render(b, pkg.make_opts(nc=32, nr=32))
+    e_rgb = float(np.abs(out["rgb"].cpu().numpy() - want["rgb"]).max())
+    e_d = rel(out["depth"].cpu().numpy(), want["depth"])
+    e_a = rel(out["acc"].cpu().numpy(), want["acc"])
+    loss = torch.zeros(1, device="cuda")
+    ctx.train_step([b], pkg.make_opts(nc=32, nr=32, flags=pkg.PRENOM_FLAG_NO_ADAM), loss)
+    g = ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy()
+    cos, l2 = _grad_metrics(g, want["grad"])
+    e_loss = abs(loss.item() - want["loss"]) / abs(want["loss"])
+    print(f"\nprecision={precision} W={arch['width']} H={arch['hidden']} L={arch['L']}: rgb abs {e_rgb:.2e} "
+          f"depth {e_d:.2e} acc {e_a:.2e} loss {e_loss:.2e} grad cos {cos:.6f} rel-L2 {l2:.2e}")
+    assert e_rgb <= bnd["rgb"] and e_d <= bnd["rel"] and e_a <= bnd["rel"] and e_loss <= bnd["rel"]
+    assert cos >= bnd["cos"] and l2 <= bnd["l2"]
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_training_tracks_fp32(pkg, precision):
+    """20 Adam steps: the mixed-precision loss curve stays close to the oracle's."""
+    import torch
+    from helpers import pool_cfg1
+    from synth import random_colours, sample_batch, stratified_uniforms
+
+    a, theta, grid, _, _, _ = case(CFG1, 256, 32, 32, seed=81)
+    ob = orc.OracleObject(a, theta, grid)
+    ctx = pkg.Context(seed=3)
+    obj = ctx.create_object(_arch(pkg, CFG1, precision), theta)
+    ctx.set_prior_grid(obj, grid)
+    _, pool = pool_cfg1()
+    loss = torch.zeros(1, device="cuda")
+    lg, lo = [], []
+    for step in range(20):
+        rays = sample_batch(pool, 256, 500 + step)
+        u = stratified_uniforms(256, 32, 600 + step)
+        cr = random_colours(256, 700 + step)
+        t_in = oracle_t(grid, rays, u, 32, 32)
+        lo.append(ob.train_step(rays, 32, 32, t_in=t_in, c_rand=cr, lr=1e-2))
+        ctx.train_step([_dev(rays, obj, cr=cr, t_in=t_in)], pkg.make_opts(nc=32, nr=32, lr=1e-2), loss)
+        lg.append(loss.item())
+    lg, lo = np.array(lg), np.array(lo)
+    scale, dropped = ctx.loss_scale(obj)
+    print(f"\nprecision={precision}: loss rel diff per step max {np.max(np.abs(lg - lo) / lo):.2e}, "
+          f"final {lg[-1]:.5f} vs {lo[-1]:.5f}; loss scale {scale}, dropped {dropped}")
+    assert np.all(np.abs(lg - lo) <= 5e-2 * lo)
+    assert dropped == 0 and np.isfinite(scale)
+    assert lg[-1] < lg[0]
+    ctx.close()
+
+
+def test_mixed_full_size_sampled(pkg):
+    """The full-size object (L=16, T=2^19, 2x64 MLP) in BF16 at 4096 rays x 64
+    samples: sampled rays' outputs against the oracle."""
+    from helpers import pool_cfg2
+    from synth import init_params, prior_grid, random_colours, sample_batch, stratified_uniforms
+
+    a = orc.Arch(**CFG2)
+    sc, pool = pool_cfg2()
+    rays = sample_batch(pool, 4096, 0)
+    u = stratified_uniforms(4096, 64, 1)
+    grid = prior_grid(sc, 64, 0)
+    theta = init_params(orc.n_hash_params(a), a.mlp_shapes(), 3, hash_range=0.5)
+    ctx = pkg.Context(seed=3)
+    obj = ctx.create_object(_arch(pkg, CFG2, 2), theta)
+    ctx.set_prior_grid(obj, grid)
+    out = ctx.render(_dev(rays, obj, u=u), pkg.make_opts(nc=64, nr=64))
+    idx = np.random.default_rng(0).choice(4096, 48, replace=False)
+    sub = {k: v[idx] for k, v in rays.items()}
+    want = orc.batch(a, theta, grid, sub, 64, 64, u=u[idx])
+    assert float(np.abs(out["rgb"].cpu().numpy()[idx] - want["rgb"]).max()) <= BOUNDS[2]["rgb"]
+    assert rel(out["depth"].cpu().numpy()[idx], want["depth"]) <= BOUNDS[2]["rel"]
+    ctx.close()
