@@ -65,7 +65,8 @@ extern "C" {
 
 /* prenom_train_opts.flags */
 #define PRENOM_FLAG_NO_ADAM 1u      /* accumulate gradients, skip Adam (step count unchanged) */
-#define PRENOM_FLAG_CHECK_FINITE 2u /* synchronise and fail with NONFINITE on a NaN/inf loss */
+#define PRENOM_FLAG_CHECK_FINITE 2u /* synchronise and fail with NONFINITE on a NaN/inf loss (per-object path) */
+#define PRENOM_FLAG_NO_GRAPH 4u     /* batched steps: launch directly instead of replaying a captured graph */
 
 /* prenom_get_state / prenom_set_state: which buffer */
 #define PRENOM_STATE_THETA 0
@@ -179,6 +180,17 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * back-propagate into the object's gradient buffer; then one Adam step for
  * every distinct object named by the batches (unless PRENOM_FLAG_NO_ADAM).
  * Gradients are zeroed by the Adam step, so NO_ADAM steps accumulate.
+ * n_batches > 1 is the batched form (§IV-A trains objects in parallel): the
+ * batches are grouped by kernel variant (precision, width, encoding width)
+ * and each group runs as ONE persistent launch over a work list spanning all
+ * its objects; one Adam launch then updates every object.  The first calls of
+ * a new group signature try several work-chunk sizes (tiles per CTA) and keep
+ * the fastest; afterwards, on a non-default stream and with timing off, the
+ * whole step is captured once per signature as a CUDA graph and replayed
+ * (PRENOM_FLAG_NO_GRAPH disables the graph).  A batched step synchronises
+ * with the step before the previous one (two staging buffers are in flight),
+ * allocates its work-list buffers on first use and when they must grow, and
+ * updates at most 128 objects.
  * loss_dev: device [n_batches] floats receiving each batch's loss, or NULL.
  * Each object named must have a prior grid unless every batch naming it
  * gives t_in. */

@@ -18,6 +18,7 @@ from ._abi import (  # noqa: F401
     KERNEL_NAMES,
     PRENOM_FLAG_CHECK_FINITE,
     PRENOM_FLAG_NO_ADAM,
+    PRENOM_FLAG_NO_GRAPH,
     PRENOM_KERNEL_ADAM,
     PRENOM_KERNEL_RENDER,
     PRENOM_KERNEL_RENDER_BWD,

@@ -24,6 +24,7 @@ PRENOM_PRECISION_FP16 = 1
 PRENOM_PRECISION_BF16 = 2
 PRENOM_FLAG_NO_ADAM = 1
 PRENOM_FLAG_CHECK_FINITE = 2
+PRENOM_FLAG_NO_GRAPH = 4
 
 PRENOM_STATE_THETA = 0
 PRENOM_STATE_GRAD = 1

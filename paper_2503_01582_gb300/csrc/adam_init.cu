@@ -1,5 +1,6 @@
 // Adam update over every parameter of a step's objects, random initialisation,
 // and the host-side dispatch of the fused kernels.
+#include "fused_fp32_kernel.cuh"
 #include "fused_tc.cuh"
 
 namespace prenom {
@@ -38,24 +39,29 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
                 sg.grad[i] = 0.f;
             continue;
         }
+        float lr_c1 = sg.lr_c1, inv_c2 = sg.inv_c2;
+        if (sg.scal) {
+            const float2 s = *sg.scal;
+            lr_c1 = s.x;
+            inv_c2 = s.y;
+        }
         for (int64_t i = base + threadIdx.x * 4; i < end; i += blockDim.x * 4) {
             if (i + 4 <= end) {
                 float4 th = *reinterpret_cast<float4 *>(sg.theta + i);
                 const float4 g = __ldcs(reinterpret_cast<const float4 *>(sg.grad + i));
                 float4 m = __ldcs(reinterpret_cast<const float4 *>(sg.m + i));
                 float4 v = __ldcs(reinterpret_cast<const float4 *>(sg.v + i));
-                adam_one(th.x, m.x, v.x, g.x, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
-                adam_one(th.y, m.y, v.y, g.y, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
-                adam_one(th.z, m.z, v.z, g.z, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
-                adam_one(th.w, m.w, v.w, g.w, a.beta1, a.beta2, a.eps, sg.lr_c1, sg.inv_c2);
+                adam_one(th.x, m.x, v.x, g.x, a.beta1, a.beta2, a.eps, lr_c1, inv_c2);
+                adam_one(th.y, m.y, v.y, g.y, a.beta1, a.beta2, a.eps, lr_c1, inv_c2);
+                adam_one(th.z, m.z, v.z, g.z, a.beta1, a.beta2, a.eps, lr_c1, inv_c2);
+                adam_one(th.w, m.w, v.w, g.w, a.beta1, a.beta2, a.eps, lr_c1, inv_c2);
                 *reinterpret_cast<float4 *>(sg.theta + i) = th;
                 __stcs(reinterpret_cast<float4 *>(sg.m + i), m);
                 __stcs(reinterpret_cast<float4 *>(sg.v + i), v);
                 *reinterpret_cast<float4 *>(sg.grad + i) = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
                 for (int64_t j = i; j < end; ++j) {
-                    adam_one(sg.theta[j], sg.m[j], sg.v[j], sg.grad[j], a.beta1, a.beta2, a.eps, sg.lr_c1,
-                             sg.inv_c2);
+                    adam_one(sg.theta[j], sg.m[j], sg.v[j], sg.grad[j], a.beta1, a.beta2, a.eps, lr_c1, inv_c2);
                     sg.grad[j] = 0.f;
                 }
             }
@@ -147,6 +153,47 @@ cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The same bookkeeping for every mixed-precision object of a batched step.
+__global__ void loss_scale_update_list_kernel(const ScaleList l)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= l.n)
+        return;
+    LossScaleState *s = l.s[i];
+    if (s->overflow) {
+        s->scale = fmaxf(s->scale * 0.5f, 1.f);
+        s->good_steps = 0;
+        s->skipped += 1;
+        s->overflow = 0;
+    } else if (++s->good_steps >= 1000) {
+        s->scale = fminf(s->scale * 2.f, 16777216.f);
+        s->good_steps = 0;
+    }
+}
+
+cudaError_t launch_loss_scale_update_list(const ScaleList &l, cudaStream_t st)
+{
+    if (l.n <= 0)
+        return cudaSuccess;
+    loss_scale_update_list_kernel<<<(l.n + 127) / 128, 128, 0, st>>>(l);
+    return cudaGetLastError();
+}
+
+__global__ void zero_losses_kernel(const WorkItem *items, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        *items[i].bd.loss = 0.f;
+}
+
+cudaError_t launch_zero_losses(const WorkItem *items, int n, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    zero_losses_kernel<<<(n + 127) / 128, 128, 0, st>>>(items, n);
+    return cudaGetLastError();
+}
+
 size_t fused_tc_smem(int W, int IN, int H)
 {
     switch (W * 100 + IN) {
@@ -163,13 +210,29 @@ size_t fused_tc_smem(int W, int IN, int H)
     }
 }
 
-cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precision, int grid, cudaStream_t st)
+static cudaError_t tc_dispatch(const WorkItem &one, const WorkList &wl, int W, int IN, int precision, int grid,
+                               cudaStream_t st)
 {
     if (precision == 1)
-        return launch_fused_tc_fp16(od, bd, grid, st);
+        return launch_fused_tc_fp16(one, wl, W, IN, grid, st);
     if (precision == 2)
-        return launch_fused_tc_bf16(od, bd, grid, st);
+        return launch_fused_tc_bf16(one, wl, W, IN, grid, st);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precision, int grid, cudaStream_t st)
+{
+    WorkItem one{};
+    one.od = od;
+    one.bd = bd;
+    one.tile_begin = 0;
+    return tc_dispatch(one, WorkList{nullptr, 1, bd.n_tiles, od.H}, od.W, od.IN, precision, grid, st);
+}
+
+cudaError_t launch_fused_tc_list(const WorkList &wl, int W, int IN, int precision, int grid, cudaStream_t st)
+{
+    WorkItem unused{};
+    return tc_dispatch(unused, wl, W, IN, precision, grid, st);
 }
 
 // ------------------------------------------------------- fused dispatch
@@ -187,14 +250,30 @@ int fused_fp32_pick_tile(int W, int IN, int H, size_t smem_limit)
     return 0;
 }
 
-cudaError_t launch_fused_fp32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st)
+static cudaError_t fp32_dispatch(const WorkItem &one, const WorkList &wl, int W, int IN, int S, int grid,
+                                 cudaStream_t st)
 {
-    switch (od.W) {
-    case 16: return launch_fused_fp32_w16(od, bd, S, grid, st);
-    case 32: return launch_fused_fp32_w32(od, bd, S, grid, st);
-    case 64: return launch_fused_fp32_w64(od, bd, S, grid, st);
+    switch (W) {
+    case 16: return launch_fused_fp32_w16(one, wl, IN, S, grid, st);
+    case 32: return launch_fused_fp32_w32(one, wl, IN, S, grid, st);
+    case 64: return launch_fused_fp32_w64(one, wl, IN, S, grid, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fused_fp32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st)
+{
+    WorkItem one{};
+    one.od = od;
+    one.bd = bd;
+    one.tile_begin = 0;
+    return fp32_dispatch(one, WorkList{nullptr, 1, bd.n_tiles, od.H}, od.W, od.IN, S, grid, st);
+}
+
+cudaError_t launch_fused_fp32_list(const WorkList &wl, int W, int IN, int S, int grid, cudaStream_t st)
+{
+    WorkItem unused{};
+    return fp32_dispatch(unused, wl, W, IN, S, grid, st);
 }
 
 }  // namespace prenom

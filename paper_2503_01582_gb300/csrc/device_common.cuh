@@ -167,6 +167,19 @@ __device__ __forceinline__ float prior_lookup(const float *__restrict__ grid, in
     return s;
 }
 
+// Fire-and-forget reductions into global memory.  The explicit .global state
+// space matters: a pointer read from a descriptor is otherwise a generic
+// address, and generic atomics are ordered against shared-memory traffic.
+__device__ __forceinline__ void red_add_f2(float2 *p, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b));
+}
+
+__device__ __forceinline__ void red_add_f(float *p, float a)
+{
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(a));
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

@@ -367,7 +367,7 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
             for (int c = 0; c < 8; ++c) {
                 const float w = cs.wt[c];
                 if (w != 0.f)
-                    atomicAdd(gtab + lv.offset + cs.idx[c], make_float2(w * g0, w * g1));
+                    red_add_f2(gtab + lv.offset + cs.idx[c], w * g0, w * g1);
             }
         }
     }
@@ -523,181 +523,29 @@ __device__ __forceinline__ float composite_warp(const ObjDesc &od, const BatchDe
     return loss;
 }
 
-// ------------------------------------------------------------------ kernel
-template <int W, int IN, int S>
-__global__ void __launch_bounds__(kThreads, 1) fused_fp32_kernel(const ObjDesc od, const BatchDesc bd)
+// Block-wide copy of a work item into shared memory (the inner loops then
+// read the descriptors with broadcast shared loads).  Ends with a barrier.
+__device__ __forceinline__ void stage_item(const WorkItem &src, WorkItem &dst)
 {
-    constexpr int SP = S + 4;
-    constexpr int MAXR = S / kMinNr;
-    extern __shared__ __align__(16) float sm[];
-    const int H = od.H;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nW = IN * W + (H - 1) * W * W + 4 * W;  // multiple of 4
-    const int off_out = IN * W + (H - 1) * W * W;
-    float *Wf = sm;             // [in][out] per layer (forward operand)
-    float *Wb = Wf + nW;        // [out][in] per layer (backward operand, = theta layout)
-    float *dWs = Wb + nW;       // weight-gradient accumulators, [out][in]
-    float *XT = dWs + nW;       // [IN][SP]: encoding, then dL/dX
-    float *HT = XT + IN * SP;   // [H][W][SP]: activations, then dL/dH in place
-    float *OT = HT + H * W * SP;  // [4][SP] raw outputs
-    float *dOT = OT + 4 * SP;   // [4][SP] dL/d(raw outputs)
-    float *ts = dOT + 4 * SP;   // [SP] sample depths
-    float *rayf = ts + SP;      // [MAXR][16]
-    float *cdfs = rayf + MAXR * kRayStride;  // [8][kMaxNc + 1]
-
-    const float *th = od.theta + od.mlp_off;
-    for (int i = tid; i < nW; i += kThreads) {
-        const float v = th[i];
-        Wb[i] = v;
-        dWs[i] = 0.f;
-        int lo, nin, nout, j;
-        if (i < IN * W) {
-            lo = 0; nin = IN; nout = W; j = i;
-        } else if (i < off_out) {
-            const int jj = i - IN * W;
-            lo = IN * W + (jj / (W * W)) * W * W; nin = W; nout = W; j = jj % (W * W);
-        } else {
-            lo = off_out; nin = W; nout = 4; j = i - off_out;
-        }
-        Wf[lo + (j % nin) * nout + (j / nin)] = v;
-    }
+    const int *s = reinterpret_cast<const int *>(&src);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(WorkItem) / sizeof(int)); i += blockDim.x)
+        d[i] = s[i];
     __syncthreads();
-
-    const int nr = bd.nr, NR = bd.rays_per_tile;
-    float loss_acc = 0.f;
-    for (int tile = blockIdx.x; tile < bd.n_tiles; tile += gridDim.x) {
-        const int ray0 = tile * NR;
-        const int nrt = min(NR, bd.n_rays - ray0);
-        const int ns = nrt * nr;
-        // (1) ray data
-        for (int i = tid; i < nrt; i += kThreads) {
-            const int g = ray0 + i;
-            float *rf = rayf + i * kRayStride;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                rf[RF_O + a] = bd.o[(size_t)g * 3 + a];
-                rf[RF_D + a] = bd.d[(size_t)g * 3 + a];
-            }
-            if (bd.mode == kTrain) {
-                const bool obj = bd.is_obj[g] != 0;
-                rf[RF_OBJ] = obj ? 1.f : 0.f;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    rf[RF_RGB + a] = obj ? bd.rgb[(size_t)g * 3 + a] : 0.f;
-                rf[RF_DEPTH] = obj ? bd.depth[g] : 0.f;
-                if (!obj) {
-                    if (bd.c_rand) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            rf[RF_CR + a] = bd.c_rand[(size_t)g * 3 + a];
-                    } else {
-                        const float3 c = philox_colour(bd.seed, bd.step, bd.obj_id, (uint32_t)g);
-                        rf[RF_CR] = c.x;
-                        rf[RF_CR + 1] = c.y;
-                        rf[RF_CR + 2] = c.z;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // (2) sampling
-        for (int r = warp; r < nrt; r += kThreads / 32)
-            sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
-        __syncthreads();
-        // (3) encoding
-        encode_or_scatter<IN, S, false>(od, bd, rayf, ts, XT, dOT, ns);
-        __syncthreads();
-        // (4) MLP forward
-        gemm_sn<S, W, kRelu>(XT, Wf, IN, HT);
-        __syncthreads();
-        for (int l = 1; l < H; ++l) {
-            gemm_sn<S, W, kRelu>(HT + (l - 1) * W * SP, Wf + IN * W + (l - 1) * W * W, W, HT + l * W * SP);
-            __syncthreads();
-        }
-        out_layer_fwd<W, S>(HT + (H - 1) * W * SP, Wf + off_out, OT);
-        __syncthreads();
-        // (5) compositing, loss and its adjoint
-        for (int r = warp; r < nrt; r += kThreads / 32) {
-            const float lr = composite_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane);
-            if (lane == 0)
-                loss_acc += lr;
-        }
-        __syncthreads();
-        if (bd.mode == kRender)
-            continue;
-        // (6) MLP backward
-        gemm_dw<S, 4, W>(dOT, HT + (H - 1) * W * SP, dWs + off_out);
-        __syncthreads();
-        gemm_sn<S, W, kMaskByOld>(dOT, Wb + off_out, 4, HT + (H - 1) * W * SP);
-        __syncthreads();
-        for (int l = H - 1; l >= 1; --l) {
-            gemm_dw<S, W, W>(HT + l * W * SP, HT + (l - 1) * W * SP, dWs + IN * W + (l - 1) * W * W);
-            __syncthreads();
-            gemm_sn<S, W, kMaskByOld>(HT + l * W * SP, Wb + IN * W + (l - 1) * W * W, W, HT + (l - 1) * W * SP);
-            __syncthreads();
-        }
-        gemm_dw<S, W, IN>(HT, XT, dWs);
-        __syncthreads();
-        gemm_sn<S, IN, kStore>(HT, Wb, W, XT);
-        __syncthreads();
-        // (7) hash-grid scatter
-        encode_or_scatter<IN, S, true>(od, bd, rayf, ts, XT, dOT, ns);
-        __syncthreads();
-    }
-    if (bd.mode == kRender)
-        return;
-    if (lane == 0 && bd.mode == kTrain && loss_acc != 0.f)
-        atomicAdd(bd.loss, loss_acc);
-    float *gw = od.grad + od.mlp_off;
-    for (int i = tid; i < nW; i += kThreads) {
-        const float v = dWs[i];
-        if (v != 0.f)
-            atomicAdd(gw + i, v);
-    }
 }
 
-inline size_t fused_fp32_smem_floats(int W, int IN, int H, int S)
+// Index of the work item owning launch-wide tile t (items sorted by tile_begin).
+__device__ __forceinline__ int item_of_tile(const WorkItem *list, int n, int t)
 {
-    const size_t SP = (size_t)S + 4;
-    const size_t nW = (size_t)IN * W + (size_t)(H - 1) * W * W + 4 * (size_t)W;
-    return 3 * nW + IN * SP + (size_t)H * W * SP + 8 * SP + SP + (size_t)(S / kMinNr) * kRayStride +
-           8 * (size_t)(kMaxNc + 1);
-}
-
-template <int W, int IN, int S>
-cudaError_t launch_fused_t(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
-{
-    const size_t smem = fused_fp32_smem_floats(W, IN, od.H, S) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fused_fp32_kernel<W, IN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess)
-        return e;
-    fused_fp32_kernel<W, IN, S><<<grid, kThreads, smem, st>>>(od, bd);
-    return cudaGetLastError();
-}
-
-template <int W>
-cudaError_t launch_fused_w(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st)
-{
-    if (S == 128) {
-        switch (od.IN) {
-        case 8: return launch_fused_t<W, 8, 128>(od, bd, grid, st);
-        case 16: return launch_fused_t<W, 16, 128>(od, bd, grid, st);
-        case 32: return launch_fused_t<W, 32, 128>(od, bd, grid, st);
-        default: return cudaErrorInvalidValue;
-        }
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (list[mid].tile_begin <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
-    if constexpr (W == 64) {  // only the widest MLP ever needs the smaller tile
-        if (S != 64)
-            return cudaErrorInvalidValue;
-        switch (od.IN) {
-        case 8: return launch_fused_t<W, 8, 64>(od, bd, grid, st);
-        case 16: return launch_fused_t<W, 16, 64>(od, bd, grid, st);
-        case 32: return launch_fused_t<W, 32, 64>(od, bd, grid, st);
-        default: return cudaErrorInvalidValue;
-        }
-    }
-    return cudaErrorInvalidValue;
+    return lo;
 }
 
 }  // namespace prenom

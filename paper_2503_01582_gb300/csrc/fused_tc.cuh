@@ -201,8 +201,74 @@ __device__ __forceinline__ uint32_t dw_col(int layer)
     return layer == 0 ? 64u : (uint32_t)(64 + INP + (layer - 1) * W);
 }
 
+// 16-bit weights of one object into the interleaved buffers (their padding
+// rows and columns were cleared once at kernel start and are never written).
 template <int W, int IN, bool BF16>
-__global__ void __launch_bounds__(kThreads, 2) fused_tc_kernel(const ObjDesc od, const BatchDesc bd)
+__device__ __forceinline__ void tc_load_object(const ObjDesc &od, unsigned char *Wt0, unsigned char *WtH,
+                                               unsigned char *WtO)
+{
+    using Hf = Half<BF16>;
+    constexpr int INP = TcLayout<W, IN>::INP;
+    const int H = od.H;
+    const float *th = od.theta + od.mlp_off;
+    for (int i = threadIdx.x; i < W * IN; i += kThreads) {
+        const int o = i / IN, c = i % IN;
+        *reinterpret_cast<uint16_t *>(Wt0 + il_off(o, c, INP)) = Hf::bits(th[i]);
+    }
+    for (int l = 1; l < H; ++l)
+        for (int i = threadIdx.x; i < W * W; i += kThreads) {
+            const int o = i / W, c = i % W;
+            *reinterpret_cast<uint16_t *>(WtH + (l - 1) * TcLayout<W, IN>::wh + il_off(o, c, W)) =
+                Hf::bits(th[IN * W + (l - 1) * W * W + i]);
+        }
+    for (int i = threadIdx.x; i < 4 * W; i += kThreads) {
+        const int o = i / W, c = i % W;
+        *reinterpret_cast<uint16_t *>(WtO + il_off(o, c, W)) = Hf::bits(th[IN * W + (H - 1) * W * W + i]);
+    }
+}
+
+// Loss, dW_out (CUDA-core sums) and the TMEM weight-gradient accumulators of
+// the CTA into the object (all threads call it; M = 64 accumulator layout:
+// warp quadrant q holds rows 16q .. 16q+15 in its lanes 0..15).
+template <int W, int IN>
+__device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDesc &bd, uint32_t lane_base,
+                                                bool have_dw, float &dwo_acc, float &loss_acc, float inv_scale)
+{
+    constexpr int INP = TcLayout<W, IN>::INP;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int quad = warp & 3, half = warp >> 2;
+    if (lane == 0 && bd.mode == kTrain && loss_acc != 0.f)
+        red_add_f(bd.loss, loss_acc);
+    loss_acc = 0.f;
+    if (bd.mode == kRender)
+        return;
+    const int H = od.H;
+    float *gw = od.grad + od.mlp_off;
+    if (tid < 4 * W && dwo_acc != 0.f)
+        red_add_f(gw + IN * W + (H - 1) * W * W + tid, dwo_acc);
+    dwo_acc = 0.f;
+    if (!have_dw)
+        return;
+    for (int l = 0; l < H; ++l) {
+        const int ncol = l == 0 ? INP : W;
+        const int nin = l == 0 ? IN : W;
+        float *dst = gw + (l == 0 ? 0 : IN * W + (l - 1) * W * W);
+        for (int c0 = half * 8; c0 < ncol; c0 += 16) {
+            float v[8];
+            tmem_ld8(lane_base + dw_col<W, IN>(l) + c0, v);
+            const int row = 16 * quad + lane;
+            if (lane < 16 && row < W)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (c0 + j < nin && v[j] != 0.f)
+                        red_add_f(dst + row * nin + c0 + j, v[j] * inv_scale);
+        }
+    }
+}
+
+template <int W, int IN, bool BF16>
+__global__ void __launch_bounds__(kThreads, 2)
+    fused_tc_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
     using L = TcLayout<W, IN>;
     using Hf = Half<BF16>;
@@ -211,17 +277,20 @@ __global__ void __launch_bounds__(kThreads, 2) fused_tc_kernel(const ObjDesc od,
     constexpr int MAXR = kTcTile / kMinNr;
     constexpr int NL = IN / 2;  // levels (F = 2)
     extern __shared__ __align__(128) unsigned char smc[];
-    const int H = od.H;
+    const WorkItem *list = wl.items ? wl.items : &one;
+    const int n_items = wl.items ? wl.n_items : 1;
+    const int total = wl.items ? wl.total_tiles : one.bd.n_tiles;
+    const int hmax = wl.items ? wl.hmax : one.od.H;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int quad = warp & 3, half = warp >> 2;
     const int srow = 32 * quad + lane;  // TMEM lane = sample row of this thread
 
     unsigned char *Wt0 = smc;
     unsigned char *WtH = Wt0 + L::w0;                 // layers 1..H-1
-    unsigned char *WtO = WtH + (H - 1) * L::wh;
+    unsigned char *WtO = WtH + (hmax - 1) * L::wh;
     unsigned char *XA = WtO + L::wo;
     unsigned char *HA = XA + L::xa;                   // H buffers of ha bytes
-    unsigned char *DA = HA + H * L::ha;
+    unsigned char *DA = HA + hmax * L::ha;
     unsigned char *DOA = DA + L::da;
     float *OT = reinterpret_cast<float *>(DOA + L::doa);  // [4][SP] raw outputs
     float *dOT = OT + 4 * SP;                         // [4][SP] dL/d(raw outputs), unscaled
@@ -231,39 +300,17 @@ __global__ void __launch_bounds__(kThreads, 2) fused_tc_kernel(const ObjDesc od,
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cdfs + 8 * (kMaxNc + 1));
     uint64_t *mbar = reinterpret_cast<uint64_t *>(tmem_slot + 2);
 
-    const bool train = bd.mode != kRender;
-    const float scale = (train && bd.loss_scale) ? *bd.loss_scale : 1.f;
-    const float inv_scale = 1.f / scale;
-
-    // ---- 16-bit weights into the interleaved layout; padding stays zero
-    {
-        const float *th = od.theta + od.mlp_off;
-        // buffers with padding that is never written again: W_0 (columns IN..INP),
-        // W_out (rows 4..15), DA (columns W..63), dO (columns 4..15)
-        for (int i = tid; i < L::w0 / 4; i += kThreads)
-            reinterpret_cast<uint32_t *>(Wt0)[i] = 0u;
-        for (int i = tid; i < L::wo / 4; i += kThreads)
-            reinterpret_cast<uint32_t *>(WtO)[i] = 0u;
-        for (int i = tid; i < L::da / 4; i += kThreads)
-            reinterpret_cast<uint32_t *>(DA)[i] = 0u;
-        for (int i = tid; i < L::doa / 4; i += kThreads)
-            reinterpret_cast<uint32_t *>(DOA)[i] = 0u;
-        __syncthreads();
-        for (int i = tid; i < W * IN; i += kThreads) {
-            const int o = i / IN, c = i % IN;
-            *reinterpret_cast<uint16_t *>(Wt0 + il_off(o, c, INP)) = Hf::bits(th[i]);
-        }
-        for (int l = 1; l < H; ++l)
-            for (int i = tid; i < W * W; i += kThreads) {
-                const int o = i / W, c = i % W;
-                *reinterpret_cast<uint16_t *>(WtH + (l - 1) * L::wh + il_off(o, c, W)) =
-                    Hf::bits(th[IN * W + (l - 1) * W * W + i]);
-            }
-        for (int i = tid; i < 4 * W; i += kThreads) {
-            const int o = i / W, c = i % W;
-            *reinterpret_cast<uint16_t *>(WtO + il_off(o, c, W)) = Hf::bits(th[IN * W + (H - 1) * W * W + i]);
-        }
-    }
+    // buffers with padding that is never written again: W_0 (columns IN..INP),
+    // W_out (rows 4..15), DA (columns W..63), dO (columns 4..15)
+    for (int i = tid; i < L::w0 / 4; i += kThreads)
+        reinterpret_cast<uint32_t *>(Wt0)[i] = 0u;
+    for (int i = tid; i < L::wo / 4; i += kThreads)
+        reinterpret_cast<uint32_t *>(WtO)[i] = 0u;
+    for (int i = tid; i < L::da / 4; i += kThreads)
+        reinterpret_cast<uint32_t *>(DA)[i] = 0u;
+    for (int i = tid; i < L::doa / 4; i += kThreads)
+        reinterpret_cast<uint32_t *>(DOA)[i] = 0u;
+    __syncthreads();
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -287,12 +334,37 @@ __global__ void __launch_bounds__(kThreads, 2) fused_tc_kernel(const ObjDesc od,
     uint32_t parity = 0;
     bool ok = true;
     bool first_dw = true;
-    const int off_out = IN * W + (H - 1) * W * W;
     float dwo_acc = 0.f;  // dW_out entry (o, i) = (tid / W, tid % W) for tid < 4W
     float loss_acc = 0.f;
-    const int nr = bd.nr, NR = bd.rays_per_tile;
+    float scale = 1.f, inv_scale = 1.f;
 
-    for (int tile = blockIdx.x; tile < bd.n_tiles && ok; tile += gridDim.x) {
+    __shared__ __align__(16) WorkItem cur;  // the item being processed
+    const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t0 = (int)blockIdx.x * per, t1 = min(total, t0 + per);
+    int k = -1;
+    for (int t = t0; t < t1 && ok; ++t) {
+        int nk = k < 0 ? item_of_tile(list, n_items, t) : k;
+        while (nk + 1 < n_items && list[nk + 1].tile_begin <= t)
+            ++nk;
+        if (nk != k) {  // entering another object: flush the previous one, load this one
+            if (k >= 0)
+                tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, dwo_acc, loss_acc, inv_scale);
+            __syncthreads();
+            stage_item(list[nk], cur);
+            tc_load_object<W, IN, BF16>(cur.od, Wt0, WtH, WtO);
+            k = nk;
+            first_dw = true;
+            const BatchDesc &nb = cur.bd;
+            scale = (nb.mode != kRender && nb.loss_scale) ? *nb.loss_scale : 1.f;
+            inv_scale = 1.f / scale;
+            tc_sync();
+        }
+        const ObjDesc &od = cur.od;
+        const BatchDesc &bd = cur.bd;
+        const int H = od.H;
+        const bool train = bd.mode != kRender;
+        const int nr = bd.nr, NR = bd.rays_per_tile;
+        const int tile = t - cur.tile_begin;
         const int ray0 = tile * NR;
         const int nrt = min(NR, bd.n_rays - ray0);
         const int ns = nrt * nr;
@@ -533,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused_tc_kernel(const ObjDesc od,
                     for (int c = 0; c < 8; ++c) {
                         const float w = cs.wt[c];
                         if (w != 0.f)
-                            atomicAdd(gtab + lv.offset + cs.idx[c], make_float2(w * g0, w * g1));
+                            red_add_f2(gtab + lv.offset + cs.idx[c], w * g0, w * g1);
                     }
                 }
             }
@@ -541,56 +613,31 @@ __global__ void __launch_bounds__(kThreads, 2) fused_tc_kernel(const ObjDesc od,
         tc_sync();
     }
 
-    if (train && ok) {
-        if (lane == 0 && bd.mode == kTrain && loss_acc != 0.f)
-            atomicAdd(bd.loss, loss_acc);
-        float *gw = od.grad + od.mlp_off;
-        if (tid < 4 * W && dwo_acc != 0.f)
-            atomicAdd(gw + off_out + tid, dwo_acc);
-        // dW accumulators: M = 64 layout, warp quadrant q holds rows 16q .. 16q+15 in lanes 0..15
-        if (!first_dw) {
-            for (int l = 0; l < H; ++l) {
-                const int ncol = l == 0 ? INP : W;
-                const int nin = l == 0 ? IN : W;
-                float *dst = gw + (l == 0 ? 0 : IN * W + (l - 1) * W * W);
-                for (int c0 = half * 8; c0 < ncol; c0 += 16) {
-                    float v[8];
-                    tmem_ld8(lane_base + dw_col<W, IN>(l) + c0, v);
-                    const int row = 16 * quad + lane;
-                    if (lane < 16 && row < W)
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (c0 + j < nin && v[j] != 0.f)
-                                atomicAdd(dst + row * nin + c0 + j, v[j] * inv_scale);
-                }
-            }
-        }
-    } else if (lane == 0 && bd.mode == kTrain && loss_acc != 0.f) {
-        atomicAdd(bd.loss, loss_acc);
-    }
+    if (k >= 0 && ok)
+        tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, dwo_acc, loss_acc, inv_scale);
     tc_sync();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
 template <int W, int IN, bool BF16>
-cudaError_t launch_tc_t(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
+cudaError_t launch_tc_t(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
-    const size_t smem = TcLayout<W, IN>::bytes(od.H);
+    const size_t smem = TcLayout<W, IN>::bytes(wl.items ? wl.hmax : one.od.H);
     cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<W, IN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)
         return e;
-    fused_tc_kernel<W, IN, BF16><<<grid, kThreads, smem, st>>>(od, bd);
+    fused_tc_kernel<W, IN, BF16><<<grid, kThreads, smem, st>>>(one, wl);
     return cudaGetLastError();
 }
 
 template <bool BF16>
-cudaError_t launch_tc_prec(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
+cudaError_t launch_tc_prec(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st)
 {
 #define PRENOM_TC_CASE(Wv, INv)                                                                                       \
-    if (od.W == Wv && od.IN == INv)                                                                                   \
-        return launch_tc_t<Wv, INv, BF16>(od, bd, grid, st);
+    if (W == Wv && IN == INv)                                                                                         \
+        return launch_tc_t<Wv, INv, BF16>(one, wl, grid, st);
     PRENOM_TC_CASE(16, 8)
     PRENOM_TC_CASE(16, 16)
     PRENOM_TC_CASE(16, 32)

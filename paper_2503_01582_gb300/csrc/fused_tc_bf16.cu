@@ -3,9 +3,9 @@
 
 namespace prenom {
 
-cudaError_t launch_fused_tc_bf16(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st)
+cudaError_t launch_fused_tc_bf16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st)
 {
-    return launch_tc_prec<true>(od, bd, grid, st);
+    return launch_tc_prec<true>(one, wl, W, IN, grid, st);
 }
 
 }  // namespace prenom

@@ -1,11 +1,11 @@
 // Fused FP32 kernels for MLP width 32 (all encoding widths and tile sizes).
-#include "fused_fp32.cuh"
+#include "fused_fp32_kernel.cuh"
 
 namespace prenom {
 
-cudaError_t launch_fused_fp32_w32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st)
+cudaError_t launch_fused_fp32_w32(const WorkItem &one, const WorkList &wl, int IN, int S, int grid, cudaStream_t st)
 {
-    return launch_fused_w<32>(od, bd, S, grid, st);
+    return launch_fused_w<32>(one, wl, IN, S, grid, st);
 }
 
 }  // namespace prenom

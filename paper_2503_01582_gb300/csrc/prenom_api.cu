@@ -4,7 +4,11 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <array>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -54,6 +58,18 @@ struct prenom_ctx {
     double total_ms[PRENOM_N_KERNELS] = {};
     int64_t count[PRENOM_N_KERNELS] = {};
     int64_t launches = 0;
+    // batched steps: device work list (+ per-object Adam factors behind it),
+    // two pinned staging buffers, the graphs captured per step signature and
+    // the autotuner's choice of tiles per CTA per group signature
+    unsigned char *d_work = nullptr;
+    size_t d_work_cap = 0;
+    unsigned char *h_stage[2] = {nullptr, nullptr};
+    size_t h_stage_cap = 0;
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    int stage_idx = 0;
+    std::map<std::string, cudaGraphExec_t> graphs;
+    std::map<std::string, std::vector<float>> tune_ms;  // measured ms per candidate
+    std::map<std::string, int> tune_best;               // chosen candidate index
 };
 
 namespace {
@@ -341,6 +357,299 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
     return PRENOM_OK;
 }
 
+// ------------------------------------------------------------ batched step
+// A batched step groups its (object, batch) items by kernel variant
+// (precision, W, IN, tile) and runs each group as one persistent launch over
+// a device work list; one Adam launch then updates every object.  The work
+// list and the per-object Adam factors are copied from a pinned staging
+// buffer by the step itself, so the whole step can be captured once per
+// signature as a CUDA graph and replayed with new rays.
+struct Group {
+    int precision, W, IN, S, hmax, first, count, total_tiles, grid;
+};
+
+struct Plan {
+    std::vector<WorkItem> items;
+    std::vector<Group> groups;
+    std::vector<int32_t> touched;   // objects updated by Adam, first appearance order
+    std::vector<float2> adam_scal;  // (lr_c1, inv_c2) per touched object
+    AdamArgs adam{};                // constant across steps (factors read from device)
+    int adam_grid = 0;
+    ScaleList scales{};
+};
+
+// Work-chunk candidates of the autotuner: tiles per CTA (0 = one persistent
+// wave of resident CTAs).
+constexpr int kTuneTpc[] = {0, 16, 8, 4};
+constexpr int kTuneN = 4;
+
+int group_grid(const prenom_ctx *c, const Group &g, int cand)
+{
+    int per_sm = 1;
+    if (g.precision != PRENOM_PRECISION_FP32 && 2 * (fused_tc_smem(g.W, g.IN, g.hmax) + 1024) <= 228 * 1024)
+        per_sm = 2;
+    const int wave = c->n_sm * per_sm;
+    if (kTuneTpc[cand] == 0)
+        return std::max(1, std::min(g.total_tiles, wave));
+    return std::max(1, std::min(g.total_tiles, std::max(wave, (g.total_tiles + kTuneTpc[cand] - 1) / kTuneTpc[cand])));
+}
+
+std::string group_key(const Group &g)
+{
+    char buf[128];
+    snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", g.precision, g.W, g.IN, g.S, g.hmax, g.count, g.total_tiles);
+    return buf;
+}
+
+int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const prenom_train_opts &op, float *loss_dev,
+                 Plan &p)
+{
+    std::vector<std::array<int, 4>> keys(n);
+    for (int i = 0; i < n; ++i) {
+        const Object &o = c->objs[batches[i].obj];
+        int S = 128;
+        if (o.arch.precision == PRENOM_PRECISION_FP32) {
+            S = fused_fp32_pick_tile(o.arch.width, o.IN, o.arch.hidden, c->smem_optin);
+            if (S == 0)
+                return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
+        }
+        keys[i] = {o.arch.precision, o.arch.width, o.IN, S};
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return keys[a] < keys[b]; });
+    p.items.resize(n);
+    for (int j = 0; j < n;) {
+        Group g{keys[order[j]][0], keys[order[j]][1], keys[order[j]][2], keys[order[j]][3], 1, j, 0, 0, 0};
+        int tiles = 0;
+        while (j < n && keys[order[j]] == keys[order[g.first]]) {
+            const int i = order[j];
+            const prenom_ray_batch &b = batches[i];
+            const Object &o = c->objs[b.obj];
+            WorkItem &w = p.items[j];
+            w.od = make_objdesc(o, o.grad);
+            w.bd = make_batchdesc(c, o, b, op, kTrain, g.S);
+            w.bd.loss = loss_dev ? loss_dev + i : c->scratch;
+            w.tile_begin = tiles;
+            tiles += w.bd.n_tiles;
+            g.hmax = std::max(g.hmax, o.arch.hidden);
+            ++g.count;
+            ++j;
+        }
+        g.total_tiles = tiles;
+        const size_t smem = g.precision == PRENOM_PRECISION_FP32 ? fused_fp32_smem(g.W, g.IN, g.hmax, g.S)
+                                                                 : fused_tc_smem(g.W, g.IN, g.hmax);
+        if (smem == 0 || smem > c->smem_optin)
+            return fail(c, PRENOM_ERR_INVALID_ARG, "architecture group needs more shared memory than the device offers");
+        p.groups.push_back(g);
+    }
+    for (int i = 0; i < n; ++i)
+        if (std::find(p.touched.begin(), p.touched.end(), batches[i].obj) == p.touched.end())
+            p.touched.push_back(batches[i].obj);
+    if ((int)p.touched.size() > kMaxAdamSegs)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "a batched step updates at most %d objects", kMaxAdamSegs);
+    if (!(op.flags & PRENOM_FLAG_NO_ADAM)) {
+        AdamArgs &a = p.adam;
+        a.beta1 = op.beta1;
+        a.beta2 = op.beta2;
+        a.eps = op.eps;
+        a.n_segs = (int32_t)p.touched.size();
+        a.chunk_start[0] = 0;
+        for (size_t s = 0; s < p.touched.size(); ++s) {
+            Object &o = c->objs[p.touched[s]];
+            const int t = o.step + 1;
+            const double c1 = 1.0 - pow((double)op.beta1, (double)t);
+            const double c2 = 1.0 - pow((double)op.beta2, (double)t);
+            p.adam_scal.push_back(make_float2((float)((double)op.lr / c1), (float)(1.0 / c2)));
+            AdamSeg &sg = a.seg[s];
+            sg.theta = o.theta;
+            sg.grad = o.grad;
+            sg.m = o.m;
+            sg.v = o.v;
+            sg.n = o.n;
+            sg.skip = o.lss ? &o.lss->overflow : nullptr;
+            a.chunk_start[s + 1] = a.chunk_start[s] + (o.n + kAdamChunk - 1) / kAdamChunk;
+            if (o.lss && p.scales.n < kMaxScaleObjs)
+                p.scales.s[p.scales.n++] = o.lss;
+        }
+        p.adam_grid = (int)std::min<int64_t>(a.chunk_start[a.n_segs], (int64_t)c->n_sm * 8);
+    }
+    return PRENOM_OK;
+}
+
+// Enqueues one batched step on the context's stream (also used under capture).
+cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *stage, size_t bytes, bool timed)
+{
+    const size_t items_bytes = p.items.size() * sizeof(WorkItem);
+    const WorkItem *d_items = reinterpret_cast<const WorkItem *>(c->d_work);
+    const float2 *d_scal = reinterpret_cast<const float2 *>(c->d_work + items_bytes);
+    cudaError_t e = cudaMemcpyAsync(c->d_work, stage, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_zero_losses(d_items, (int)p.items.size(), c->stream);
+    for (const Group &g : p.groups) {
+        if (e != cudaSuccess || g.total_tiles == 0)
+            continue;
+        const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax};
+        cudaEvent_t ev;
+        if (timed)
+            timed_begin(c, PRENOM_KERNEL_TRAIN, &ev);
+        e = g.precision == PRENOM_PRECISION_FP32 ? launch_fused_fp32_list(wl, g.W, g.IN, g.S, g.grid, c->stream)
+                                                 : launch_fused_tc_list(wl, g.W, g.IN, g.precision, g.grid, c->stream);
+        if (timed)
+            timed_end(c, PRENOM_KERNEL_TRAIN, ev);
+    }
+    if (e == cudaSuccess && p.adam_grid > 0) {
+        AdamArgs a = p.adam;
+        for (int s = 0; s < a.n_segs; ++s)
+            a.seg[s].scal = d_scal + s;
+        cudaEvent_t ev;
+        if (timed)
+            timed_begin(c, PRENOM_KERNEL_ADAM, &ev);
+        e = launch_adam(a, p.adam_grid, c->stream);
+        if (timed)
+            timed_end(c, PRENOM_KERNEL_ADAM, ev);
+        if (e == cudaSuccess)
+            e = launch_loss_scale_update_list(p.scales, c->stream);
+    }
+    return e;
+}
+
+int launches_of(const Plan &p)
+{
+    int n = 1;  // loss reset
+    for (const Group &g : p.groups)
+        n += g.total_tiles > 0;
+    if (p.adam_grid > 0)
+        n += 1 + (p.scales.n > 0);
+    return n;
+}
+
+int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const prenom_train_opts &op, float *loss_dev)
+{
+    Plan p;
+    int rc = plan_batched(c, batches, n, op, loss_dev, p);
+    if (rc)
+        return rc;
+    // autotuner: the first calls of a group signature try each work-chunk size once
+    bool tuning = false;
+    std::vector<std::string> gkeys;
+    for (Group &g : p.groups) {
+        gkeys.push_back(group_key(g));
+        auto it = c->tune_best.find(gkeys.back());
+        int cand;
+        if (it != c->tune_best.end()) {
+            cand = it->second;
+        } else {
+            cand = (int)c->tune_ms[gkeys.back()].size();
+            tuning = true;
+        }
+        g.grid = group_grid(c, g, cand);
+    }
+    // staging buffer: wait until the step that last read it has finished
+    const size_t items_bytes = p.items.size() * sizeof(WorkItem);
+    const size_t bytes = items_bytes + p.adam_scal.size() * sizeof(float2);
+    const int b = c->stage_idx;
+    cudaError_t e = cudaSuccess;
+    if (c->stage_ev[b])
+        e = cudaEventSynchronize(c->stage_ev[b]);
+    if (e == cudaSuccess && bytes > c->h_stage_cap) {
+        cudaStreamSynchronize(c->stream);
+        for (int i = 0; i < 2; ++i) {
+            cudaFreeHost(c->h_stage[i]);
+            c->h_stage[i] = nullptr;
+        }
+        const size_t cap = std::max(bytes, (size_t)64 * sizeof(WorkItem));
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+            e = cudaMallocHost((void **)&c->h_stage[i], cap);
+        c->h_stage_cap = e == cudaSuccess ? cap : 0;
+        if (e == cudaSuccess) {
+            cudaFree(c->d_work);
+            c->d_work = nullptr;
+            e = cudaMalloc(&c->d_work, cap);
+            c->d_work_cap = e == cudaSuccess ? cap : 0;
+        }
+        for (auto &kv : c->graphs)  // captured graphs point at the old buffers
+            cudaGraphExecDestroy(kv.second);
+        c->graphs.clear();
+    }
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        if (!c->stage_ev[i])
+            e = cudaEventCreateWithFlags(&c->stage_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess)
+        return fail(c, e == cudaErrorMemoryAllocation ? PRENOM_ERR_OOM : PRENOM_ERR_CUDA, "batched step buffers: %s",
+                    cudaGetErrorString(e));
+    memcpy(c->h_stage[b], p.items.data(), items_bytes);
+    if (!p.adam_scal.empty())
+        memcpy(c->h_stage[b] + items_bytes, p.adam_scal.data(), p.adam_scal.size() * sizeof(float2));
+
+    const bool use_graph = !tuning && !c->timing && c->stream != nullptr && !(op.flags & PRENOM_FLAG_NO_GRAPH);
+    if (tuning) {
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0);
+        cudaEventCreate(&t1);
+        cudaEventRecord(t0, c->stream);
+        e = enqueue_batched(c, p, c->h_stage[b], bytes, false);
+        cudaEventRecord(t1, c->stream);
+        cudaEventSynchronize(t1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        for (size_t gi = 0; gi < p.groups.size(); ++gi) {  // whole-step time, charged to each tuned group
+            std::vector<float> &v = c->tune_ms[gkeys[gi]];
+            if (c->tune_best.count(gkeys[gi]))
+                continue;
+            v.push_back(ms);
+            if ((int)v.size() == kTuneN)
+                c->tune_best[gkeys[gi]] = (int)(std::min_element(v.begin(), v.end()) - v.begin());
+        }
+    } else if (use_graph) {
+        std::string key = std::to_string(b) + ":" + std::to_string(bytes) + ":" + std::to_string(p.adam_grid);
+        for (const Group &g : p.groups)
+            key += "|" + group_key(g) + "/" + std::to_string(g.grid);
+        for (int32_t id : p.touched)
+            key += "," + std::to_string(id);
+        char tail[96];
+        snprintf(tail, sizeof(tail), "#%a/%a/%a", (double)op.beta1, (double)op.beta2, (double)op.eps);
+        key += tail;
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t e1 = enqueue_batched(c, p, c->h_stage[b], bytes, false);
+                e = cudaStreamEndCapture(c->stream, &graph);
+                if (e == cudaSuccess)
+                    e = e1;
+            }
+            if (e == cudaSuccess)
+                e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph)
+                cudaGraphDestroy(graph);
+            if (e != cudaSuccess)
+                return cuda_fail(c, e, "batched step graph capture");
+            it = c->graphs.emplace(key, exec).first;
+        }
+        e = cudaGraphLaunch(it->second, c->stream);
+    } else {
+        const int64_t before = c->launches;  // timed launches count themselves; the total is set below
+        e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing);
+        c->launches = before;
+    }
+    if (e == cudaSuccess)
+        e = cudaEventRecord(c->stage_ev[b], c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "batched step");
+    c->stage_idx ^= 1;
+    c->launches += launches_of(p);
+    if (!(op.flags & PRENOM_FLAG_NO_ADAM))
+        for (int32_t id : p.touched)
+            c->objs[id].step += 1;
+    return PRENOM_OK;
+}
+
 }  // namespace
 
 namespace prenom {
@@ -427,6 +736,14 @@ void prenom_destroy(prenom_ctx *c)
         cudaFree(o.lss);
     }
     cudaFree(c->status);
+    for (auto &kv : c->graphs)
+        cudaGraphExecDestroy(kv.second);
+    for (int i = 0; i < 2; ++i) {
+        cudaFreeHost(c->h_stage[i]);
+        if (c->stage_ev[i])
+            cudaEventDestroy(c->stage_ev[i]);
+    }
+    cudaFree(c->d_work);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -576,6 +893,17 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
     for (int i = 0; i < n_batches; ++i)
         if ((rc = check_batch(c, batches[i], true)))
             return rc;
+    for (int i = 0; i < n_batches; ++i) {
+        Object &o = c->objs[batches[i].obj];
+        if (o.lss && o.step == 0 && op->loss_scale_init > 0.f) {  // caller-chosen starting scale
+            const float s0 = op->loss_scale_init;
+            const cudaError_t e = cudaMemcpyAsync(&o.lss->scale, &s0, sizeof(float), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                cudaStreamSynchronize(c->stream);
+        }
+    }
+    if (n_batches > 1 && !(op->flags & PRENOM_FLAG_CHECK_FINITE))
+        return train_batched(c, batches, n_batches, *op, loss_dev);
     if (loss_dev && n_batches > 0) {
         const cudaError_t e = cudaMemsetAsync(loss_dev, 0, (size_t)n_batches * sizeof(float), c->stream);
         if (e != cudaSuccess)
@@ -585,12 +913,6 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
     for (int i = 0; i < n_batches; ++i) {
         const prenom_ray_batch &b = batches[i];
         Object &o = c->objs[b.obj];
-        if (o.lss && o.step == 0 && op->loss_scale_init > 0.f) {  // caller-chosen starting scale
-            const float s0 = op->loss_scale_init;
-            const cudaError_t e = cudaMemcpyAsync(&o.lss->scale, &s0, sizeof(float), cudaMemcpyHostToDevice, c->stream);
-            if (e == cudaSuccess)
-                cudaStreamSynchronize(c->stream);
-        }
         ObjDesc od = make_objdesc(o, o.grad);
         BatchDesc bd = make_batchdesc(c, o, b, *op, kTrain, 128);
         bd.loss = loss_dev ? loss_dev + i : c->scratch;

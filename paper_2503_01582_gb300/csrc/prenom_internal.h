@@ -63,23 +63,53 @@ struct LossScaleState {
     int32_t skipped;
 };
 
+struct WorkItem;
+struct WorkList;
+
 // Mixed-precision fused kernel (tcgen05 MLP); precision 1 = FP16, 2 = BF16.
 size_t fused_tc_smem(int W, int IN, int H);
 cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precision, int grid, cudaStream_t st);
-cudaError_t launch_fused_tc_bf16(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st);
-cudaError_t launch_fused_tc_fp16(const ObjDesc &od, const BatchDesc &bd, int grid, cudaStream_t st);
+cudaError_t launch_fused_tc_list(const WorkList &wl, int W, int IN, int precision, int grid, cudaStream_t st);
+cudaError_t launch_fused_tc_bf16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st);
+cudaError_t launch_fused_tc_fp16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st);
 // Loss-scale bookkeeping after the Adam step of a mixed-precision object.
 cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st);
+constexpr int kMaxScaleObjs = 256;
+struct ScaleList {
+    int32_t n;
+    LossScaleState *s[kMaxScaleObjs];
+};
+cudaError_t launch_loss_scale_update_list(const ScaleList &l, cudaStream_t st);
+// Zeroes the loss accumulator of every item of a device work list.
+cudaError_t launch_zero_losses(const WorkItem *items, int n, cudaStream_t st);
+
+// One unit of work of a fused launch: an object's field, one batch of its
+// rays, and the launch-wide index of the batch's first tile.
+struct WorkItem {
+    ObjDesc od;
+    BatchDesc bd;
+    int32_t tile_begin;
+};
+
+// The work of a batched launch (all items share the MLP width and encoding
+// width; hidden depths may differ, hmax is the deepest).  items == nullptr
+// means a single item passed by value.
+struct WorkList {
+    const WorkItem *items;  // device memory
+    int32_t n_items, total_tiles, hmax;
+};
 
 // Dynamic shared memory (bytes) of the fused FP32 kernel for (W, IN, H, S).
 size_t fused_fp32_smem(int W, int IN, int H, int S);
 // Largest tile (128 or 64 samples) whose shared memory fits; 0 if none.
 int fused_fp32_pick_tile(int W, int IN, int H, size_t smem_limit);
-// Launches the fused kernel; returns the CUDA error of the launch.
+// Launches the fused kernel on one object; returns the CUDA error of the launch.
 cudaError_t launch_fused_fp32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
-cudaError_t launch_fused_fp32_w16(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
-cudaError_t launch_fused_fp32_w32(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
-cudaError_t launch_fused_fp32_w64(const ObjDesc &od, const BatchDesc &bd, int S, int grid, cudaStream_t st);
+// Launches the fused kernel on a work list of objects of one (W, IN).
+cudaError_t launch_fused_fp32_list(const WorkList &wl, int W, int IN, int S, int grid, cudaStream_t st);
+cudaError_t launch_fused_fp32_w16(const WorkItem &one, const WorkList &wl, int IN, int S, int grid, cudaStream_t st);
+cudaError_t launch_fused_fp32_w32(const WorkItem &one, const WorkList &wl, int IN, int S, int grid, cudaStream_t st);
+cudaError_t launch_fused_fp32_w64(const WorkItem &one, const WorkList &wl, int IN, int S, int grid, cudaStream_t st);
 
 // Adam over up to kMaxAdamSegs parameter spans.
 struct AdamSeg {
@@ -88,6 +118,7 @@ struct AdamSeg {
     float lr_c1;     // lr / (1 - beta1^t)
     float inv_c2;    // 1 / (1 - beta2^t)
     const int32_t *skip;  // mixed precision: nonzero overflow flag = drop this step (NULL for FP32)
+    const float2 *scal;   // device (lr_c1, inv_c2) of this step, or NULL to use the two fields above
 };
 struct AdamArgs {
     int32_t n_segs;
