@@ -32,7 +32,7 @@ ARCH = dict(L=16, F=2, log2T=19, n_min=16, n_max=2048, width=64, hidden=2, lambd
 N_RAYS, NR, NC, GRID_RES = 4096, 64, 64, 64
 WORKLOAD = ("single object at full size: hash grid L=16 F=2 T=2^19 res 16..2048, MLP 32-64-64-4 (ReLU, exp "
             "density, sigmoid colour), 4096 rays x 64 samples/step from the prior sampler (Nc=64) over a 64^3 "
-            "prior grid, random CSG scene, 480x640 views, depth noise 2 mm, FP32 per-object form")
+            "prior grid, random CSG scene, 480x640 views, depth noise 2 mm")
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
 DTYPE = {"fp32": "f32", "fp16": "f16 MLP / f32 accumulate", "bf16": "bf16 MLP / f32 accumulate"}
@@ -235,6 +235,90 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------- GPU arm
+# (log2 T, width, hidden layers) per object category, a stand-in for the
+# architecture table the paper's genetic search produces (its values are not
+# printed): display, laptop, chair, mug, ball, keyboard, mouse, book, plant.
+CATEGORY_ARCHS = [(17, 32, 1), (16, 32, 2), (19, 64, 3), (18, 64, 2), (14, 16, 1), (17, 32, 2), (14, 16, 1),
+                  (15, 16, 2), (19, 64, 3)]
+BATCHED_OBJECTS, BATCHED_NR = 32, 48
+
+
+def _device_batches(batches_np, obj, stream):
+    import torch
+
+    out = []
+    with torch.cuda.stream(stream):
+        for b in batches_np:
+            d = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in b.items()}
+            d["obj"] = obj
+            out.append(d)
+    return out
+
+
+def _setup_single(pkg, ctx, precision, seed, stream):
+    arch = pkg.make_arch(**ARCH, precision=PRECISION[precision])
+    probe = ctx.create_object(arch)
+    n_params = ctx.param_count(probe)
+    ctx.destroy_object(probe)
+    grid, theta, batches_np = _workload(seed, 8, n_params - mlp_macs(ARCH))
+    obj = ctx.create_object(arch, theta)
+    ctx.set_prior_grid(obj, grid)
+    return obj, _device_batches(batches_np, obj, stream), batches_np, n_params
+
+
+def _time(stream, fn, steps, warmup, barrier=lambda: None, clocks=None):
+    """Device time (ms) of `steps` calls of fn(i) on `stream`, after `warmup` calls."""
+    import torch
+
+    for i in range(warmup):
+        fn(i)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.time()
+    ev0.record(stream)
+    for i in range(steps):
+        fn(i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.mark(w0, time.time())
+    barrier()
+    return ev0.elapsed_time(ev1)
+
+
+def _batched_workload(pkg, ctx, stream, precision, seed, theta_from=None):
+    """32 objects of the category table with random CSG shapes; rays per object
+    32 * round(8 * 2^(5 a)), a ~ U[0,1) (256..8192, a projected-area share),
+    48 samples per ray, 64^3 prior grids.  Four rotating ray sets."""
+    from synth import (cameras_on_sphere, make_ray_pool, prior_grid, random_colours, sample_batch,
+                       scene_random_csg, stratified_uniforms)
+
+    rng = np.random.default_rng(seed)
+    objs, sets, n_samples = [], [[], [], [], []], 0
+    for i in range(BATCHED_OBJECTS):
+        log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
+        rays = int(32 * round(8 * 2 ** (5 * rng.random())))
+        arch = pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
+                             lambda_sigma=1e-3, precision=PRECISION[precision])
+        sc = scene_random_csg(1000 * seed + i)
+        init = None if theta_from is None else theta_from[i]
+        obj = ctx.create_object(arch, init)
+        ctx.set_prior_grid(obj, prior_grid(sc, GRID_RES, i))
+        pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 50, 480, 640, i), max(4 * rays, 4096), i,
+                             depth_noise=0.004)
+        for j in range(4):
+            b = sample_batch(pool, rays, 10 * i + j)
+            b["uniforms"] = stratified_uniforms(rays, BATCHED_NR, 20 * i + j)
+            b["c_rand"] = random_colours(rays, 30 * i + j)
+            sets[j].append(b)
+        objs.append(obj)
+        n_samples += rays * BATCHED_NR
+    dev_sets = [[_device_batches([b], o, stream)[0] for b, o in zip(s, objs)] for s in sets]
+    return objs, dev_sets, n_samples
+
+
 def run_ours(args):
     import torch
 
@@ -253,53 +337,27 @@ def run_ours(args):
         torch.distributed.barrier()
     pkg._abi.lib()
 
-    stream = torch.cuda.Stream()
-    ctx = pkg.Context(seed=rank, stream=stream)
-    arch = pkg.make_arch(**{k: v for k, v in ARCH.items()}, precision=PRECISION[args.precision])
-    probe = ctx.create_object(arch)
-    n_params = ctx.param_count(probe)
-    ctx.destroy_object(probe)
-    n_hash = n_params - mlp_macs(ARCH)
-    grid, theta, batches_np = _workload(rank, 8, n_hash)
-    obj = ctx.create_object(arch, theta)
-    ctx.set_prior_grid(obj, grid)
-    dev_batches = []
-    with torch.cuda.stream(stream):
-        for b in batches_np:
-            d = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in b.items()}
-            d["obj"] = obj
-            dev_batches.append(d)
-    opts = pkg.make_opts(nc=NC, nr=NR, lr=1e-2)
-    loss = torch.zeros(1, device="cuda")
-    torch.cuda.synchronize()
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    # warm-up
-    for i in range(args.warmup):
-        ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)
-    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    ctx = pkg.Context(seed=rank, stream=stream)
+    prec = args.precision
+    opts = pkg.make_opts(nc=NC, nr=NR, lr=1e-2)
+    loss = torch.zeros(1, device="cuda")
+    samples_per_step = N_RAYS * NR
 
-    # ---- device-resident timed region
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # ---- headline: the full-size object in the chosen form, inputs resident in HBM
+    obj, dev_batches, batches_np, n_params = _setup_single(pkg, ctx, prec, rank, stream)
+    step = lambda i: ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)  # noqa: E731
+    _time(stream, step, 0, args.warmup)
     ctx.enable_timing(True)
     launches0 = ctx.launch_count()
     clocks = ClockSampler(gpu_identifier(local))
-    barrier()
-    torch.cuda.synchronize()
     with clocks:
-        w0 = time.time()
-        ev0.record(stream)
-        for i in range(args.steps):
-            ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        clocks.mark(w0, time.time())
-    barrier()
+        ms = _time(stream, step, args.steps, 0, barrier, clocks)
     launches = ctx.launch_count() - launches0
-    ms = ev0.elapsed_time(ev1)
     k_train_ms, k_train_n = ctx.kernel_time(pkg.PRENOM_KERNEL_TRAIN)
     k_adam_ms, k_adam_n = ctx.kernel_time(pkg.PRENOM_KERNEL_ADAM)
     ctx.enable_timing(False)
@@ -307,29 +365,23 @@ def run_ours(args):
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = t.item()
-    samples_per_step = N_RAYS * NR
     value = samples_per_step * args.steps * world / (ms / 1e3)
 
-    # ---- end to end through the public API with host buffers
-    pinned = []
-    for b in batches_np:
-        pinned.append({k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in b.items()})
+    # ---- end to end through the public API with host buffers (pinned H2D, loss D2H every step)
+    pinned = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in b.items()} for b in batches_np]
     h2d = sum(t.numel() * t.element_size() for t in pinned[0].values())
     loss_host = torch.zeros(1).pin_memory()
     staging = [{k: torch.empty_like(v, device="cuda") for k, v in p.items()} for p in pinned[:2]]
-    e2e_steps = max(args.steps, 5)
+    e2e_steps = max(args.steps // 2, 5)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        src = pinned[i % len(pinned)]
-        dst = staging[i % 2]
+        src, dst = pinned[i % len(pinned)], staging[i % 2]
         with torch.cuda.stream(stream):
             for k in src:
                 dst[k].copy_(src[k], non_blocking=True)
-        b = dict(dst)
-        b["obj"] = obj
-        ctx.train_step([b], opts, loss)
+        ctx.train_step([dict(dst, obj=obj)], opts, loss)
         with torch.cuda.stream(stream):
             loss_host.copy_(loss, non_blocking=True)
         stream.synchronize()
@@ -340,27 +392,67 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = t.item()
     e2e_value = samples_per_step * e2e_steps * world / e2e_s
+    ctx.destroy_object(obj)
+
+    compare = {}
+    if world == 1 and not args.no_compare:
+        # the plain FP32 per-object form on the same object and rays
+        if prec != "fp32":
+            o32, b32, _, _ = _setup_single(pkg, ctx, "fp32", rank, stream)
+            f = lambda i: ctx.train_step([b32[i % len(b32)]], opts, loss)  # noqa: E731
+            ms32 = _time(stream, f, max(args.steps // 4, 20), args.warmup)
+            compare["fp32_per_object"] = {"value": samples_per_step * max(args.steps // 4, 20) / (ms32 / 1e3),
+                                          "unit": "samples/s", "ms_per_step": ms32 / max(args.steps // 4, 20)}
+            ctx.destroy_object(o32)
+        # 32 heterogeneous objects: one batched step (FP16, graph replay) vs FP32 one object at a time
+        objs16, sets16, n_smp = _batched_workload(pkg, ctx, stream, prec, 7)
+        thetas = [ctx.get_state(o).cpu().numpy() for o in objs16]
+        objs32, sets32, _ = _batched_workload(pkg, ctx, stream, "fp32", 7, theta_from=thetas)
+        bopts = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2)
+        lossb = torch.zeros(len(objs16), device="cuda")
+        nb = max(args.steps // 20, 10)
+        fb = lambda i: ctx.train_step(sets16[i % 4], bopts, lossb)  # noqa: E731
+        msb = _time(stream, fb, nb, max(args.warmup, 6))  # >= 4 calls tune the work-chunk size first
+        fl = lambda i: [ctx.train_step([b], bopts, lossb[j:j + 1]) for j, b in enumerate(sets32[i % 4])]  # noqa
+        msl = _time(stream, fl, nb, 2)
+        compare["batched_32_objects"] = {
+            "workload": "32 objects of the category table (T 2^14..2^19, W 16/32/64, 1-3 hidden layers), "
+                        "256..8192 rays x 48 samples, %d samples per step" % n_smp,
+            "batched_" + prec: {"value": n_smp * nb / (msb / 1e3), "unit": "samples/s", "ms_per_step": msb / nb,
+                                "form": "one launch per kernel variant, CUDA graph replay"},
+            "fp32_per_object_loop": {"value": n_smp * nb / (msl / 1e3), "unit": "samples/s",
+                                     "ms_per_step": msl / nb, "form": "32 single-object FP32 steps"},
+            "speedup": msl / msb}
+        for o in objs16 + objs32:
+            ctx.destroy_object(o)
 
     # ---- roofline of the dominant kernel (the fused training kernel)
     peaks = load_peaks()
     train_avg_s = (k_train_ms / max(k_train_n, 1)) / 1e3
     adam_avg_s = (k_adam_ms / max(k_adam_n, 1)) / 1e3
-    flops = samples_per_step * mlp_macs(ARCH) * 6  # MLP: 2 MAC fwd + 4 MAC bwd flops per sample
-    achieved = flops / train_avg_s / 1e12
-    traffic = profiled_traffic("fused_fp32_kernel")
+    feat_bytes = 8 * ARCH["L"] * ARCH["F"] * 4  # corners x levels x features x FP32, per sample
+    algo = samples_per_step * 2 * feat_bytes  # gather + scatter
+    achieved = algo / train_avg_s / 1e9
+    flops = samples_per_step * mlp_macs(ARCH) * 6  # MLP: 2 MAC forward + 4 MAC backward flops per sample
     adam_bytes = n_params * 28  # read g, m, v, theta; write m, v, theta
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4), "traffic": traffic,
-                "kernel": "fused_fp32_kernel (sample+encode+MLP+render+loss+backward+scatter)",
-                "algorithmic": f"{mlp_macs(ARCH) * 6} MLP flop/sample x {samples_per_step} samples",
-                "peak_src": "FP32 FFMA: 152 SMs x 128 lanes x 2 x 2070 MHz",
+    kname = "fused_fp32_kernel" if prec == "fp32" else "fused_tc_kernel"
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": profiled_traffic(kname + "/" + prec),
+                "kernel": kname + " (sample+encode+MLP+render+loss+backward+scatter), " + prec,
+                "algorithmic": f"{2 * feat_bytes} B/sample (hash gather {feat_bytes} + scatter {feat_bytes}) x "
+                               f"{samples_per_step} samples",
+                "peak_src": peaks["src"] + " copy bandwidth",
+                "mlp": ({"bound": "alu", "achieved_tflops": round(flops / train_avg_s / 1e12, 2),
+                         "peak_tflops": round(FP32_PEAK_TFLOPS, 1), "peak_src": "FP32 FFMA 152x128x2x2070 MHz"}
+                        if prec == "fp32" else
+                        {"bound": "tensor", "achieved_tflops": round(flops / train_avg_s / 1e12, 2),
+                         "peak_tflops": peaks["bf16"], "peak_src": peaks["src"] + " bf16 (fp16 same rate)"}),
                 "other_kernels": {"adam": {"bound": "hbm", "achieved": round(adam_bytes / adam_avg_s / 1e9, 1),
                                            "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                            "frac": round(adam_bytes / adam_avg_s / 1e9 / peaks["hbm_gbs"], 4),
-                                           "peak_src": peaks["src"], "avg_us": round(adam_avg_s * 1e6, 2)},
+                                           "avg_us": round(adam_avg_s * 1e6, 2)},
                                   "train_avg_us": round(train_avg_s * 1e6, 2)}}
 
-    line = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -370,21 +462,20 @@ def run_ours(args):
                               f"({r['t_adam']:.2f} s), FP64, 1 host thread, extrapolated to the 4096-ray step")}
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-                "config": {"workload": WORKLOAD, "rays_per_step": N_RAYS, "samples_per_ray": NR, "probes": NC,
-                           "params": n_params, "form": FORM[args.precision],
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+                "config": {"workload": WORKLOAD, "form": FORM[prec], "rays_per_step": N_RAYS, "samples_per_ray": NR,
+                           "probes": NC, "params": n_params,
                            "parallelism": f"{world} independent objects (one per GPU)" if world > 1 else "1 object",
                            "l2": "working set > L2: theta, grad, Adam m and v (4 x %.0f MB) stream every step"
                                  % (n_params * 4 / 1e6)},
                 "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": 4},
                 "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
-                "clocks": clocks.summary()}
+                "clocks": clocks.summary(), "compare": compare}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
-    return line
 
 
 def main():
@@ -394,7 +485,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=list(PRECISION))
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 and 32-object comparison runs")
+    ap.add_argument("--precision", default="fp16", choices=list(PRECISION))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -642,8 +642,9 @@ void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
 /* The library's internal draws, defined here from the generator (a reading;
  * the paper does not say how it draws its uniforms):
  *   key = (seed low 32 bits, seed high 32 bits);
- *   xi_{r,k} = word (k mod 4) of Philox(ctr = (r, k div 4, step, 2 obj)) >> 8, times 2^-24;
- *   u_{r,k}  = ((float)k + xi) / (float)Nr in IEEE single precision (stratified);
+ *   xi_{r,k} = word (k mod 4) of Philox(ctr = (r, k div 4, step, 2 obj)) >> 15, times 2^-17;
+ *   u_{r,k}  = ((float)k + xi) / (float)Nr in IEEE single precision (stratified; with 17
+ *              random bits k + xi is exact for k < 128, so u stays below 1);
  *   C_rand_r = words 0..2 of Philox(ctr = (r, 0, step, 2 obj + 1)) >> 8, times 2^-24. */
 void orc_philox_uniforms(uint64_t seed, uint32_t step, uint32_t obj, int n, int Nr, float *u)
 {
@@ -653,7 +654,8 @@ void orc_philox_uniforms(uint64_t seed, uint32_t step, uint32_t obj, int n, int 
             uint32_t ctr[4] = {(uint32_t)r, (uint32_t)(k >> 2), step, 2u * obj};
             uint32_t out[4];
             orc_philox4x32_10(ctr, key, out);
-            float xi = (float)(out[k & 3] >> 8) * 5.9604644775390625e-8f;
+            /* 17 random bits: k + xi is exact in FP32 for k < 128, so u < 1 */
+            float xi = (float)(out[k & 3] >> 15) * 7.62939453125e-06f;
             volatile float num = (float)k + xi;
             u[(int64_t)r * Nr + k] = num / (float)Nr;
         }

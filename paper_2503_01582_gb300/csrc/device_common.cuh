@@ -34,14 +34,16 @@ __device__ __forceinline__ uint32_t pick(uint4 v, int i)
     return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
-// Stratified uniform u_{r,k} = (k + xi) / nr in IEEE single precision, xi from
-// word k mod 4 of Philox(ctr = (ray, k div 4, step, 2 obj), key = seed).
+// Stratified uniform u_{r,k} = (k + xi) / nr in IEEE single precision, xi the
+// top 17 bits of word k mod 4 of Philox(ctr = (ray, k div 4, step, 2 obj),
+// key = seed) times 2^-17: k + xi is then exact for k < 128, so u < 1.
 __device__ __forceinline__ float philox_uniform(uint64_t seed, uint32_t step, uint32_t obj, uint32_t ray,
                                                 int k, int nr)
 {
     const uint4 o = philox4x32_10(make_uint4(ray, (uint32_t)k >> 2, step, 2u * obj),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-    return __fdiv_rn(__fadd_rn((float)k, u24(pick(o, k & 3))), (float)nr);
+    const float xi = (float)(pick(o, k & 3) >> 15) * 7.62939453125e-06f;
+    return __fdiv_rn(__fadd_rn((float)k, xi), (float)nr);
 }
 
 // Background colour C_rand of a ray: words 0..2 of Philox(ctr = (ray, 0, step, 2 obj + 1)).

@@ -286,7 +286,8 @@ __device__ __forceinline__ void sample_ray_warp(const ObjDesc &od, const BatchDe
     for (int q = 0; q < Q; ++q) {
         const int k = lane * Q + q;
         if (k < nr) {
-            const float u = bd.u ? bd.u[(size_t)gr * nr + k] : philox_uniform(bd.seed, bd.step, bd.obj_id, gr, k, nr);
+            float u = bd.u ? bd.u[(size_t)gr * nr + k] : philox_uniform(bd.seed, bd.step, bd.obj_id, gr, k, nr);
+            u = fminf(fmaxf(u, 0.f), 0x1.fffffep-1f);  // a caller's uniform outside [0, 1) is clamped
             int lo = 0, hi = nc - 1;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
@@ -296,7 +297,7 @@ __device__ __forceinline__ void sample_ray_warp(const ObjDesc &od, const BatchDe
                     lo = mid + 1;
             }
             const float c0 = cdf[lo], c1 = cdf[lo + 1];
-            const float frac = __fdiv_rn(u - c0, c1 - c0);
+            const float frac = c1 > c0 ? fminf(__fdiv_rn(u - c0, c1 - c0), 1.f) : 0.f;
             const float t = __fmaf_rn((float)lo + frac, delta, tn);
             ts[r * nr + k] = t;
             if (bd.out_t)

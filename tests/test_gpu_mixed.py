@@ -127,6 +127,52 @@ def test_mixed_training_tracks_fp32(pkg, precision):
     ctx.close()
 
 
+def test_equal_error_after_training(pkg):
+    """The metric compares forms at equal error: after the same training
+    budget, the mixed-precision forms' held-out colour MSE (all pixels; the
+    target of a background pixel is black) and depth L1 (object pixels) are
+    within max(5 %, 2 x the FP32 seed-to-seed std) of the FP32 form's."""
+    import torch
+    from helpers import pool_cfg1
+    from synth import cameras_on_sphere, init_params, make_ray_pool, sample_batch
+
+    sc, pool = pool_cfg1()
+    held = make_ray_pool(sc, cameras_on_sphere(4, 2.0, 40, 64, 64, 99), 4096, 99)
+    hb = {k: torch.from_numpy(np.ascontiguousarray(getattr(held, k))).cuda() for k in ("o", "d")}
+    tgt_rgb = np.where(held.is_obj[:, None] == 1, held.rgb, 0.0)
+    objm = held.is_obj == 1
+    a = orc.Arch(**CFG1)
+    from synth import prior_grid
+
+    grid = prior_grid(sc, 32, 0)
+    metrics = {0: [], 1: [], 2: []}
+    for seed in range(3):
+        theta = init_params(orc.n_hash_params(a), a.mlp_shapes(), 40 + seed)
+        for precision in (0, 1, 2):
+            ctx = pkg.Context(seed=seed)
+            obj = ctx.create_object(_arch(pkg, CFG1, precision), theta)
+            ctx.set_prior_grid(obj, grid)
+            opts = pkg.make_opts(nc=32, nr=32, lr=1e-2)
+            for step in range(300):
+                rays = sample_batch(pool, 256, 1000 * seed + step)
+                ctx.train_step([_dev(rays, obj)], opts)
+            out = ctx.render(dict(hb, obj=obj), opts)
+            rgb = out["rgb"].cpu().numpy()
+            depth = out["depth"].cpu().numpy()
+            bad = np.nonzero(~np.isfinite(rgb).all(1))[0]
+            assert bad.size == 0, (seed, precision, bad.size, bad[:5], held.o[bad[:2]], held.d[bad[:2]])
+            metrics[precision].append((float(np.mean((rgb - tgt_rgb) ** 2)),
+                                       float(np.mean(np.abs(depth - held.depth)[objm]))))
+            ctx.close()
+    ref = np.array(metrics[0])
+    tol = np.maximum(0.05 * ref.mean(0), 2 * ref.std(0))
+    for precision in (1, 2):
+        m = np.array(metrics[precision]).mean(0)
+        print(f"\nprecision={precision}: colour MSE {m[0]:.5f} depth L1 {m[1]:.5f}; FP32 {ref.mean(0)[0]:.5f} "
+              f"{ref.mean(0)[1]:.5f} (tolerance {tol[0]:.5f}, {tol[1]:.5f})")
+        assert np.all(np.abs(m - ref.mean(0)) <= tol)
+
+
 def test_mixed_full_size_sampled(pkg):
     """The full-size object (L=16, T=2^19, 2x64 MLP) in BF16 at 4096 rays x 64
     samples: sampled rays' outputs against the oracle."""
