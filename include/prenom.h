@@ -27,8 +27,10 @@
  *
  * Parameter vector layout of one object (what prenom_get_state copies):
  * hash tables level by level, each level entry-major with F features per
- * entry, then one row-major (out x in) matrix per MLP layer:
- * W_1 [W][L*F], W_2 .. W_H [W][W], W_out [4][W]; no biases.
+ * entry and padded to a multiple of 8 entries (prenom_level_info gives the
+ * offsets; padding entries are never read and never change), then one
+ * row-major (out x in) matrix per MLP layer: W_1 [W][L*F], W_2 .. W_H [W][W],
+ * W_out [4][W]; no biases.
  */
 #ifndef PRENOM_H
 #define PRENOM_H
@@ -207,7 +209,8 @@ PRENOM_API int prenom_render(prenom_ctx *ctx, const prenom_ray_batch *batch, con
 
 /* Adjoint of prenom_render for upstream gradients d_out [n][5] (dL/dC[3],
  * dL/dD, dL/dA per ray, device): adds dL/dtheta into grad (device,
- * param_count floats, caller-owned, accumulated, not zeroed). */
+ * param_count floats, caller-owned, accumulated, not zeroed, 16-byte aligned
+ * or PRENOM_ERR_INVALID_ARG). */
 PRENOM_API int prenom_render_backward(prenom_ctx *ctx, const prenom_ray_batch *batch,
                            const prenom_train_opts *opts, const float *d_out, float *grad);
 
@@ -249,7 +252,8 @@ PRENOM_API int prenom_kernel_time(prenom_ctx *ctx, int32_t kernel, double *total
  *   arch       architecture (same rules as prenom_create_object); objects with
  *              more than PRENOM_NOALLOC_MAX_PARAMS parameters are rejected
  *              with PRENOM_ERR_INVALID_ARG
- *   theta      device, param_count floats, updated in place (layout above)
+ *   theta      device, param_count floats, updated in place (layout above),
+ *              16-byte aligned (else PRENOM_ERR_INVALID_ARG)
  *   adam_m, adam_v  device, param_count floats each, updated in place (zero
  *              before the first step)
  *   step       Adam steps already taken (this call performs step + 1)

@@ -51,11 +51,14 @@ int64_t orc_level_entries(const orc_arch *a, int l)
     return orc_level_dense(a, l) ? level_vertices(a, l) : ((int64_t)1 << a->log2T);
 }
 
+/* Storage layout (not part of the method): each level's table occupies its
+ * entry count rounded up to a multiple of 8 entries, so every level starts
+ * on a 64-byte boundary; the padding entries are never addressed. */
 int64_t orc_level_offset(const orc_arch *a, int l)
 {
     int64_t off = 0;
     for (int i = 0; i < l; ++i)
-        off += orc_level_entries(a, i) * a->F;
+        off += (orc_level_entries(a, i) + 7) / 8 * 8 * a->F;
     return off;
 }
 

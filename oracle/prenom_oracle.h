@@ -22,8 +22,8 @@
  *
  * Parameter vector layout (shared by contract with the library's interface,
  * not by code): hash tables level by level, entry-major with F features per
- * entry, then one row-major (out x in) matrix per MLP layer: W_1 [W][L*F],
- * W_2..W_H [W][W], W_out [4][W].
+ * entry, each level padded to a multiple of 8 entries, then one row-major
+ * (out x in) matrix per MLP layer: W_1 [W][L*F], W_2..W_H [W][W], W_out [4][W].
  */
 #ifndef PRENOM_ORACLE_H
 #define PRENOM_ORACLE_H

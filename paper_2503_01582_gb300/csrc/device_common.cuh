@@ -177,6 +177,51 @@ __device__ __forceinline__ void red_add_f2(float2 *p, float a, float b)
     asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(__cvta_generic_to_global(p)), "f"(a), "f"(b));
 }
 
+__device__ __forceinline__ void red_add_f4(float4 *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(p)), "f"(a),
+                 "f"(b), "f"(c), "f"(d));
+}
+
+// Corners 2j and 2j+1 differ only in x.  When their entries differ only in
+// bit 0 they share one 16-byte-aligned pair of entries (every level starts on
+// a multiple of 8 two-feature entries and the table base is 16-byte aligned),
+// so one 16-byte access serves both.  At hashed levels this holds for every
+// even x (the x prime is 1); at dense levels for every even flat index.
+__device__ __forceinline__ void gather_pair(const float2 *tab, uint32_t i0, uint32_t i1, float2 &f0, float2 &f1)
+{
+    if ((i0 ^ i1) == 1u) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(tab + (i0 & ~1u)));
+        const bool first = (i0 & 1u) == 0u;
+        f0 = first ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
+        f1 = first ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+    } else {
+        f0 = __ldg(tab + i0);
+        f1 = __ldg(tab + i1);
+    }
+}
+
+// Adds (w0 g0, w0 g1) to entry i0 and (w1 g0, w1 g1) to entry i1; a corner of
+// zero weight adds nothing (an exact zero where the pair is one access).
+__device__ __forceinline__ void scatter_pair(float2 *gtab, uint32_t i0, uint32_t i1, float w0, float w1, float g0,
+                                             float g1)
+{
+    const float a0 = w0 != 0.f ? w0 * g0 : 0.f, a1 = w0 != 0.f ? w0 * g1 : 0.f;
+    const float b0 = w1 != 0.f ? w1 * g0 : 0.f, b1 = w1 != 0.f ? w1 * g1 : 0.f;
+    if ((i0 ^ i1) == 1u) {
+        if (w0 != 0.f || w1 != 0.f) {
+            const bool first = (i0 & 1u) == 0u;
+            red_add_f4(reinterpret_cast<float4 *>(gtab + (i0 & ~1u)), first ? a0 : b0, first ? a1 : b1,
+                       first ? b0 : a0, first ? b1 : a1);
+        }
+    } else {
+        if (w0 != 0.f)
+            red_add_f2(gtab + i0, a0, a1);
+        if (w1 != 0.f)
+            red_add_f2(gtab + i1, b0, b1);
+    }
+}
+
 __device__ __forceinline__ void red_add_f(float *p, float a)
 {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(a));

@@ -15,7 +15,8 @@
 //      with shuffle scans (prefix for transmittance, suffix for the adjoint);
 //   5. MLP backward: dW accumulated in shared memory across all tiles of the
 //      CTA (flushed once with atomics at the end), dX by GEMM;
-//   6. hash-grid scatter of dX with vector float2 atomics.
+//   6. hash-grid scatter of dX with vector reductions (one 16-byte reduction
+//      for an x-adjacent corner pair that shares an aligned entry pair).
 #pragma once
 
 #include "device_common.cuh"
@@ -352,8 +353,8 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
         if constexpr (!SCATTER) {
             float2 f[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                f[c] = __ldg(tab + lv.offset + cs.idx[c]);
+            for (int c = 0; c < 8; c += 2)
+                gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
             float e0 = 0.f, e1 = 0.f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -365,11 +366,8 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
         } else {
             const float g0 = XT[(2 * l) * SP + s], g1 = XT[(2 * l + 1) * SP + s];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float w = cs.wt[c];
-                if (w != 0.f)
-                    red_add_f2(gtab + lv.offset + cs.idx[c], w * g0, w * g1);
-            }
+            for (int c = 0; c < 8; c += 2)
+                scatter_pair(gtab + lv.offset, cs.idx[c], cs.idx[c + 1], cs.wt[c], cs.wt[c + 1], g0, g1);
         }
     }
 }

@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                     level_corners(lv, od.tmask, ph, pl, cs);
                     float2 f[8];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        f[c] = __ldg(tab + lv.offset + cs.idx[c]);
+                    for (int c = 0; c < 8; c += 2)
+                        gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
                     float e0 = 0.f, e1 = 0.f;
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -602,11 +602,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                     level_corners(lv, od.tmask, ph, pl, cs);
                     const float g0 = g[2 * j] * inv_scale, g1 = g[2 * j + 1] * inv_scale;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float w = cs.wt[c];
-                        if (w != 0.f)
-                            red_add_f2(gtab + lv.offset + cs.idx[c], w * g0, w * g1);
-                    }
+                    for (int c = 0; c < 8; c += 2)
+                        scatter_pair(gtab + lv.offset, cs.idx[c], cs.idx[c + 1], cs.wt[c], cs.wt[c + 1], g0, g1);
                 }
             }
         }

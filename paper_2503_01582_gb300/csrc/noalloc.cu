@@ -52,6 +52,8 @@ extern "C" int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!theta || !adam_m || !adam_v || !batch || !opts)
         return err(PRENOM_ERR_INVALID_ARG, "noalloc step: theta, adam_m, adam_v, batch and opts are required");
+    if (reinterpret_cast<uintptr_t>(theta) % 16 != 0)
+        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: theta is not 16-byte aligned");
     if (step < 0)
         return err(PRENOM_ERR_INVALID_ARG, "noalloc step: step %lld < 0", step);
     if (opts->nr < kMinNr || opts->nr > kMaxNr || opts->nc < 1 || opts->nc > kMaxNc)

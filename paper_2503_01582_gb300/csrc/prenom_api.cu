@@ -109,7 +109,9 @@ void level_geometry(const prenom_arch &a, Object &o)
         const int64_t v = (int64_t)(N + 1) * (N + 1) * (N + 1);
         o.res[l] = N;
         o.dense[l] = v <= T;
-        o.off[l + 1] = o.off[l] + (o.dense[l] ? v : T) * a.F;
+        // each level padded to a multiple of 8 entries: levels start 64-byte
+        // aligned, so an aligned pair of entries is one 16-byte access
+        o.off[l + 1] = o.off[l] + ((o.dense[l] ? v : T) + 7) / 8 * 8 * a.F;
     }
     o.n_hash = o.off[a.L];
     o.IN = a.L * a.F;
@@ -968,6 +970,8 @@ int prenom_render_backward(prenom_ctx *c, const prenom_ray_batch *b, const preno
         return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
     if (!b || !grad || (b->n_rays > 0 && !d_out))
         return fail(c, PRENOM_ERR_INVALID_ARG, "batch, d_out and grad are required");
+    if (reinterpret_cast<uintptr_t>(grad) % 16 != 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "grad is not 16-byte aligned");
     int rc = check_opts(c, op, false);
     if (rc || (rc = check_batch(c, *b, false)))
         return rc;

@@ -354,11 +354,18 @@ def test_full_size_config_sampled(pkg):
     grid = prior_grid(sc, 64, 0)
     theta = init_params(orc.n_hash_params(a), a.mlp_shapes(), 3, hash_range=0.5)
     ctx, obj = _setup(pkg, arch, theta, grid)
-    b = _dev(rays, obj, u, cr)
-    out = ctx.render(b, pkg.make_opts(nc=64, nr=64))
     idx = np.random.default_rng(0).choice(4096, 48, replace=False)
     sub = {k: v[idx] for k, v in rays.items()}
-    want = orc.batch(a, theta, grid, sub, 64, 64, u=u[idx], c_rand=cr[idx])
+    # the sampler over the whole batch: bins of the sampled rays exact outside the edge margin
+    out = ctx.render(_dev(rays, obj, u, cr), pkg.make_opts(nc=64, nr=64), want_samples=True)
+    ws = oracle_samples(grid, sub, u[idx], 64, 64)
+    bad, _ = bins_match(out["bins"].cpu().numpy()[idx], ws["bins"], ws["cdf"], u[idx])
+    assert bad == 0
+    # field and rendering over the whole batch on identical samples: at the finest
+    # level (n_max 2048) one FP32 ulp of t already moves a feature by ~1e-5
+    t_all = oracle_t(grid, rays, u, 64, 64)
+    out = ctx.render(_dev(rays, obj, cr=cr, t_in=t_all), pkg.make_opts(nc=64, nr=64))
+    want = orc.batch(a, theta, grid, sub, 64, 64, t_in=t_all[idx], c_rand=cr[idx])
     for k in ("rgb", "depth", "acc"):
         assert rel(out[k].cpu().numpy()[idx], want[k]) <= FWD_TOL, k
     # gradients of a 64-ray batch at full architecture size

@@ -32,11 +32,16 @@ def test_dense_hashed_split_and_sizes(orc):
     # cfg 1: (17^3 = 4913) and (24^3 = 13824) fit in 2^14 = 16384; 36^3 = 46656 does not
     a = orc.Arch(**CFG1)
     assert [orc.level_dense(a, l) for l in range(8)] == [True, True] + [False] * 6
-    assert orc.n_hash_params(a) == 2 * (4913 + 13824 + 6 * 16384)
+    assert [orc.level_entries(a, l) for l in range(2)] == [4913, 13824]
+    # storage pads every level to a multiple of 8 entries: 4913 -> 4920
+    assert orc.n_hash_params(a) == 2 * (4920 + 13824 + 6 * 16384)
+    assert [orc.level_offset(a, l) for l in range(3)] == [0, 2 * 4920, 2 * (4920 + 13824)]
     # cfg 2: 17^3, 23^3, 31^3, 43^3, 59^3 fit in 2^19; 81^3 = 531441 > 524288
     a2 = orc.Arch(**CFG2)
     assert [orc.level_dense(a2, l) for l in range(16)] == [True] * 5 + [False] * 11
-    assert orc.n_hash_params(a2) == 2 * (4913 + 12167 + 29791 + 79507 + 205379 + 11 * 524288)
+    assert [orc.level_entries(a2, l) for l in range(5)] == [4913, 12167, 29791, 79507, 205379]
+    assert orc.n_hash_params(a2) == 2 * (4920 + 12168 + 29792 + 79512 + 205384 + 11 * 524288)
+    assert all(orc.level_offset(a2, l) % 16 == 0 for l in range(17))  # 8 entries x 2 features
     # MLP: 32->64, 64->64, 64->4 without biases
     assert orc.n_mlp_params(a2) == 32 * 64 + 64 * 64 + 4 * 64
     assert orc.param_count(a2) == orc.n_hash_params(a2) + 6400
