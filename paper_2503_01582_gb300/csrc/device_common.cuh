@@ -119,6 +119,7 @@ __device__ __forceinline__ uint32_t grid_index(bool dense, uint32_t n1, uint32_t
 struct Corners {
     uint32_t idx[8];
     float wt[8];
+    int cell[3];  // lower corner of the cell
 };
 
 __device__ __forceinline__ void level_corners(const LevelDesc &lv, uint32_t tmask, const float (&ph)[3],
@@ -129,6 +130,9 @@ __device__ __forceinline__ void level_corners(const LevelDesc &lv, uint32_t tmas
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         level_cell(ph[a], pl[a], lv.res, c[a], w[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        cs.cell[a] = c[a];
     const bool dense = lv.dense != 0;
     const uint32_t n1 = (uint32_t)lv.res + 1u;
 #pragma unroll
@@ -201,24 +205,66 @@ __device__ __forceinline__ void gather_pair(const float2 *tab, uint32_t i0, uint
     }
 }
 
-// Adds (w0 g0, w0 g1) to entry i0 and (w1 g0, w1 g1) to entry i1; a corner of
-// zero weight adds nothing (an exact zero where the pair is one access).
-__device__ __forceinline__ void scatter_pair(float2 *gtab, uint32_t i0, uint32_t i1, float w0, float w1, float g0,
-                                             float g1)
+// Adds (a0, a1) to entry i0 and (b0, b1) to entry i1, skipping an entry whose
+// two addends are zero (an exact zero where the pair is one access).
+__device__ __forceinline__ void scatter_pair(float2 *gtab, uint32_t i0, uint32_t i1, float a0, float a1, float b0,
+                                             float b1)
 {
-    const float a0 = w0 != 0.f ? w0 * g0 : 0.f, a1 = w0 != 0.f ? w0 * g1 : 0.f;
-    const float b0 = w1 != 0.f ? w1 * g0 : 0.f, b1 = w1 != 0.f ? w1 * g1 : 0.f;
+    const bool ua = a0 != 0.f || a1 != 0.f, ub = b0 != 0.f || b1 != 0.f;
     if ((i0 ^ i1) == 1u) {
-        if (w0 != 0.f || w1 != 0.f) {
+        if (ua || ub) {
             const bool first = (i0 & 1u) == 0u;
             red_add_f4(reinterpret_cast<float4 *>(gtab + (i0 & ~1u)), first ? a0 : b0, first ? a1 : b1,
                        first ? b0 : a0, first ? b1 : a1);
         }
     } else {
-        if (w0 != 0.f)
+        if (ua)
             red_add_f2(gtab + i0, a0, a1);
-        if (w1 != 0.f)
+        if (ub)
             red_add_f2(gtab + i1, b0, b1);
+    }
+}
+
+// Hash-grid scatter of one level for the 32 samples of a warp (all lanes call
+// it together; inactive lanes add nothing).  dL/d(entry) of corner c is the sum
+// over samples of w_c(x) (g0, g1).  Samples of a ray sit in depth order in
+// consecutive lanes, so at coarse levels runs of lanes share one cell: a
+// segmented warp scan sums each run first and only the run's last lane issues
+// the reductions, which removes about half of the global reductions over a
+// 16-level grid.  A corner of zero weight adds nothing.
+__device__ __forceinline__ void scatter_level_warp(float2 *gtab, bool active, const Corners &cs, float g0, float g1,
+                                                   int lane)
+{
+    const int k0 = active ? cs.cell[0] : -1 - lane;  // inactive lanes match no neighbour
+    const int k1 = active ? cs.cell[1] : 0, k2 = active ? cs.cell[2] : 0;
+    const int p0 = __shfl_up_sync(kFull, k0, 1), p1 = __shfl_up_sync(kFull, k1, 1), p2 = __shfl_up_sync(kFull, k2, 1);
+    const bool head = lane == 0 || p0 != k0 || p1 != k1 || p2 != k2;
+    const uint32_t heads = __ballot_sync(kFull, head);
+    const uint32_t upto = 0xffffffffu >> (31 - lane);  // lanes 0..lane
+    const int pos = lane - (31 - __clz(heads & upto));  // position in the run
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) != 0u;
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const bool use = active && cs.wt[c] != 0.f;
+        v[2 * c] = use ? cs.wt[c] * g0 : 0.f;
+        v[2 * c + 1] = use ? cs.wt[c] * g1 : 0.f;
+    }
+    if (heads != 0xffffffffu) {
+        const int maxpos = (int)__reduce_max_sync(kFull, (unsigned)pos);
+        for (int d = 1; d <= maxpos; d <<= 1) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float up = __shfl_up_sync(kFull, v[q], d);
+                if (pos >= d)
+                    v[q] += up;
+            }
+        }
+    }
+    if (active && tail) {
+#pragma unroll
+        for (int c = 0; c < 8; c += 2)
+            scatter_pair(gtab, cs.idx[c], cs.idx[c + 1], v[2 * c], v[2 * c + 1], v[2 * c + 2], v[2 * c + 3]);
     }
 }
 

@@ -15,8 +15,9 @@
 //      with shuffle scans (prefix for transmittance, suffix for the adjoint);
 //   5. MLP backward: dW accumulated in shared memory across all tiles of the
 //      CTA (flushed once with atomics at the end), dX by GEMM;
-//   6. hash-grid scatter of dX with vector reductions (one 16-byte reduction
-//      for an x-adjacent corner pair that shares an aligned entry pair).
+//   6. hash-grid scatter of dX: runs of lanes in one cell summed by a
+//      segmented warp scan, then vector reductions (one 16-byte reduction for
+//      an x-adjacent corner pair that shares an aligned entry pair).
 #pragma once
 
 #include "device_common.cuh"
@@ -321,9 +322,11 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
     constexpr int SP = S + 4;
     constexpr int PARTS = kThreads / S;
     constexpr int L = IN / 2;
+    static_assert(S % 32 == 0, "a warp holds consecutive samples of one part");
     const int s = threadIdx.x % S, part = threadIdx.x / S;
-    if (s >= ns) {
-        if constexpr (!SCATTER) {
+    const bool active = s < ns;
+    if constexpr (!SCATTER) {
+        if (!active) {
             for (int l = part; l < L; l += PARTS) {
                 XT[(2 * l) * SP + s] = 0.f;
                 XT[(2 * l + 1) * SP + s] = 0.f;
@@ -333,16 +336,17 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
                 for (int c = 0; c < 4; ++c)
                     dOT[c * SP + s] = 0.f;
             }
+            return;
         }
-        return;
     }
-    const int r = s / bd.nr;
-    const float *rf = rayf + r * kRayStride;
-    const float t = ts[s];
-    float ph[3], pl[3];
+    float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
+    if (active) {  // in the scatter, inactive lanes stay with their warp and add nothing
+        const float *rf = rayf + (s / bd.nr) * kRayStride;
+        const float t = ts[s];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        pos_two_float(rf[RF_O + a], t, rf[RF_D + a], ph[a], pl[a]);
+        for (int a = 0; a < 3; ++a)
+            pos_two_float(rf[RF_O + a], t, rf[RF_D + a], ph[a], pl[a]);
+    }
     const float2 *tab = reinterpret_cast<const float2 *>(od.theta);
     float2 *gtab = reinterpret_cast<float2 *>(od.grad);
 #pragma unroll 2
@@ -364,10 +368,8 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
             XT[(2 * l) * SP + s] = e0;
             XT[(2 * l + 1) * SP + s] = e1;
         } else {
-            const float g0 = XT[(2 * l) * SP + s], g1 = XT[(2 * l + 1) * SP + s];
-#pragma unroll
-            for (int c = 0; c < 8; c += 2)
-                scatter_pair(gtab + lv.offset, cs.idx[c], cs.idx[c + 1], cs.wt[c], cs.wt[c + 1], g0, g1);
+            const float g0 = active ? XT[(2 * l) * SP + s] : 0.f, g1 = active ? XT[(2 * l + 1) * SP + s] : 0.f;
+            scatter_level_warp(gtab + lv.offset, active, cs, g0, g1, threadIdx.x & 31);
         }
     }
 }

@@ -582,29 +582,27 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int j = 0; j < 8; ++j)
                     g[j] = g8[j];
             }
-            if (s < ns) {
-                const int r = s / nr;
-                const float *rf = rayf + r * kRayStride;
+            const bool active = s < ns;  // the whole warp scatters together
+            float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
+            if (active) {
+                const float *rf = rayf + (s / nr) * kRayStride;
                 const float t = ts[s];
-                float ph[3], pl[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
                     pos_two_float(rf[RF_O + a], t, rf[RF_D + a], ph[a], pl[a]);
-                float2 *gtab = reinterpret_cast<float2 *>(od.grad);
-                const int l0 = half * (INP / 4);
+            }
+            float2 *gtab = reinterpret_cast<float2 *>(od.grad);
+            const int l0 = half * (INP / 4);
 #pragma unroll
-                for (int j = 0; j < INP / 4; ++j) {
-                    const int l = l0 + j;
-                    if (l >= NL)
-                        break;
-                    const LevelDesc lv = od.lv[l];
-                    Corners cs;
-                    level_corners(lv, od.tmask, ph, pl, cs);
-                    const float g0 = g[2 * j] * inv_scale, g1 = g[2 * j + 1] * inv_scale;
-#pragma unroll
-                    for (int c = 0; c < 8; c += 2)
-                        scatter_pair(gtab + lv.offset, cs.idx[c], cs.idx[c + 1], cs.wt[c], cs.wt[c + 1], g0, g1);
-                }
+            for (int j = 0; j < INP / 4; ++j) {
+                const int l = l0 + j;
+                if (l >= NL)
+                    break;
+                const LevelDesc lv = od.lv[l];
+                Corners cs;
+                level_corners(lv, od.tmask, ph, pl, cs);
+                scatter_level_warp(gtab + lv.offset, active, cs, g[2 * j] * inv_scale, g[2 * j + 1] * inv_scale,
+                                   lane);
             }
         }
         tc_sync();
