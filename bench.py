@@ -288,20 +288,29 @@ def _time(stream, fn, steps, warmup, barrier=lambda: None, clocks=None):
     return ev0.elapsed_time(ev1)
 
 
-def _batched_workload(pkg, ctx, stream, precision, seed, theta_from=None):
-    """32 objects of the category table with random CSG shapes; rays per object
-    32 * round(8 * 2^(5 a)), a ~ U[0,1) (256..8192, a projected-area share),
-    48 samples per ray, 64^3 prior grids.  Four rotating ray sets."""
-    from synth import (cameras_on_sphere, make_ray_pool, prior_grid, random_colours, sample_batch,
-                       scene_random_csg, stratified_uniforms)
-
+def _batched_specs(pkg, precision, seed):
+    """(arch, rays) of the 32 objects: the category table's architectures, rays
+    per object 32 * round(8 * 2^(5 a)), a ~ U[0,1) (256..8192, a projected-area share)."""
     rng = np.random.default_rng(seed)
-    objs, sets, n_samples = [], [[], [], [], []], 0
+    specs = []
     for i in range(BATCHED_OBJECTS):
         log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
         rays = int(32 * round(8 * 2 ** (5 * rng.random())))
-        arch = pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
-                             lambda_sigma=1e-3, precision=PRECISION[precision])
+        specs.append((pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
+                                    lambda_sigma=1e-3, precision=PRECISION[precision]), rays))
+    return specs
+
+
+def _batched_workload(pkg, ctx, stream, precision, seed, theta_from=None, only=None):
+    """The 32 objects with random CSG shapes, 48 samples per ray, 64^3 prior
+    grids, four rotating ray sets; `only` restricts it to some object indices."""
+    from synth import (cameras_on_sphere, make_ray_pool, prior_grid, random_colours, sample_batch,
+                       scene_random_csg, stratified_uniforms)
+
+    objs, sets, n_samples = [], [[], [], [], []], 0
+    for i, (arch, rays) in enumerate(_batched_specs(pkg, precision, seed)):
+        if only is not None and i not in only:
+            continue
         sc = scene_random_csg(1000 * seed + i)
         init = None if theta_from is None else theta_from[i]
         obj = ctx.create_object(arch, init)
@@ -424,6 +433,32 @@ def run_ours(args):
                                      "ms_per_step": msl / nb, "form": "32 single-object FP32 steps"},
             "speedup": msl / msb}
         for o in objs16 + objs32:
+            ctx.destroy_object(o)
+
+    if world > 1 and not args.no_compare:
+        # the 32-object workload split over the ranks (longest processing time
+        # first on the per-object cost), one batched step per rank, no exchange
+        from paper_2503_01582_gb300.shard import object_cost, rank_objects
+
+        specs = _batched_specs(pkg, prec, 7)
+        costs = [object_cost(a.L, a.F, a.width, a.hidden, pkg.arch_param_count(a), r * BATCHED_NR,
+                             4 if prec == "fp32" else 2) for a, r in specs]
+        mine = rank_objects(costs, world, rank)
+        objs, sets, n_mine = _batched_workload(pkg, ctx, stream, prec, 7, only=set(mine))
+        bopts = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2)
+        lossb = torch.zeros(max(len(objs), 1), device="cuda")
+        nb = max(args.steps // 20, 10)
+        fb = lambda i: ctx.train_step(sets[i % 4], bopts, lossb) if objs else None  # noqa: E731
+        msb = _time(stream, fb, nb, max(args.warmup, 6), barrier)
+        t = torch.tensor([msb], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        n_all = sum(r * BATCHED_NR for _, r in specs)
+        compare["batched_32_objects_sharded"] = {
+            "workload": "the 32-object batched workload split over %d GPUs by longest-processing-time "
+                        "first; %d samples per step in total" % (world, n_all),
+            "value": n_all * nb / (t.item() / 1e3), "unit": "samples/s", "ms_per_step": t.item() / nb,
+            "scaling": "strong"}
+        for o in objs:
             ctx.destroy_object(o)
 
     # ---- roofline of the dominant kernel (the fused training kernel)

@@ -166,6 +166,12 @@ PRENOM_API int prenom_destroy_object(prenom_ctx *ctx, int32_t obj);
 /* Number of floats in the object's parameter vector. */
 PRENOM_API int prenom_param_count(prenom_ctx *ctx, int32_t obj, size_t *n);
 
+/* Number of floats in the parameter vector of architecture arch (host
+ * pointer; the same rules as prenom_create_object, PRENOM_ERR_INVALID_ARG
+ * otherwise), without a context or any device work: for sizing caller-owned
+ * state (prenom_train_step_noalloc) and balancing objects across GPUs. */
+PRENOM_API int prenom_arch_param_count(const prenom_arch *arch, size_t *n);
+
 /* Level geometry of the hash grid, for checking the layout contract:
  * res[l] = N_l, offset[l] = float offset of level l in theta (l = 0..L;
  * offset[L] = offset of W_1), dense[l] = 1 if level l is stored densely. */

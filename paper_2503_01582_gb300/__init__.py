@@ -37,12 +37,17 @@ from ._abi import (  # noqa: F401
     prenom_train_opts,
 )
 
-__all__ = ["Context", "make_arch", "make_opts", "PrenomError"]
+__all__ = ["Context", "make_arch", "make_opts", "arch_param_count", "PrenomError"]
 
 
 def make_arch(L=8, F=2, log2T=14, n_min=16, n_max=256, width=32, hidden=2, precision=PRENOM_PRECISION_FP32,
               lambda_d=0.1, lambda_sigma=0.0) -> prenom_arch:
     return prenom_arch(L, F, log2T, n_min, n_max, width, hidden, precision, lambda_d, lambda_sigma)
+
+
+def arch_param_count(arch: prenom_arch) -> int:
+    """Parameters of an architecture (host query, no context or GPU needed)."""
+    return _abi.prenom_arch_param_count(arch)
 
 
 def make_opts(nc=32, nr=32, lr=1e-2, beta1=0.9, beta2=0.99, eps=1e-15, escape_eps=1e-4, flags=0,

@@ -73,6 +73,7 @@ _SIGS = {
     "prenom_create_object": (C.c_int, [_CTX, C.POINTER(prenom_arch), _P, C.POINTER(C.c_int32)]),
     "prenom_destroy_object": (C.c_int, [_CTX, C.c_int32]),
     "prenom_param_count": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_size_t)]),
+    "prenom_arch_param_count": (C.c_int, [C.POINTER(prenom_arch), C.POINTER(C.c_size_t)]),
     "prenom_level_info": (C.c_int, [_CTX, C.c_int32, _P, _P, _P]),
     "prenom_set_prior_grid": (C.c_int, [_CTX, C.c_int32, _P, C.c_int32]),
     "prenom_train_step": (C.c_int, [_CTX, C.POINTER(prenom_ray_batch), C.c_int32,
@@ -162,6 +163,12 @@ def prenom_destroy_object(ctx, obj: int):
 def prenom_param_count(ctx, obj: int) -> int:
     n = C.c_size_t()
     check(lib().prenom_param_count(ctx, obj, C.byref(n)), ctx)
+    return n.value
+
+
+def prenom_arch_param_count(arch: prenom_arch) -> int:
+    n = C.c_size_t()
+    check(lib().prenom_arch_param_count(C.byref(arch), C.byref(n)), None)
     return n.value
 
 

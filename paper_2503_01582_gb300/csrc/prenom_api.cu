@@ -841,6 +841,20 @@ int prenom_param_count(prenom_ctx *c, int32_t obj, size_t *n)
     return PRENOM_OK;
 }
 
+int prenom_arch_param_count(const prenom_arch *arch, size_t *n)
+{
+    if (!arch || !n)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "arch and n are required");
+    const int rc = check_arch(nullptr, arch);
+    if (rc)
+        return rc;
+    Object o;
+    o.arch = *arch;
+    level_geometry(*arch, o);
+    *n = (size_t)o.n;
+    return PRENOM_OK;
+}
+
 int prenom_level_info(prenom_ctx *c, int32_t obj, int32_t *res, int64_t *offset, int32_t *dense)
 {
     Object *o = get_obj(c, obj);

@@ -45,3 +45,23 @@ def test_package_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
                 assert "prenom_oracle" not in text, f
+
+
+def test_arch_param_count_matches_oracle_layout(orc):
+    """Host-only query of the library (no device work): the parameter count of
+    an architecture equals the oracle's for the same layout contract."""
+    import paper_2503_01582_gb300 as pkg
+    from paper_2503_01582_gb300 import build
+
+    build.build()
+    cases = [dict(L=8, F=2, log2T=14, n_min=16, n_max=256, width=32, hidden=2),
+             dict(L=16, F=2, log2T=19, n_min=16, n_max=2048, width=64, hidden=2),
+             dict(L=4, F=2, log2T=12, n_min=16, n_max=64, width=16, hidden=3),
+             dict(L=16, F=2, log2T=14, n_min=16, n_max=2048, width=16, hidden=1)]
+    for c in cases:
+        assert pkg.arch_param_count(pkg.make_arch(**c)) == orc.param_count(orc.Arch(**c)), c
+    import pytest
+
+    with pytest.raises(pkg.PrenomError) as e:
+        pkg.arch_param_count(pkg.make_arch(width=48))
+    assert e.value.code == -1
