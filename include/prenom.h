@@ -69,6 +69,10 @@ extern "C" {
 #define PRENOM_FLAG_NO_ADAM 1u      /* accumulate gradients, skip Adam (step count unchanged) */
 #define PRENOM_FLAG_CHECK_FINITE 2u /* synchronise and fail with NONFINITE on a NaN/inf loss (per-object path) */
 #define PRENOM_FLAG_NO_GRAPH 4u     /* batched steps: launch directly instead of replaying a captured graph */
+#define PRENOM_FLAG_FUSED 8u        /* mixed-precision training: one fused kernel per step instead of the
+                                       split form (sampling+encoding, tensor-core MLP, hash scatter as
+                                       three kernels); the results agree to rounding order */
+#define PRENOM_FLAG_SPLIT 16u       /* mixed-precision training: always the split form (not tuned) */
 
 /* prenom_get_state / prenom_set_state: which buffer */
 #define PRENOM_STATE_THETA 0
@@ -77,12 +81,14 @@ extern "C" {
 #define PRENOM_STATE_ADAM_V 3
 
 /* Kernel ids for the timing interface. */
-#define PRENOM_KERNEL_TRAIN 0  /* fused sample+encode+MLP+render+loss+backward */
+#define PRENOM_KERNEL_TRAIN 0  /* fused sample+encode+MLP+render+loss+backward (split form: MLP+render+loss+MLP backward) */
 #define PRENOM_KERNEL_ADAM 1   /* dense Adam over every parameter of the step's objects */
 #define PRENOM_KERNEL_RENDER 2 /* forward only */
 #define PRENOM_KERNEL_RENDER_BWD 3
 #define PRENOM_KERNEL_INIT 4   /* random parameter initialisation */
-#define PRENOM_N_KERNELS 5
+#define PRENOM_KERNEL_SAMPLE_ENCODE 5 /* split form: prior sampling + hash encoding */
+#define PRENOM_KERNEL_SCATTER 6       /* split form: hash-grid scatter of the encoding's gradient */
+#define PRENOM_N_KERNELS 7
 
 typedef struct prenom_ctx prenom_ctx; /* opaque; owns all device state */
 
@@ -188,17 +194,23 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * back-propagate into the object's gradient buffer; then one Adam step for
  * every distinct object named by the batches (unless PRENOM_FLAG_NO_ADAM).
  * Gradients are zeroed by the Adam step, so NO_ADAM steps accumulate.
- * n_batches > 1 is the batched form (§IV-A trains objects in parallel): the
- * batches are grouped by kernel variant (precision, width, encoding width)
- * and each group runs as ONE persistent launch over a work list spanning all
- * its objects; one Adam launch then updates every object.  The first calls of
- * a new group signature try several work-chunk sizes (tiles per CTA) and keep
- * the fastest; afterwards, on a non-default stream and with timing off, the
- * whole step is captured once per signature as a CUDA graph and replayed
- * (PRENOM_FLAG_NO_GRAPH disables the graph).  A batched step synchronises
- * with the step before the previous one (two staging buffers are in flight),
- * allocates its work-list buffers on first use and when they must grow, and
- * updates at most 128 objects.
+ * Several batches form the batched form (§IV-A trains objects in parallel):
+ * the batches are grouped by kernel variant (precision, width, encoding
+ * width) and each group runs as ONE persistent launch over a work list
+ * spanning all its objects (a mixed-precision group may instead run the split
+ * form: sampling + encoding, the tensor-core MLP and the hash scatter as three
+ * launches over the same list); one Adam launch then updates every object.
+ * A single batch takes the same path.  The first calls of a new group
+ * signature (one untimed call, then two rounds over the candidates) try the
+ * split form and several work-chunk sizes (tiles per CTA) and keep the
+ * fastest; afterwards,
+ * on a non-default stream and with timing off, the whole step is captured
+ * once per signature as a CUDA graph and replayed (PRENOM_FLAG_NO_GRAPH
+ * disables the graph).  A step synchronises with the step before the previous
+ * one (two staging buffers are in flight), allocates its work-list and split
+ * buffers on first use and when they must grow, and updates at most 128
+ * objects.  With PRENOM_FLAG_CHECK_FINITE the batches run one launch each,
+ * without tuning or graphs.
  * loss_dev: device [n_batches] floats receiving each batch's loss, or NULL.
  * Each object named must have a prior grid unless every batch naming it
  * gives t_in. */

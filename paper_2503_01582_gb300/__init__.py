@@ -17,11 +17,15 @@ from . import _abi
 from ._abi import (  # noqa: F401
     KERNEL_NAMES,
     PRENOM_FLAG_CHECK_FINITE,
+    PRENOM_FLAG_FUSED,
+    PRENOM_FLAG_SPLIT,
     PRENOM_FLAG_NO_ADAM,
     PRENOM_FLAG_NO_GRAPH,
     PRENOM_KERNEL_ADAM,
     PRENOM_KERNEL_RENDER,
     PRENOM_KERNEL_RENDER_BWD,
+    PRENOM_KERNEL_SAMPLE_ENCODE,
+    PRENOM_KERNEL_SCATTER,
     PRENOM_KERNEL_TRAIN,
     PRENOM_N_KERNELS,
     PRENOM_PRECISION_BF16,

@@ -25,6 +25,8 @@ PRENOM_PRECISION_BF16 = 2
 PRENOM_FLAG_NO_ADAM = 1
 PRENOM_FLAG_CHECK_FINITE = 2
 PRENOM_FLAG_NO_GRAPH = 4
+PRENOM_FLAG_FUSED = 8
+PRENOM_FLAG_SPLIT = 16
 
 PRENOM_STATE_THETA = 0
 PRENOM_STATE_GRAD = 1
@@ -36,8 +38,10 @@ PRENOM_KERNEL_ADAM = 1
 PRENOM_KERNEL_RENDER = 2
 PRENOM_KERNEL_RENDER_BWD = 3
 PRENOM_KERNEL_INIT = 4
-PRENOM_N_KERNELS = 5
-KERNEL_NAMES = ["train", "adam", "render", "render_bwd", "init"]
+PRENOM_KERNEL_SAMPLE_ENCODE = 5
+PRENOM_KERNEL_SCATTER = 6
+PRENOM_N_KERNELS = 7
+KERNEL_NAMES = ["train", "adam", "render", "render_bwd", "init", "sample_encode", "scatter"]
 
 
 class prenom_arch(C.Structure):

@@ -205,12 +205,10 @@ __device__ __forceinline__ void out_layer_fwd(const float *__restrict__ HTl, con
 // by a warp scan, sum_{j<=i} rho_term_j = 1 - exp(-s_i) (the telescoped form of
 // Eq. 5), CDF of Eq. 6, uniform CDF i/nc for escaping rays, then for each
 // uniform the first bin b with CDF(b+1) > u and a linear position inside it.
-__device__ __forceinline__ void sample_ray_warp(const ObjDesc &od, const BatchDesc &bd, int r, int gr, float *rf,
-                                                float *ts, float *cdf, int lane)
+// Slab intersection of the ray o + t d (t >= 0) with the unit cube: [tn, tf],
+// or tn = tf = 0 for a ray that misses it.
+__device__ __forceinline__ bool ray_box(const float (&o)[3], const float (&d)[3], float &tn, float &tf)
 {
-    const int nc = bd.nc, nr = bd.nr;
-    const float o[3] = {rf[RF_O], rf[RF_O + 1], rf[RF_O + 2]};
-    const float d[3] = {rf[RF_D], rf[RF_D + 1], rf[RF_D + 2]};
     float t0 = 0.f, t1 = INFINITY;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -224,7 +222,19 @@ __device__ __forceinline__ void sample_ray_warp(const ObjDesc &od, const BatchDe
         }
     }
     const bool hit = t1 > t0;
-    const float tn = hit ? t0 : 0.f, tf = hit ? t1 : 0.f;
+    tn = hit ? t0 : 0.f;
+    tf = hit ? t1 : 0.f;
+    return hit;
+}
+
+__device__ __forceinline__ void sample_ray_warp(const ObjDesc &od, const BatchDesc &bd, int r, int gr, float *rf,
+                                                float *ts, float *cdf, int lane)
+{
+    const int nc = bd.nc, nr = bd.nr;
+    const float o[3] = {rf[RF_O], rf[RF_O + 1], rf[RF_O + 2]};
+    const float d[3] = {rf[RF_D], rf[RF_D + 1], rf[RF_D + 2]};
+    float tn, tf;
+    const bool hit = ray_box(o, d, tn, tf);
     if (lane == 0) {
         rf[RF_TN] = tn;
         rf[RF_TF] = tf;
@@ -533,6 +543,43 @@ __device__ __forceinline__ void stage_item(const WorkItem &src, WorkItem &dst)
     for (int i = threadIdx.x; i < (int)(sizeof(WorkItem) / sizeof(int)); i += blockDim.x)
         d[i] = s[i];
     __syncthreads();
+}
+
+// A tile's ray data into shared memory (kRayStride floats per ray): four
+// threads per ray load the origin, the direction, the object targets and the
+// background colour in parallel, so the tile pays about one memory latency.
+__device__ __forceinline__ void load_ray_tile(const BatchDesc &bd, int ray0, int nrt, float *rayf)
+{
+    for (int i = threadIdx.x; i < nrt * 4; i += blockDim.x) {
+        const int r = i >> 2, f = i & 3, g = ray0 + r;
+        float *rf = rayf + r * kRayStride;
+        if (f < 2) {
+            const float *src = (f == 0 ? bd.o : bd.d) + (size_t)g * 3;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                rf[(f == 0 ? RF_O : RF_D) + a] = src[a];
+        } else if (bd.mode == kTrain) {
+            const bool obj = bd.is_obj[g] != 0;
+            if (f == 2) {
+                rf[RF_OBJ] = obj ? 1.f : 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    rf[RF_RGB + a] = obj ? bd.rgb[(size_t)g * 3 + a] : 0.f;
+                rf[RF_DEPTH] = obj ? bd.depth[g] : 0.f;
+            } else if (!obj) {
+                if (bd.c_rand) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        rf[RF_CR + a] = bd.c_rand[(size_t)g * 3 + a];
+                } else {
+                    const float3 c = philox_colour(bd.seed, bd.step, bd.obj_id, (uint32_t)g);
+                    rf[RF_CR] = c.x;
+                    rf[RF_CR + 1] = c.y;
+                    rf[RF_CR + 2] = c.z;
+                }
+            }
+        }
+    }
 }
 
 // Index of the work item owning launch-wide tile t (items sorted by tile_begin).

@@ -109,35 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nrt = min(NR, bd.n_rays - ray0);
         const int ns = nrt * nr;
         // (1) ray data
-        for (int i = tid; i < nrt; i += kThreads) {
-            const int g = ray0 + i;
-            float *rf = rayf + i * kRayStride;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                rf[RF_O + a] = bd.o[(size_t)g * 3 + a];
-                rf[RF_D + a] = bd.d[(size_t)g * 3 + a];
-            }
-            if (bd.mode == kTrain) {
-                const bool obj = bd.is_obj[g] != 0;
-                rf[RF_OBJ] = obj ? 1.f : 0.f;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    rf[RF_RGB + a] = obj ? bd.rgb[(size_t)g * 3 + a] : 0.f;
-                rf[RF_DEPTH] = obj ? bd.depth[g] : 0.f;
-                if (!obj) {
-                    if (bd.c_rand) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            rf[RF_CR + a] = bd.c_rand[(size_t)g * 3 + a];
-                    } else {
-                        const float3 c = philox_colour(bd.seed, bd.step, bd.obj_id, (uint32_t)g);
-                        rf[RF_CR] = c.x;
-                        rf[RF_CR + 1] = c.y;
-                        rf[RF_CR + 2] = c.z;
-                    }
-                }
-            }
-        }
+        load_ray_tile(bd, ray0, nrt, rayf);
         __syncthreads();
         // (2) sampling
         for (int r = warp; r < nrt; r += kThreads / 32)

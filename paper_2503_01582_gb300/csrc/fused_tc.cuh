@@ -232,7 +232,7 @@ __device__ __forceinline__ void tc_load_object(const ObjDesc &od, unsigned char 
 // warp quadrant q holds rows 16q .. 16q+15 in its lanes 0..15).
 template <int W, int IN>
 __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDesc &bd, uint32_t lane_base,
-                                                bool have_dw, float &dwo_acc, float &loss_acc, float inv_scale)
+                                                bool have_dw, float (&dwo_acc)[8], float &loss_acc, float inv_scale)
 {
     constexpr int INP = TcLayout<W, IN>::INP;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -244,9 +244,17 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
         return;
     const int H = od.H;
     float *gw = od.grad + od.mlp_off;
-    if (tid < 4 * W && dwo_acc != 0.f)
-        red_add_f(gw + IN * W + (H - 1) * W * W + tid, dwo_acc);
-    dwo_acc = 0.f;
+    {  // dW_out: slice 0 of each (output, 8-column) group holds its sums
+        constexpr int SL = kThreads / (W / 2);
+        const int pair = tid / SL;
+        const int o = pair / (W / 8), i0 = (pair % (W / 8)) * 8;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (tid % SL == 0 && dwo_acc[j] != 0.f)
+                red_add_f(gw + IN * W + (H - 1) * W * W + o * W + i0 + j, dwo_acc[j]);
+            dwo_acc[j] = 0.f;
+        }
+    }
     if (!have_dw)
         return;
     for (int l = 0; l < H; ++l) {
@@ -334,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint32_t parity = 0;
     bool ok = true;
     bool first_dw = true;
-    float dwo_acc = 0.f;  // dW_out entry (o, i) = (tid / W, tid % W) for tid < 4W
+    float dwo_acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dW_out entries of this thread's group
     float loss_acc = 0.f;
     float scale = 1.f, inv_scale = 1.f;
 
@@ -369,41 +377,40 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int nrt = min(NR, bd.n_rays - ray0);
         const int ns = nrt * nr;
         // ---- ray data and sampling (FP32, shared with the FP32 kernel)
-        for (int i = tid; i < nrt; i += kThreads) {
-            const int g = ray0 + i;
-            float *rf = rayf + i * kRayStride;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                rf[RF_O + a] = bd.o[(size_t)g * 3 + a];
-                rf[RF_D + a] = bd.d[(size_t)g * 3 + a];
-            }
-            if (bd.mode == kTrain) {
-                const bool obj = bd.is_obj[g] != 0;
-                rf[RF_OBJ] = obj ? 1.f : 0.f;
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    rf[RF_RGB + a] = obj ? bd.rgb[(size_t)g * 3 + a] : 0.f;
-                rf[RF_DEPTH] = obj ? bd.depth[g] : 0.f;
-                if (!obj) {
-                    if (bd.c_rand) {
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            rf[RF_CR + a] = bd.c_rand[(size_t)g * 3 + a];
-                    } else {
-                        const float3 c = philox_colour(bd.seed, bd.step, bd.obj_id, (uint32_t)g);
-                        rf[RF_CR] = c.x;
-                        rf[RF_CR + 1] = c.y;
-                        rf[RF_CR + 2] = c.z;
-                    }
+        load_ray_tile(bd, ray0, nrt, rayf);
+        __syncthreads();
+        const bool split = bd.sp_x != nullptr;  // sampling, encoding and scatter run in kernels of their own
+        if (split) {
+            for (int r = warp; r < nrt; r += kThreads / 32) {
+                float *rf = rayf + r * kRayStride;
+                if (lane == 0) {
+                    const float o[3] = {rf[RF_O], rf[RF_O + 1], rf[RF_O + 2]};
+                    const float d[3] = {rf[RF_D], rf[RF_D + 1], rf[RF_D + 2]};
+                    float tn, tf;
+                    ray_box(o, d, tn, tf);
+                    rf[RF_TN] = tn;
+                    rf[RF_TF] = tf;
                 }
+                for (int k = lane; k < nr; k += 32)
+                    ts[r * nr + k] = bd.sp_t[(size_t)(ray0 + r) * nr + k];
             }
+        } else {
+            for (int r = warp; r < nrt; r += kThreads / 32)
+                sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
         }
         __syncthreads();
-        for (int r = warp; r < nrt; r += kThreads / 32)
-            sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
-        __syncthreads();
         // ---- encoding -> XA (16-bit, interleaved [128][INP])
-        {
+        if (split) {  // the tile's image from the sampling-encoding kernel; rows past the samples zeroed
+            const uint4 *src = bd.sp_x + (size_t)tile * (kSplitXBytes / 16);
+            for (int i = tid; i < kTcTile * INP * 2 / 16; i += kThreads) {
+                const int row = ((i >> 3) / (INP >> 3)) * 8 + (i & 7);
+                reinterpret_cast<uint4 *>(XA)[i] = row < ns ? src[i] : make_uint4(0u, 0u, 0u, 0u);
+            }
+            if (tid < kTcTile && tid >= ns)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dOT[c * SP + tid] = 0.f;
+        } else {
             const int s = tid % kTcTile, part = tid / kTcTile;
             if (s >= ns) {
                 for (int l = part; l < INP / 2; l += 2)
@@ -504,14 +511,33 @@ __global__ void __launch_bounds__(kThreads, 2)
                   Hf::finite(hi >> 16)) && bd.overflow)
                 atomicExch(bd.overflow, 1);
         }
-        if (tid < 4 * W) {
-            const int o = tid / W, i = tid % W;
+        {  // dW_out[o][i0..i0+7] over the tile's samples: each thread sums an interleaved slice
+            // of the samples (conflict-free 16-byte rows of H), the slices meet by shuffles
+            constexpr int SL = kThreads / (W / 2);  // slices per output group (8, 16, 32 for W = 64, 32, 16)
+            const int pair = tid / SL, slice = tid % SL;
+            const int o = pair / (W / 8), i0 = (pair % (W / 8)) * 8;
             const unsigned char *hl = HA + (H - 1) * L::ha;
-            float acc = 0.f;
-            for (int s = 0; s < kTcTile; ++s)
-                acc = fmaf(dOT[o * SP + s], Hf::value(*reinterpret_cast<const uint16_t *>(hl + il_off(s, i, W))),
-                           acc);
-            dwo_acc += acc;
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int k = 0; k < kTcTile / SL; ++k) {
+                const int s = k * SL + slice;
+                const float d = dOT[o * SP + s];
+                const uint4 hv = *reinterpret_cast<const uint4 *>(hl + il_off(s, i0, W));
+                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[2 * j] = fmaf(d, Hf::value((uint16_t)(hw[j] & 0xFFFFu)), acc[2 * j]);
+                    acc[2 * j + 1] = fmaf(d, Hf::value((uint16_t)(hw[j] >> 16)), acc[2 * j + 1]);
+                }
+            }
+#pragma unroll
+            for (int off = SL / 2; off > 0; off >>= 1)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[j] += __shfl_xor_sync(kFull, acc[j], off);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                dwo_acc[j] += acc[j];  // meaningful in slice 0 of each group
         }
         tc_sync();
         // ---- backward through the hidden layers
@@ -583,6 +609,18 @@ __global__ void __launch_bounds__(kThreads, 2)
                     g[j] = g8[j];
             }
             const bool active = s < ns;  // the whole warp scatters together
+            if (split) {  // dL/d(encoding) to the scatter kernel, unscaled FP32, level-major
+                if (active) {
+                    float2 *dst = bd.sp_dx + (size_t)tile * kSplitDx;
+                    const int l0 = half * (INP / 4);
+#pragma unroll
+                    for (int j = 0; j < INP / 4; ++j)
+                        if (l0 + j < NL)
+                            dst[(l0 + j) * kTcTile + s] = make_float2(g[2 * j] * inv_scale, g[2 * j + 1] * inv_scale);
+                }
+                tc_sync();
+                continue;
+            }
             float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
             if (active) {
                 const float *rf = rayf + (s / nr) * kRayStride;

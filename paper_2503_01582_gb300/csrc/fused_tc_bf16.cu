@@ -1,11 +1,16 @@
 // Mixed-precision fused kernels with BF16 MLP operands (all widths and encoding sizes).
-#include "fused_tc.cuh"
+#include "split_tc.cuh"
 
 namespace prenom {
 
 cudaError_t launch_fused_tc_bf16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st)
 {
     return launch_tc_prec<true>(one, wl, W, IN, grid, st);
+}
+
+cudaError_t launch_sample_encode_bf16(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
+{
+    return launch_sample_encode_t<true>(one, wl, grid, st);
 }
 
 }  // namespace prenom

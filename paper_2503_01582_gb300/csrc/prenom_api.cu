@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <array>
 #include <map>
+#include <set>
 #include <new>
 #include <string>
 #include <vector>
@@ -70,6 +71,10 @@ struct prenom_ctx {
     std::map<std::string, cudaGraphExec_t> graphs;
     std::map<std::string, std::vector<float>> tune_ms;  // measured ms per candidate
     std::map<std::string, int> tune_best;               // chosen candidate index
+    std::set<std::string> tune_warm;                    // signatures past their untimed first call
+    // split form of mixed-precision training: the buffers its kernels hand over
+    unsigned char *split_buf = nullptr;
+    size_t split_cap = 0;
 };
 
 namespace {
@@ -274,7 +279,50 @@ BatchDesc make_batchdesc(const prenom_ctx *c, const Object &o, const prenom_ray_
     return d;
 }
 
-int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &bd, int kernel_id)
+// Grows the split-form buffer to at least `bytes` (waits for the stream first:
+// the previous step may still read the old buffer).
+int ensure_split(prenom_ctx *c, size_t bytes)
+{
+    if (bytes <= c->split_cap)
+        return PRENOM_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream");
+    cudaFree(c->split_buf);
+    c->split_buf = nullptr;
+    c->split_cap = 0;
+    const size_t cap = bytes + bytes / 4;
+    e = cudaMalloc(&c->split_buf, cap);
+    if (e != cudaSuccess)
+        return fail(c, PRENOM_ERR_OOM, "split-form buffers of %zu bytes: %s", cap, cudaGetErrorString(e));
+    c->split_cap = cap;
+    return PRENOM_OK;
+}
+
+// Points a batch's split buffers into base; returns the bytes they take.
+size_t assign_split(BatchDesc &bd, unsigned char *base)
+{
+    const size_t t_bytes = ((size_t)bd.n_rays * bd.nr * sizeof(float) + 255) / 256 * 256;
+    bd.sp_t = reinterpret_cast<float *>(base);
+    bd.sp_x = reinterpret_cast<uint4 *>(base + t_bytes);
+    bd.sp_dx = reinterpret_cast<float2 *>(base + t_bytes + (size_t)bd.n_tiles * kSplitXBytes);
+    return split_bytes(bd.n_rays, bd.nr, bd.n_tiles);
+}
+
+// Grids of the split form's two extra kernels: the sampling-encoding kernel
+// runs one warp per ray slot, the scatter kernel one block per tile range.
+int grid_sample_encode(const prenom_ctx *c, int total_tiles, int rays_per_tile)
+{
+    const int64_t blocks = ((int64_t)total_tiles * rays_per_tile + kThreads / 32 - 1) / (kThreads / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)c->n_sm * 4));
+}
+
+int grid_scatter(const prenom_ctx *c, int total_tiles)
+{
+    return std::max(1, std::min(total_tiles, c->n_sm * 4));
+}
+
+int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &bd, int kernel_id, bool split = false)
 {
     if (bd.n_rays == 0)
         return PRENOM_OK;
@@ -286,6 +334,34 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
         bd.n_tiles = (bd.n_rays + bd.rays_per_tile - 1) / bd.rays_per_tile;
         const int per_sm = (2 * (smem + 1024) <= 228 * 1024) ? 2 : 1;  // two CTAs share an SM when they fit
         const int grid = std::min(bd.n_tiles, c->n_sm * per_sm);
+        if (split && bd.mode == kTrain) {
+            int rc = ensure_split(c, split_bytes(bd.n_rays, bd.nr, bd.n_tiles));
+            if (rc)
+                return rc;
+            assign_split(bd, c->split_buf);
+            WorkItem one{};
+            one.od = od;
+            one.bd = bd;
+            const WorkList wl{nullptr, 1, bd.n_tiles, od.H};
+            cudaEvent_t ev;
+            timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
+            cudaError_t e = launch_sample_encode(one, wl, o.arch.precision,
+                                                 grid_sample_encode(c, bd.n_tiles, bd.rays_per_tile), c->stream);
+            timed_end(c, PRENOM_KERNEL_SAMPLE_ENCODE, ev);
+            if (e != cudaSuccess)
+                return cuda_fail(c, e, "sampling-encoding kernel launch");
+            timed_begin(c, kernel_id, &ev);
+            e = launch_fused_tc(od, bd, o.arch.precision, grid, c->stream);
+            timed_end(c, kernel_id, ev);
+            if (e != cudaSuccess)
+                return cuda_fail(c, e, "mixed-precision kernel launch");
+            timed_begin(c, PRENOM_KERNEL_SCATTER, &ev);
+            e = launch_hash_scatter(one, wl, grid_scatter(c, bd.n_tiles), c->stream);
+            timed_end(c, PRENOM_KERNEL_SCATTER, ev);
+            if (e != cudaSuccess)
+                return cuda_fail(c, e, "hash scatter kernel launch");
+            return PRENOM_OK;
+        }
         cudaEvent_t ev;
         timed_begin(c, kernel_id, &ev);
         const cudaError_t e = launch_fused_tc(od, bd, o.arch.precision, grid, c->stream);
@@ -368,6 +444,7 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
 // signature as a CUDA graph and replayed with new rays.
 struct Group {
     int precision, W, IN, S, hmax, first, count, total_tiles, grid;
+    bool split = false;  // mixed precision: the three-kernel split form
 };
 
 struct Plan {
@@ -380,20 +457,30 @@ struct Plan {
     ScaleList scales{};
 };
 
-// Work-chunk candidates of the autotuner: tiles per CTA (0 = one persistent
-// wave of resident CTAs).
+// Candidates of the autotuner: tiles per CTA of the training kernel (0 = one
+// persistent wave of resident CTAs).  A mixed-precision group tries the split
+// form first (its tensor-core kernel in one wave), then the fused kernel with
+// three work-chunk sizes.
 constexpr int kTuneTpc[] = {0, 16, 8, 4};
+constexpr int kTuneTpcTc[] = {0, 0, 16, 8};
 constexpr int kTuneN = 4;
+constexpr int kTuneRounds = 2;  // each candidate is timed this many times (one whole step each)
 
-int group_grid(const prenom_ctx *c, const Group &g, int cand)
+bool cand_split(const Group &g, int cand, bool split_allowed)
+{
+    return g.precision != PRENOM_PRECISION_FP32 && split_allowed && cand == 0;
+}
+
+int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed)
 {
     int per_sm = 1;
     if (g.precision != PRENOM_PRECISION_FP32 && 2 * (fused_tc_smem(g.W, g.IN, g.hmax) + 1024) <= 228 * 1024)
         per_sm = 2;
     const int wave = c->n_sm * per_sm;
-    if (kTuneTpc[cand] == 0)
+    const int tpc = (g.precision != PRENOM_PRECISION_FP32 && split_allowed) ? kTuneTpcTc[cand] : kTuneTpc[cand];
+    if (tpc == 0)
         return std::max(1, std::min(g.total_tiles, wave));
-    return std::max(1, std::min(g.total_tiles, std::max(wave, (g.total_tiles + kTuneTpc[cand] - 1) / kTuneTpc[cand])));
+    return std::max(1, std::min(g.total_tiles, std::max(wave, (g.total_tiles + tpc - 1) / tpc)));
 }
 
 std::string group_key(const Group &g)
@@ -489,17 +576,36 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     cudaError_t e = cudaMemcpyAsync(c->d_work, stage, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = launch_zero_losses(d_items, (int)p.items.size(), c->stream);
+    const WorkItem unused{};
     for (const Group &g : p.groups) {
         if (e != cudaSuccess || g.total_tiles == 0)
             continue;
         const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax};
         cudaEvent_t ev;
+        if (g.split) {
+            if (timed)
+                timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
+            e = launch_sample_encode(unused, wl, g.precision,
+                                     grid_sample_encode(c, g.total_tiles, p.items[g.first].bd.rays_per_tile),
+                                     c->stream);
+            if (timed)
+                timed_end(c, PRENOM_KERNEL_SAMPLE_ENCODE, ev);
+            if (e != cudaSuccess)
+                continue;
+        }
         if (timed)
             timed_begin(c, PRENOM_KERNEL_TRAIN, &ev);
         e = g.precision == PRENOM_PRECISION_FP32 ? launch_fused_fp32_list(wl, g.W, g.IN, g.S, g.grid, c->stream)
                                                  : launch_fused_tc_list(wl, g.W, g.IN, g.precision, g.grid, c->stream);
         if (timed)
             timed_end(c, PRENOM_KERNEL_TRAIN, ev);
+        if (g.split && e == cudaSuccess) {
+            if (timed)
+                timed_begin(c, PRENOM_KERNEL_SCATTER, &ev);
+            e = launch_hash_scatter(unused, wl, grid_scatter(c, g.total_tiles), c->stream);
+            if (timed)
+                timed_end(c, PRENOM_KERNEL_SCATTER, ev);
+        }
     }
     if (e == cudaSuccess && p.adam_grid > 0) {
         AdamArgs a = p.adam;
@@ -521,7 +627,7 @@ int launches_of(const Plan &p)
 {
     int n = 1;  // loss reset
     for (const Group &g : p.groups)
-        n += g.total_tiles > 0;
+        n += g.total_tiles > 0 ? (g.split ? 3 : 1) : 0;
     if (p.adam_grid > 0)
         n += 1 + (p.scales.n > 0);
     return n;
@@ -535,18 +641,38 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         return rc;
     // autotuner: the first calls of a group signature try each work-chunk size once
     bool tuning = false;
+    const bool split_allowed = !(op.flags & PRENOM_FLAG_FUSED);
+    const bool split_forced = split_allowed && (op.flags & PRENOM_FLAG_SPLIT);
     std::vector<std::string> gkeys;
     for (Group &g : p.groups) {
-        gkeys.push_back(group_key(g));
+        gkeys.push_back(group_key(g) + (split_allowed ? "/s" : "/f"));
         auto it = c->tune_best.find(gkeys.back());
         int cand;
-        if (it != c->tune_best.end()) {
+        if (split_forced && g.precision != PRENOM_PRECISION_FP32) {
+            cand = 0;  // the split form, untuned
+        } else if (it != c->tune_best.end()) {
             cand = it->second;
         } else {
-            cand = (int)c->tune_ms[gkeys.back()].size();
+            cand = (int)c->tune_ms[gkeys.back()].size() % kTuneN;  // two rounds over the candidates
             tuning = true;
         }
-        g.grid = group_grid(c, g, cand);
+        g.grid = group_grid(c, g, cand, split_allowed);
+        g.split = cand_split(g, cand, split_allowed);
+    }
+    // buffers of the split groups (planned before any staging or capture)
+    size_t split_need = 0;
+    for (const Group &g : p.groups)
+        if (g.split)
+            for (int j = g.first; j < g.first + g.count; ++j)
+                split_need += split_bytes(p.items[j].bd.n_rays, p.items[j].bd.nr, p.items[j].bd.n_tiles);
+    if (split_need) {
+        if ((rc = ensure_split(c, split_need)))
+            return rc;
+        unsigned char *base = c->split_buf;
+        for (const Group &g : p.groups)
+            if (g.split)
+                for (int j = g.first; j < g.first + g.count; ++j)
+                    base += assign_split(p.items[j].bd, base);
     }
     // staging buffer: wait until the step that last read it has finished
     const size_t items_bytes = p.items.size() * sizeof(WorkItem);
@@ -600,16 +726,28 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         cudaEventDestroy(t1);
         for (size_t gi = 0; gi < p.groups.size(); ++gi) {  // whole-step time, charged to each tuned group
             std::vector<float> &v = c->tune_ms[gkeys[gi]];
-            if (c->tune_best.count(gkeys[gi]))
+            if (c->tune_best.count(gkeys[gi]) || (split_forced && p.groups[gi].precision != PRENOM_PRECISION_FP32))
                 continue;
+            if (!c->tune_warm.count(gkeys[gi])) {  // the first call loads modules and buffers: not timed
+                c->tune_warm.insert(gkeys[gi]);
+                continue;
+            }
             v.push_back(ms);
-            if ((int)v.size() == kTuneN)
-                c->tune_best[gkeys[gi]] = (int)(std::min_element(v.begin(), v.end()) - v.begin());
+            if ((int)v.size() == kTuneRounds * kTuneN) {  // keep the candidate with the best of its rounds
+                int best = 0;
+                float best_ms = INFINITY;
+                for (size_t k = 0; k < v.size(); ++k)
+                    if (v[k] < best_ms) {
+                        best_ms = v[k];
+                        best = (int)(k % kTuneN);
+                    }
+                c->tune_best[gkeys[gi]] = best;
+            }
         }
     } else if (use_graph) {
         std::string key = std::to_string(b) + ":" + std::to_string(bytes) + ":" + std::to_string(p.adam_grid);
         for (const Group &g : p.groups)
-            key += "|" + group_key(g) + "/" + std::to_string(g.grid);
+            key += "|" + group_key(g) + "/" + std::to_string(g.grid) + (g.split ? "s" : "f");
         for (int32_t id : p.touched)
             key += "," + std::to_string(id);
         char tail[96];
@@ -746,6 +884,7 @@ void prenom_destroy(prenom_ctx *c)
             cudaEventDestroy(c->stage_ev[i]);
     }
     cudaFree(c->d_work);
+    cudaFree(c->split_buf);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -918,7 +1057,7 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
                 cudaStreamSynchronize(c->stream);
         }
     }
-    if (n_batches > 1 && !(op->flags & PRENOM_FLAG_CHECK_FINITE))
+    if (n_batches > 0 && !(op->flags & PRENOM_FLAG_CHECK_FINITE))
         return train_batched(c, batches, n_batches, *op, loss_dev);
     if (loss_dev && n_batches > 0) {
         const cudaError_t e = cudaMemsetAsync(loss_dev, 0, (size_t)n_batches * sizeof(float), c->stream);
@@ -932,7 +1071,7 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
         ObjDesc od = make_objdesc(o, o.grad);
         BatchDesc bd = make_batchdesc(c, o, b, *op, kTrain, 128);
         bd.loss = loss_dev ? loss_dev + i : c->scratch;
-        if ((rc = launch_fused(c, o, od, bd, PRENOM_KERNEL_TRAIN)))
+        if ((rc = launch_fused(c, o, od, bd, PRENOM_KERNEL_TRAIN, !(op->flags & PRENOM_FLAG_FUSED))))
             return rc;
         if (std::find(touched.begin(), touched.end(), b.obj) == touched.end())
             touched.push_back(b.obj);

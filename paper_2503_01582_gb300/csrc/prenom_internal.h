@@ -53,7 +53,16 @@ struct BatchDesc {
     const float *loss_scale;  // device scalar multiplying dL/d(MLP output) before the 16-bit cast
     int32_t *overflow;        // device flag set when a scaled 16-bit gradient is not finite
     int32_t *status;          // device word: nonzero when a bounded wait gave up
+    // split execution of a mixed-precision training step (all NULL otherwise):
+    // the three kernels hand over these per-batch buffers
+    float *sp_t;    // [n_rays][nr] sample depths
+    uint4 *sp_x;    // [n_tiles][kSplitXBytes / 16] 16-bit encoding of each tile, in the MMA operand layout
+    float2 *sp_dx;  // [n_tiles][kMaxLevels][kSplitTile] dL/d(encoding), FP32, level-major
 };
+
+constexpr int kSplitTile = 128;                      // samples per tile of the mixed-precision kernels
+constexpr int kSplitXBytes = kSplitTile * 32 * 2;    // encoding image of a tile (width <= 32, 16-bit)
+constexpr int kSplitDx = kMaxLevels * kSplitTile;    // float2 per tile of dL/d(encoding)
 
 // Dynamic loss-scaling state of one mixed-precision object (device memory).
 struct LossScaleState {
@@ -72,6 +81,17 @@ cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precisio
 cudaError_t launch_fused_tc_list(const WorkList &wl, int W, int IN, int precision, int grid, cudaStream_t st);
 cudaError_t launch_fused_tc_bf16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st);
 cudaError_t launch_fused_tc_fp16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st);
+// Split execution of a mixed-precision training step: sampling + encoding,
+// then the tensor-core kernel without its scatter, then the hash scatter.
+// wl.items == nullptr means the single item `one`.
+cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int precision, int grid, cudaStream_t st);
+cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st);
+// Bytes of split buffers for a batch of n_rays rays of nr samples in n_tiles tiles.
+inline size_t split_bytes(int n_rays, int nr, int n_tiles)
+{
+    const size_t t = ((size_t)n_rays * nr * sizeof(float) + 255) / 256 * 256;
+    return t + (size_t)n_tiles * (kSplitXBytes + kSplitDx * 8);
+}
 // Loss-scale bookkeeping after the Adam step of a mixed-precision object.
 cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st);
 constexpr int kMaxScaleObjs = 256;

@@ -92,9 +92,11 @@ def test_batched_gradients_match_per_object_and_oracle(pkg):
 
 
 def test_batched_adam_graph_replay_and_autotuner(pkg):
-    """Eight batched steps on a side stream: the first four tune the work-chunk
-    size, the rest replay a captured graph while the ray buffers change; the
-    losses and parameters follow the same objects stepped one at a time."""
+    """Twelve batched steps on a side stream: the first nine tune (one untimed
+    call, then two rounds over the split form and three work-chunk sizes), the
+    rest replay a captured graph while the ray buffers change; the losses and
+    parameters follow the same objects stepped one at a time (with
+    PRENOM_FLAG_CHECK_FINITE, i.e. one launch per object, untuned)."""
     import torch
 
     objs = _setup()
@@ -103,10 +105,11 @@ def test_batched_adam_graph_replay_and_autotuner(pkg):
     ctx_b, ids_b = _make(pkg, objs, stream=stream)
     ctx_s, ids_s = _make(pkg, objs)
     opts = pkg.make_opts(nc=32, nr=32, lr=1e-2)
+    opts_s = pkg.make_opts(nc=32, nr=32, lr=1e-2, flags=pkg.PRENOM_FLAG_CHECK_FINITE)
     loss_b = torch.zeros(len(objs), device="cuda")
     sets = [[_batch(o, i) for o, i in zip(src, ids_b)] for src in (objs, alt)]
     torch.cuda.synchronize()
-    for step in range(8):
+    for step in range(12):
         src = objs if step % 2 == 0 else alt
         with torch.cuda.stream(stream):
             ctx_b.train_step(sets[step % 2], opts, loss_b)
@@ -114,13 +117,16 @@ def test_batched_adam_graph_replay_and_autotuner(pkg):
         lb = loss_b.cpu().numpy()
         for k, (o, i) in enumerate(zip(src, ids_s)):
             loss_s = torch.zeros(1, device="cuda")
-            ctx_s.train_step([_batch(o, i)], opts, loss_s)
+            ctx_s.train_step([_batch(o, i)], opts_s, loss_s)
             assert abs(lb[k] - loss_s.item()) <= 1e-4 * abs(loss_s.item()) + 1e-7, (step, k)
     for k in range(len(objs)):
-        assert ctx_b.get_step(ids_b[k]) == 8
+        assert ctx_b.get_step(ids_b[k]) == 12
         tb = ctx_b.get_state(ids_b[k]).cpu().numpy()
         ts = ctx_s.get_state(ids_s[k]).cpu().numpy()
-        # Adam normalises each entry, so rounding-level gradients may step either way: compare in bulk
-        assert np.mean(np.abs(tb - ts) <= 1e-4 * np.abs(ts).max() + 1e-6) > 0.999, k
+        # Adam normalises each entry, so an entry whose gradient is at rounding level may step either
+        # way (by at most lr per step): compare in bulk, and bound every entry by Adam's step size
+        close = np.abs(tb - ts) <= 1e-4 * np.abs(ts).max() + 1e-6
+        assert np.mean(close) > 0.99, (k, np.mean(close))
+        assert np.abs(tb - ts).max() <= 2 * 1e-2 * 12 * 1.01, k
     ctx_b.close()
     ctx_s.close()

@@ -195,3 +195,74 @@ def test_mixed_full_size_sampled(pkg):
     assert float(np.abs(out["rgb"].cpu().numpy()[idx] - want["rgb"]).max()) <= BOUNDS[2]["rgb"]
     assert rel(out["depth"].cpu().numpy()[idx], want["depth"]) <= BOUNDS[2]["rel"]
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("nr,n_rays", [(64, 301), (48, 257), (32, 200)])
+def test_split_form_matches_fused_kernel(pkg, precision, nr, n_rays):
+    """The split form (sampling + encoding, the tensor-core MLP, the hash scatter
+    as three kernels) and the single fused kernel compute the same step from the
+    same uniforms: the same loss, bins and depths, and gradients equal up to the
+    order of the FP32 reductions.  Ragged batches: the last tile is partial, and
+    for nr = 48 a tile holds 96 of its 128 rows."""
+    import torch
+
+    arch = ARCHS[1]
+    a, theta, grid, rays, u, cr = case(arch, n_rays, nr, nr, seed=91, hash_range=0.5)
+    res = {}
+    for form, flags in (("split", 0), ("fused", pkg.PRENOM_FLAG_FUSED)):
+        ctx = pkg.Context(seed=3)
+        obj = ctx.create_object(_arch(pkg, arch, precision), theta)
+        ctx.set_prior_grid(obj, grid)
+        loss = torch.zeros(1, device="cuda")
+        ctx.train_step([_dev(rays, obj, cr=cr, u=u)],
+                       pkg.make_opts(nc=nr, nr=nr, flags=flags | pkg.PRENOM_FLAG_NO_ADAM), loss)
+        res[form] = (loss.item(), ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy())
+        ctx.close()
+    (ls, gs), (lf, gf) = res["split"], res["fused"]
+    assert np.isfinite(ls) and ls > 0
+    assert abs(ls - lf) <= 1e-6 * abs(lf)
+    assert rel(gs, gf) <= 1e-5
+    assert np.all((gs == 0) == (gf == 0))  # the same entries are touched
+
+
+# At the initial hash scale U(-1e-4, 1e-4) most encodings lie below FP16's
+# smallest normal (6.1e-5) and keep fewer mantissa bits, so the weight
+# gradients of the first layer lose accuracy: measured cos 0.99923, rel-L2
+# 3.9e-2 on this case, frozen at cos >= 0.998, rel-L2 <= 0.1.  With trained-
+# scale features (U(-0.5, 0.5)) the general FP16 bounds hold.
+FULL_BOUNDS = {0.5: BOUNDS[1], 1e-4: dict(rel=5e-4, cos=0.998, l2=0.1)}
+
+
+@pytest.mark.parametrize("hash_range", [0.5, 1e-4])
+def test_split_form_against_oracle_full_size(pkg, hash_range):
+    """The default (split) FP16 form on the full-size architecture in the
+    launch configuration of the benchmark (4096 rays x 64 samples): the loss
+    and the gradient of the whole batch on identical samples against the
+    oracle."""
+    import torch
+    from helpers import pool_cfg2
+    from synth import init_params, prior_grid, random_colours, sample_batch, stratified_uniforms
+
+    a = orc.Arch(**CFG2)
+    sc, pool = pool_cfg2()
+    rays = sample_batch(pool, 4096, 3)
+    u = stratified_uniforms(4096, 64, 4)
+    cr = random_colours(4096, 5)
+    grid = prior_grid(sc, 64, 0)
+    theta = init_params(orc.n_hash_params(a), a.mlp_shapes(), 6, hash_range=hash_range)
+    t_in = oracle_t(grid, rays, u, 64, 64)
+    ctx = pkg.Context(seed=3)
+    obj = ctx.create_object(_arch(pkg, CFG2, 1), theta)
+    ctx.set_prior_grid(obj, grid)
+    loss = torch.zeros(1, device="cuda")
+    ctx.train_step([_dev(rays, obj, cr=cr, t_in=t_in)], pkg.make_opts(nc=64, nr=64, flags=pkg.PRENOM_FLAG_NO_ADAM),
+                   loss)
+    g = ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy()
+    ctx.close()
+    want = orc.batch(a, theta, grid, rays, 64, 64, t_in=t_in, c_rand=cr, want_grad=True)
+    cos, l2 = _grad_metrics(g, want["grad"])
+    e_loss = abs(loss.item() - want["loss"]) / abs(want["loss"])
+    print(f"\nfull size split FP16, hash range {hash_range}: loss {e_loss:.2e} grad cos {cos:.6f} rel-L2 {l2:.2e}")
+    bnd = FULL_BOUNDS[hash_range]
+    assert e_loss <= bnd["rel"] and cos >= bnd["cos"] and l2 <= bnd["l2"]
