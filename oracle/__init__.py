@@ -119,6 +119,7 @@ def lib():
             "orc_adam": (None, [C.c_int64, _D, _D, _D, _D, C.c_int, C.c_double, C.c_double,
                                 C.c_double, C.c_double]),
             "orc_philox4x32_10": (None, [_U32, _U32, _U32]),
+            "orc_reptile": (None, [C.c_int64, _D, C.POINTER(_D), C.c_int, C.c_double]),
             "orc_philox_uniforms": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, _F]),
             "orc_philox_colours": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, _F]),
         }
@@ -310,6 +311,37 @@ def adam(theta, m, v, g, step: int, lr: float, beta1: float = 0.9, beta2: float 
         assert x.dtype == np.float64 and x.flags.c_contiguous
     g = _d(g)
     lib().orc_adam(theta.size, _p(theta), _p(m), _p(v), _p(g), step, lr, beta1, beta2, eps)
+
+
+def reptile(theta, tasks, beta: float):
+    """In-place Reptile outer update (Eq. 2, batched over the tasks) of a float64 array."""
+    assert theta.dtype == np.float64 and theta.flags.c_contiguous
+    ts = [_d(t) for t in tasks]
+    assert all(t.size == theta.size for t in ts) and len(ts) > 0
+    arr = (_D * len(ts))(*[_p(t) for t in ts])
+    lib().orc_reptile(theta.size, _p(theta), arr, len(ts), beta)
+
+
+def meta_step(a: Arch, theta_meta, grid_of, task_batches, nc: int, nr: int, *, lr: float = 1e-2,
+              beta: float = 0.1, **kw):
+    """One meta-training step (§III-A): every task starts from theta_meta with fresh
+    Adam state, takes len(task_batches[t]) inner steps (Eq. 1, with Adam as the inner
+    optimiser) on its own batches and prior grid, then Eq. 2 moves theta_meta toward
+    the tasks' mean.  task_batches[t] is a list of dicts (rays plus optional
+    t_in / u / c_rand).  Returns the new theta_meta and each task's losses."""
+    theta = _d(theta_meta).copy()
+    finals, losses = [], []
+    for t, batches in enumerate(task_batches):
+        ob = OracleObject(a, theta, grid_of(t))
+        lt = []
+        for b in batches:
+            rays = {k: b[k] for k in ("o", "d", "rgb", "depth", "is_obj")}
+            lt.append(ob.train_step(rays, nc, nr, u=b.get("u"), t_in=b.get("t_in"), c_rand=b.get("c_rand"), lr=lr,
+                                    **kw))
+        finals.append(ob.theta)
+        losses.append(lt)
+    reptile(theta, finals, beta)
+    return theta, losses
 
 
 # -------------------------------------------------------------------- Philox

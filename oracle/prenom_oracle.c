@@ -608,6 +608,23 @@ void orc_adam(int64_t n, double *theta, double *m, double *v, const double *g, i
     }
 }
 
+/* ============================================================== Reptile
+ * §III-A, Eq. 2: after q inner steps on task i, the meta-parameters move toward
+ * the task's parameters, theta <- theta + beta (theta_i^(q) - theta).  Reading
+ * for a meta-batch of n tasks adapted from the same theta: the batched form of
+ * Reptile, theta <- theta + beta (mean_t theta_t^(q) - theta), which is Eq. 2
+ * itself for n = 1.  Sum in task order, then the mean, then the step. */
+void orc_reptile(int64_t n, double *theta, const double *const *tasks, int n_tasks, double beta)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int t = 0; t < n_tasks; ++t)
+            sum += tasks[t][i];
+        const double mean = sum / (double)n_tasks;
+        theta[i] = theta[i] + beta * (mean - theta[i]);
+    }
+}
+
 /* ============================================================== Philox
  * Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC 2011): each round multiplies counter words

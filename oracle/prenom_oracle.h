@@ -17,7 +17,9 @@
  *   - §III-B "Volume Rendering": colour, depth and opacity compositing (Eq. 7),
  *     the losses L_c, L_d, L_sigma (Eq. 8) and their weighted sum (Eq. 9);
  *   - reverse-mode gradients of that loss and the Adam update that the
- *     paper's last sentence of §III-B names.
+ *     paper's last sentence of §III-B names;
+ *   - §III-A "Meta-learning": the Reptile outer update (Eq. 2) after inner
+ *     training steps (Eq. 1).
  * Readings of points the paper leaves open are listed beside each routine.
  *
  * Parameter vector layout (shared by contract with the library's interface,
@@ -97,6 +99,9 @@ double orc_batch(const orc_arch *a, const double *theta, const double *grid, int
 /* ---- Adam (§III-B, last sentence) ---- */
 void orc_adam(int64_t n, double *theta, double *m, double *v, const double *g, int step,
               double lr, double beta1, double beta2, double eps);
+
+/* ---- Reptile outer update (§III-A, Eq. 2; batched over n_tasks) ---- */
+void orc_reptile(int64_t n, double *theta, const double *const *tasks, int n_tasks, double beta);
 
 /* ---- Philox4x32-10 counter-based generator (Salmon et al., SC 2011) ---- */
 void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out);

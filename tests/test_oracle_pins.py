@@ -481,3 +481,67 @@ def test_philox_uniforms_are_stratified(orc):
     assert np.all(u >= k / nr) and np.all(u < (k + 1) / nr)
     c = orc.philox_colours(1234, 3, 1, 5000)
     assert c.min() >= 0 and c.max() < 1 and abs(c.mean() - 0.5) < 0.01
+
+
+# ------------------------------------------------------------------ Reptile (§III-A, Eq. 2)
+def test_reptile_special_cases(orc):
+    theta = np.array([1.0, -2.0, 0.5, 8.0])
+    t1 = np.array([3.0, 2.0, 0.5, -8.0])
+    # beta = 0 leaves the meta-parameters alone; one task with beta = 1 copies it
+    x = theta.copy()
+    orc.reptile(x, [t1], 0.0)
+    np.testing.assert_array_equal(x, theta)
+    x = theta.copy()
+    orc.reptile(x, [t1], 1.0)
+    np.testing.assert_array_equal(x, t1)
+    # one task, beta = 1/4: theta + (t - theta)/4 (dyadic, so exact)
+    x = theta.copy()
+    orc.reptile(x, [t1], 0.25)
+    np.testing.assert_array_equal(x, np.array([1.5, -1.0, 0.5, 4.0]))
+    # tasks symmetric about theta cancel; beta = 1 lands on the mean of the tasks
+    x = theta.copy()
+    orc.reptile(x, [theta + 1.0, theta - 1.0, theta + 0.5, theta - 0.5], 0.7)
+    np.testing.assert_array_equal(x, theta)
+    x = theta.copy()
+    orc.reptile(x, [np.zeros(4), np.full(4, 2.0), np.full(4, 4.0), np.full(4, 6.0)], 1.0)
+    np.testing.assert_array_equal(x, np.full(4, 3.0))
+
+
+def test_reptile_is_the_mean_step_and_order_free(orc):
+    rng = np.random.default_rng(5)
+    theta = rng.normal(size=1000)
+    tasks = [rng.normal(size=1000) for _ in range(16)]
+    a = theta.copy()
+    orc.reptile(a, tasks, 0.1)
+    b = theta.copy()
+    orc.reptile(b, tasks[::-1], 0.1)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
+    # n tasks at once = one task equal to their mean (Eq. 2 with theta_i^(q) the mean)
+    c = theta.copy()
+    orc.reptile(c, [np.mean(tasks, axis=0)], 0.1)
+    np.testing.assert_allclose(a, c, rtol=0, atol=1e-14)
+    # two half steps toward a fixed target compose to one step of 1 - (1 - beta)^2
+    d = theta.copy()
+    orc.reptile(d, [tasks[0]], 0.5)
+    orc.reptile(d, [tasks[0]], 0.5)
+    e = theta.copy()
+    orc.reptile(e, [tasks[0]], 0.75)
+    np.testing.assert_allclose(d, e, rtol=0, atol=1e-14)
+
+
+def test_meta_step_composes_inner_training_and_outer_update(orc):
+    """The meta-step driver: no inner steps leaves theta unchanged; one task with
+    beta = 1 yields exactly that task trained alone from theta (Eq. 1 then Eq. 2)."""
+    from helpers import CFG1, case
+
+    a, theta, grid, rays, u, cr = case(CFG1, 16, 8, 8, seed=3, hash_range=0.5)
+    b = dict(rays, u=u, c_rand=cr)
+    th, losses = orc.meta_step(a, theta, lambda t: grid, [[], []], 8, 8, beta=0.5)
+    np.testing.assert_array_equal(th, theta.astype(np.float64))
+    th, losses = orc.meta_step(a, theta, lambda t: grid, [[b, b]], 8, 8, lr=1e-2, beta=1.0)
+    ob = orc.OracleObject(a, theta, grid)
+    l0 = ob.train_step(rays, 8, 8, u=u, c_rand=cr, lr=1e-2)
+    l1 = ob.train_step(rays, 8, 8, u=u, c_rand=cr, lr=1e-2)
+    # theta + 1 (x - theta) equals x up to one rounding of the subtraction and the sum
+    np.testing.assert_allclose(th, ob.theta, rtol=0, atol=4 * np.finfo(np.float64).eps * np.abs(ob.theta).max())
+    assert losses == [[l0, l1]] and l1 < l0
