@@ -328,6 +328,51 @@ def _batched_workload(pkg, ctx, stream, precision, seed, theta_from=None, only=N
     return objs, dev_sets, n_samples
 
 
+META_TASKS, META_INNER, META_RAYS, META_NR = 16, 16, 2048, 48
+
+
+def _meta_compare(pkg, ctx, stream, prec):
+    """One Reptile meta step (§III-A): 16 tasks of one CSG topology with per-task
+    scale jitter U[0.8, 1.2], each adapted by 16 inner Adam steps of 2048 rays x 48
+    samples (all tasks of an inner step in one batched call), then the outer update
+    of Eq. 2 (beta = 0.1); architecture L=8, F=2, T=2^14, res 16..256, MLP 16-32-32-4."""
+    import torch
+    from paper_2503_01582_gb300.meta import meta_step
+    from synth import (cameras_on_sphere, make_ray_pool, prior_grid, random_colours, sample_batch,
+                       scene_random_csg, stratified_uniforms)
+
+    arch = pkg.make_arch(L=8, log2T=14, n_min=16, n_max=256, width=32, hidden=2, lambda_d=0.1, lambda_sigma=1e-3,
+                         precision=PRECISION[prec])
+    rng = np.random.default_rng(11)
+    meta = ctx.create_object(arch)
+    tasks, batches = [], []
+    for t in range(META_TASKS):
+        sc = scene_random_csg(21, scale=float(rng.uniform(0.8, 1.2)))
+        obj = ctx.create_object(arch)
+        ctx.set_prior_grid(obj, prior_grid(sc, 32, t))
+        pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 40, 128, 128, t), 4 * META_RAYS, t)
+        bs = []
+        for j in range(4):  # four rotating ray sets per task
+            b = sample_batch(pool, META_RAYS, 1000 * t + j)
+            b["uniforms"] = stratified_uniforms(META_RAYS, META_NR, 2000 * t + j)
+            b["c_rand"] = random_colours(META_RAYS, 3000 * t + j)
+            bs.append(_device_batches([b], obj, stream)[0])
+        tasks.append(obj)
+        batches.append(bs)
+    inner = [[batches[t][j % 4] for t in range(META_TASKS)] for j in range(META_INNER)]
+    opts = pkg.make_opts(nc=META_NR, nr=META_NR, lr=1e-2)
+    loss = torch.zeros(META_TASKS, device="cuda")
+    f = lambda i: meta_step(ctx, meta, tasks, inner, opts, 0.1, loss)  # noqa: E731
+    steps = 3
+    ms = _time(stream, f, steps, 2)
+    for o in [meta] + tasks:
+        ctx.destroy_object(o)
+    n_smp = META_TASKS * META_INNER * META_RAYS * META_NR
+    return {"workload": "Reptile meta step: 16 tasks x 16 inner Adam steps x 2048 rays x 48 samples, outer update "
+                        "(Eq. 2, beta 0.1); L=8 T=2^14 res 16..256, MLP 16-32-32-4; %d samples per meta step" % n_smp,
+            "value": n_smp * steps / (ms / 1e3), "unit": "samples/s", "ms_per_meta_step": ms / steps}
+
+
 def run_ours(args):
     import torch
 
@@ -362,6 +407,7 @@ def run_ours(args):
     obj, dev_batches, batches_np, n_params = _setup_single(pkg, ctx, prec, rank, stream)
     step = lambda i: ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)  # noqa: E731
     _time(stream, step, 0, args.warmup)  # also runs the autotuner's first calls
+    tuning = ctx.tuning_report().strip()
     launches0 = ctx.launch_count()
     clocks = ClockSampler(gpu_identifier(local))
     with clocks:  # the step as a user runs it: CUDA-graph replay, no per-kernel events
@@ -437,6 +483,9 @@ def run_ours(args):
             "speedup": msl / msb}
         for o in objs16 + objs32:
             ctx.destroy_object(o)
+
+    if world == 1 and not args.no_compare:
+        compare["reptile_meta_step"] = _meta_compare(pkg, ctx, stream, prec)
 
     if world > 1 and not args.no_compare:
         # the 32-object workload split over the ranks (longest processing time
@@ -532,7 +581,7 @@ def run_ours(args):
                                                   "split": ", split: sampling+encoding / tensor-core MLP / "
                                                            "hash scatter"}[args.form]),
                            "rays_per_step": N_RAYS, "samples_per_ray": NR,
-                           "probes": NC, "params": n_params,
+                           "probes": NC, "params": n_params, "autotuner": tuning,
                            "parallelism": f"{world} independent objects (one per GPU)" if world > 1 else "1 object",
                            "l2": "working set > L2: theta, grad, Adam m and v (4 x %.0f MB) stream every step"
                                  % (n_params * 4 / 1e6)},

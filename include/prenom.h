@@ -241,6 +241,44 @@ PRENOM_API int prenom_set_state(prenom_ctx *ctx, int32_t obj, int32_t which, con
 PRENOM_API int prenom_get_step(prenom_ctx *ctx, int32_t obj, int32_t *step);
 PRENOM_API int prenom_set_step(prenom_ctx *ctx, int32_t obj, int32_t step);
 
+/* ------------------------------------------------- meta-learning (§III-A)
+ * One Reptile meta step over a meta-batch of tasks (§III-A "Meta-learning"):
+ * every task object starts from the meta object's parameters with fresh Adam
+ * state, takes q inner training steps on its own reconstruction task (Eq. 1;
+ * the inner optimiser is the Adam step of prenom_train_step, whose batched
+ * form trains all tasks of the meta-batch in one launch per step), and the
+ * meta-parameters then move toward the tasks' result:
+ *     theta <- theta + beta (mean_t theta_t^(q) - theta)
+ * (the batched reading of Eq. 2; with one task it is Eq. 2 itself).  Meta and
+ * task objects are ordinary objects of one architecture (L, F, T, N_min,
+ * N_max, width, depth; their precisions may differ); at most 128 tasks, each
+ * listed once, the meta object not among them.  Stream-ordered, no
+ * synchronisation.  Errors: PRENOM_ERR_INVALID_ARG for a bad object list or
+ * beta outside [0, 1].
+ *
+ * prenom_reptile_begin: theta_t <- theta_meta, gradient and Adam moments of
+ *   every task zeroed, its step count reset to 0 (its loss scale is kept).
+ * prenom_reptile_update: the outer update above over the n_tasks tasks (their
+ *   sum in task order, FP32), in one pass.
+ * Across several GPUs the tasks are split between ranks: each rank calls
+ * prenom_reptile_task_sum (sum: device, param_count floats, 16-byte aligned,
+ * overwritten with the sum of its tasks' parameters), the ranks add their sums
+ * (one all-reduce), and each calls prenom_reptile_apply with n_total = the
+ * number of tasks over all ranks. */
+PRENOM_API int prenom_reptile_begin(prenom_ctx *ctx, int32_t meta, const int32_t *tasks, int32_t n_tasks);
+PRENOM_API int prenom_reptile_update(prenom_ctx *ctx, int32_t meta, const int32_t *tasks, int32_t n_tasks,
+                                     float beta);
+PRENOM_API int prenom_reptile_task_sum(prenom_ctx *ctx, const int32_t *tasks, int32_t n_tasks, float *sum);
+PRENOM_API int prenom_reptile_apply(prenom_ctx *ctx, int32_t meta, const float *sum, int32_t n_total, float beta);
+
+/* The autotuner's record as text (one line per group signature: the step
+ * times in ms of each timed call, "cK" = candidate K, and the chosen candidate
+ * after "->"; candidates of a mixed-precision group: c0 split form, c1..c3 the
+ * fused kernel in one wave / 16 / 8 tiles per CTA; of an FP32 group: one wave
+ * / 16 / 8 / 4 tiles per CTA).  buf: host, cap bytes, NUL-terminated,
+ * truncated to fit. */
+PRENOM_API int prenom_tuning_report(prenom_ctx *ctx, char *buf, size_t cap);
+
 /* Zeroes an object's gradient buffer (stream-ordered). */
 PRENOM_API int prenom_zero_grads(prenom_ctx *ctx, int32_t obj);
 

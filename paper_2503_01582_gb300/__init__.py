@@ -202,6 +202,27 @@ class Context:
     def zero_grads(self, obj: int):
         _abi.prenom_zero_grads(self._ctx, obj)
 
+    def tuning_report(self) -> str:
+        """The autotuner's measured candidates and choices, one line per group signature."""
+        return _abi.prenom_tuning_report(self._ctx)
+
+    # ---- Reptile meta step (§III-A, Eq. 1-2)
+    def reptile_begin(self, meta: int, tasks):
+        """Every task object <- the meta object's parameters, fresh Adam state."""
+        _abi.prenom_reptile_begin(self._ctx, meta, list(tasks))
+
+    def reptile_update(self, meta: int, tasks, beta: float):
+        """theta_meta <- theta_meta + beta (mean of the tasks' parameters - theta_meta)."""
+        _abi.prenom_reptile_update(self._ctx, meta, list(tasks), beta)
+
+    def reptile_task_sum(self, tasks, out):
+        """out (CUDA float32, param_count) <- sum of the tasks' parameters."""
+        _abi.prenom_reptile_task_sum(self._ctx, list(tasks), _dptr(out, name="out"))
+
+    def reptile_apply(self, meta: int, task_sum, n_total: int, beta: float):
+        """theta_meta <- theta_meta + beta (task_sum / n_total - theta_meta)."""
+        _abi.prenom_reptile_apply(self._ctx, meta, _dptr(task_sum, name="task_sum"), n_total, beta)
+
     def sync(self):
         _abi.prenom_sync(self._ctx)
 

@@ -90,6 +90,11 @@ _SIGS = {
     "prenom_get_step": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32)]),
     "prenom_set_step": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "prenom_zero_grads": (C.c_int, [_CTX, C.c_int32]),
+    "prenom_tuning_report": (C.c_int, [_CTX, C.c_char_p, C.c_size_t]),
+    "prenom_reptile_begin": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
+    "prenom_reptile_update": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_float]),
+    "prenom_reptile_task_sum": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.c_int32, _P]),
+    "prenom_reptile_apply": (C.c_int, [_CTX, C.c_int32, _P, C.c_int32, C.c_float]),
     "prenom_sync": (C.c_int, [_CTX]),
     "prenom_enable_timing": (C.c_int, [_CTX, C.c_int32]),
     "prenom_kernel_time": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -223,6 +228,32 @@ def prenom_set_step(ctx, obj: int, step: int):
 
 def prenom_zero_grads(ctx, obj: int):
     check(lib().prenom_zero_grads(ctx, obj), ctx)
+
+
+def prenom_tuning_report(ctx) -> str:
+    buf = C.create_string_buffer(1 << 16)
+    check(lib().prenom_tuning_report(ctx, buf, len(buf)), ctx)
+    return buf.value.decode()
+
+
+def _ids(tasks):
+    return (C.c_int32 * len(tasks))(*[int(t) for t in tasks])
+
+
+def prenom_reptile_begin(ctx, meta: int, tasks):
+    check(lib().prenom_reptile_begin(ctx, meta, _ids(tasks), len(tasks)), ctx)
+
+
+def prenom_reptile_update(ctx, meta: int, tasks, beta: float):
+    check(lib().prenom_reptile_update(ctx, meta, _ids(tasks), len(tasks), beta), ctx)
+
+
+def prenom_reptile_task_sum(ctx, tasks, sum_ptr: int):
+    check(lib().prenom_reptile_task_sum(ctx, _ids(tasks), len(tasks), _P(sum_ptr)), ctx)
+
+
+def prenom_reptile_apply(ctx, meta: int, sum_ptr: int, n_total: int, beta: float):
+    check(lib().prenom_reptile_apply(ctx, meta, _P(sum_ptr), n_total, beta), ctx)
 
 
 def prenom_sync(ctx):

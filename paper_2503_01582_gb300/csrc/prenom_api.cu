@@ -1187,6 +1187,147 @@ int prenom_set_step(prenom_ctx *c, int32_t obj, int32_t step)
     return PRENOM_OK;
 }
 
+// ------------------------------------------------------------- Reptile
+static bool same_layout(const prenom_arch &a, const prenom_arch &b)
+{
+    return a.L == b.L && a.F == b.F && a.log2T == b.log2T && a.n_min == b.n_min && a.n_max == b.n_max &&
+           a.width == b.width && a.hidden == b.hidden;
+}
+
+// Validates a meta object and its tasks and fills the task pointers of a.
+static int reptile_args(prenom_ctx *c, int32_t meta, const int32_t *tasks, int32_t n_tasks, ReptileArgs &a,
+                        Object **meta_out)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_tasks < 1 || n_tasks > kMaxReptileTasks || !tasks)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "1..%d task objects are required", kMaxReptileTasks);
+    Object *m = meta >= 0 ? get_obj(c, meta) : nullptr;
+    if (meta >= 0 && !m)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown meta object %d", meta);
+    const Object *first = nullptr;
+    for (int i = 0; i < n_tasks; ++i) {
+        Object *t = get_obj(c, tasks[i]);
+        if (!t)
+            return fail(c, PRENOM_ERR_INVALID_ARG, "unknown task object %d", tasks[i]);
+        if (tasks[i] == meta)
+            return fail(c, PRENOM_ERR_INVALID_ARG, "the meta object cannot be one of its tasks");
+        for (int j = 0; j < i; ++j)
+            if (tasks[j] == tasks[i])
+                return fail(c, PRENOM_ERR_INVALID_ARG, "task object %d is listed twice", tasks[i]);
+        const Object *ref = m ? m : (first ? first : t);
+        if (!same_layout(t->arch, ref->arch))
+            return fail(c, PRENOM_ERR_INVALID_ARG, "task object %d has another architecture", tasks[i]);
+        first = first ? first : t;
+        a.theta[i] = t->theta;
+    }
+    a.n_tasks = n_tasks;
+    a.n = first->n;
+    a.n_pad = first->n_pad;
+    if (meta_out)
+        *meta_out = m;
+    return PRENOM_OK;
+}
+
+static int reptile_launch(prenom_ctx *c, const ReptileArgs &a, int op)
+{
+    const int64_t work = (a.n + 3) / 4;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)c->n_sm * 8));
+    const cudaError_t e = launch_reptile(a, op, grid, c->stream);
+    c->launches++;
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "Reptile kernel launch");
+}
+
+int prenom_reptile_begin(prenom_ctx *c, int32_t meta, const int32_t *tasks, int32_t n_tasks)
+{
+    ReptileArgs a{};
+    Object *m = nullptr;
+    int rc = meta < 0 ? fail(c, PRENOM_ERR_INVALID_ARG, "a meta object is required")
+                      : reptile_args(c, meta, tasks, n_tasks, a, &m);
+    if (rc)
+        return rc;
+    a.meta = m->theta;
+    if ((rc = reptile_launch(c, a, kReptileBroadcast)))
+        return rc;
+    for (int i = 0; i < n_tasks; ++i)
+        c->objs[tasks[i]].step = 0;
+    return PRENOM_OK;
+}
+
+int prenom_reptile_update(prenom_ctx *c, int32_t meta, const int32_t *tasks, int32_t n_tasks, float beta)
+{
+    ReptileArgs a{};
+    Object *m = nullptr;
+    int rc = meta < 0 ? fail(c, PRENOM_ERR_INVALID_ARG, "a meta object is required")
+                      : reptile_args(c, meta, tasks, n_tasks, a, &m);
+    if (rc)
+        return rc;
+    if (!(beta >= 0.f && beta <= 1.f))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "beta must lie in [0, 1]");
+    a.meta = m->theta;
+    a.beta = beta;
+    a.nf = (float)n_tasks;
+    return reptile_launch(c, a, kReptileSum);
+}
+
+int prenom_reptile_task_sum(prenom_ctx *c, const int32_t *tasks, int32_t n_tasks, float *sum)
+{
+    ReptileArgs a{};
+    int rc = reptile_args(c, -1, tasks, n_tasks, a, nullptr);
+    if (rc)
+        return rc;
+    if (!sum || reinterpret_cast<uintptr_t>(sum) % 16 != 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "sum must be a 16-byte aligned device buffer");
+    a.sum = sum;
+    return reptile_launch(c, a, kReptileSum);
+}
+
+int prenom_reptile_apply(prenom_ctx *c, int32_t meta, const float *sum, int32_t n_total, float beta)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    Object *m = get_obj(c, meta);
+    if (!m)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown meta object %d", meta);
+    if (!sum || reinterpret_cast<uintptr_t>(sum) % 16 != 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "sum must be a 16-byte aligned device buffer");
+    if (n_total < 1 || !(beta >= 0.f && beta <= 1.f))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "n_total >= 1 and beta in [0, 1] are required");
+    ReptileArgs a{};
+    a.n = m->n;
+    a.n_pad = m->n_pad;
+    a.meta = m->theta;
+    a.sum = const_cast<float *>(sum);
+    a.beta = beta;
+    a.nf = (float)n_total;
+    return reptile_launch(c, a, kReptileApply);
+}
+
+int prenom_tuning_report(prenom_ctx *c, char *buf, size_t cap)
+{
+    if (!c || !buf || cap == 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "ctx, buf and cap are required");
+    std::string r;
+    for (const auto &kv : c->tune_ms) {
+        r += kv.first + ":";
+        char tmp[48];
+        for (size_t k = 0; k < kv.second.size(); ++k) {
+            snprintf(tmp, sizeof(tmp), " c%d=%.4f", (int)(k % kTuneN), kv.second[k]);
+            r += tmp;
+        }
+        auto it = c->tune_best.find(kv.first);
+        if (it != c->tune_best.end()) {
+            snprintf(tmp, sizeof(tmp), " -> c%d", it->second);
+            r += tmp;
+        }
+        r += "\n";
+    }
+    const size_t n = std::min(cap - 1, r.size());
+    memcpy(buf, r.data(), n);
+    buf[n] = 0;
+    return PRENOM_OK;
+}
+
 int prenom_zero_grads(prenom_ctx *c, int32_t obj)
 {
     Object *o = get_obj(c, obj);

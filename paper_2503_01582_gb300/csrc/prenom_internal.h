@@ -149,6 +149,22 @@ struct AdamArgs {
 constexpr int kAdamChunk = 4096;  // floats per chunk
 cudaError_t launch_adam(const AdamArgs &a, int grid, cudaStream_t st);
 
+// Reptile meta step (§III-A): broadcast of the meta-parameters to the task
+// objects (with zeroed gradient and Adam state), the task sum, and the outer
+// update of Eq. 2.
+constexpr int kMaxReptileTasks = 128;
+enum ReptileOp : int { kReptileBroadcast = 0, kReptileSum = 1, kReptileApply = 2 };
+struct ReptileArgs {
+    int32_t n_tasks;
+    int64_t n;       // parameters
+    int64_t n_pad;   // stride of the arrays in a task's arena (a multiple of 64)
+    float beta, nf;  // step size and the total number of tasks (as float)
+    float *meta;     // meta theta (broadcast source; updated by sum-with-meta and apply)
+    float *sum;      // task sum (output of a sum without meta, input of apply)
+    float *theta[kMaxReptileTasks];  // each task's arena: theta, grad, m, v at n_pad strides
+};
+cudaError_t launch_reptile(const ReptileArgs &a, int op, int grid, cudaStream_t st);
+
 // Random initialisation of theta: hash entries U(-1e-4, 1e-4), MLP Xavier-uniform.
 cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_shape /*[2*(H+1)]*/,
                                int n_layers, uint64_t seed, uint32_t obj, int grid, cudaStream_t st);

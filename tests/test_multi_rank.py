@@ -122,3 +122,97 @@ def test_two_gloo_ranks_agree_on_partition_and_time(orc, tmp_path):
         assert everyone == parts  # every rank derived the same partition
         assert tmax == pytest.approx(makespan(costs, parts))
     assert sorted(i for p in parts for i in p) == list(range(len(costs)))
+
+
+# ------------------------------------------------------- multi-GPU Reptile meta step (host flow)
+class _HostCtx:
+    """Stands in for a Context on the CPU: parameters are float64 numpy arrays and
+    the inner "training" moves each task by a fixed per-task offset, so the meta
+    step's flow (begin, inner steps, task sum, all-reduce, apply) runs over gloo."""
+
+    def __init__(self, n_params, theta0):
+        self.theta = {0: np.array(theta0, np.float64)}
+        self.n = n_params
+
+    def param_count(self, obj):
+        return self.n
+
+    def reptile_begin(self, meta, tasks):
+        for t in tasks:
+            self.theta[t] = self.theta[meta].copy()
+
+    def train_step(self, batches, opts, loss=None):
+        for b in batches:
+            self.theta[b["obj"]] += b["delta"]
+
+    def reptile_update(self, meta, tasks, beta):
+        import oracle
+
+        oracle.reptile(self.theta[meta], [self.theta[t] for t in tasks], beta)
+
+    def reptile_task_sum(self, tasks, out):
+        import torch
+
+        out.copy_(torch.from_numpy(np.sum([self.theta[t] for t in tasks], axis=0)))
+
+    def reptile_apply(self, meta, task_sum, n_total, beta):
+        import oracle
+
+        mean = task_sum.numpy().astype(np.float64) / n_total
+        oracle.reptile(self.theta[meta], [mean], beta)
+
+    def sync(self):
+        pass
+
+
+def _meta_worker(rank, world, port, n_tasks, out_dir):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_01582_gb300.meta import meta_step, split_tasks
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    rng = np.random.default_rng(0)
+    theta0 = rng.normal(size=64)
+    deltas = rng.normal(size=(n_tasks, 64))
+    mine = split_tasks(n_tasks, world, rank)
+    ctx = _HostCtx(64, theta0)
+    ids = [1 + t for t in mine]
+    inner = [[dict(obj=1 + t, delta=deltas[t] / 3) for t in mine] for _ in range(3)]
+    n_total = meta_step(ctx, 0, ids, inner, None, 0.25, group=dist.group.WORLD,
+                        task_sum=torch.zeros(64, dtype=torch.float64))
+    np.save(os.path.join(out_dir, f"meta{rank}.npy"), ctx.theta[0])
+    with open(os.path.join(out_dir, f"n{rank}.txt"), "w") as f:
+        f.write(str(n_total))
+    dist.destroy_process_group()
+
+
+def test_split_tasks_covers_evenly():
+    from paper_2503_01582_gb300.meta import split_tasks
+
+    for n in (0, 1, 5, 16, 17):
+        for world in (1, 2, 3, 8):
+            parts = [split_tasks(n, world, r) for r in range(world)]
+            assert sorted(i for p in parts for i in p) == list(range(n))
+            assert max(map(len, parts)) - min(map(len, parts)) <= 1
+
+
+def test_two_gloo_ranks_meta_step_equals_single_process(orc, tmp_path):
+    """Tasks split over two ranks, sums all-reduced, outer update applied on each
+    rank: every rank ends with the meta-parameters of the whole meta-batch
+    updated at once (Eq. 2 over all 5 tasks)."""
+    import torch.multiprocessing as mp
+
+    n_tasks = 5
+    mp.start_processes(_meta_worker, args=(2, _free_port(), n_tasks, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    rng = np.random.default_rng(0)
+    theta0 = rng.normal(size=64)
+    deltas = rng.normal(size=(n_tasks, 64))
+    want = theta0.copy()
+    orc.reptile(want, [theta0 + d for d in deltas], 0.25)
+    for r in range(2):
+        assert open(tmp_path / f"n{r}.txt").read() == str(n_tasks)
+        np.testing.assert_allclose(np.load(tmp_path / f"meta{r}.npy"), want, rtol=0, atol=1e-12)
