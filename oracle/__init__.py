@@ -120,6 +120,8 @@ def lib():
                                 C.c_double, C.c_double]),
             "orc_philox4x32_10": (None, [_U32, _U32, _U32]),
             "orc_reptile": (None, [C.c_int64, _D, C.POINTER(_D), C.c_int, C.c_double]),
+            "orc_density_grid": (None, [A, _D, C.c_int, _D]),
+            "orc_canonical_yaw": (C.c_int, [_D, C.c_int, _D, C.c_int, C.c_int, _D]),
             "orc_philox_uniforms": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, _F]),
             "orc_philox_colours": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, _F]),
         }
@@ -311,6 +313,24 @@ def adam(theta, m, v, g, step: int, lr: float, beta1: float = 0.9, beta2: float 
         assert x.dtype == np.float64 and x.flags.c_contiguous
     g = _d(g)
     lib().orc_adam(theta.size, _p(theta), _p(m), _p(v), _p(g), step, lr, beta1, beta2, eps)
+
+
+def density_grid(a: Arch, theta, R: int):
+    """[R, R, R] (z, y, x) density of the field at the voxel centres."""
+    th = _d(theta)
+    out = np.zeros((R, R, R))
+    lib().orc_density_grid(C.byref(a.c()), _p(th), R, _p(out))
+    return out
+
+
+def canonical_yaw(grid, P, n_gamma: int):
+    """Eq. 3: (index of the best yaw sample, scores of all n_gamma samples)."""
+    g = _d(grid)
+    R = g.shape[0]
+    pts = _d(np.asarray(P).reshape(-1, 3))
+    score = np.zeros(n_gamma)
+    best = lib().orc_canonical_yaw(_p(g), R, _p(pts), pts.shape[0], n_gamma, _p(score))
+    return best, score
 
 
 def reptile(theta, tasks, beta: float):

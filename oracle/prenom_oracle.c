@@ -608,6 +608,76 @@ void orc_adam(int64_t n, double *theta, double *m, double *v, const double *g, i
     }
 }
 
+/* ========================================================= prior grid
+ * §III-A "Normalized mesh generation": the prior density grid is the density
+ * output of the NeRF over a cubic grid of resolution R; §III-B refreshes it the
+ * same way every m iterations.  Reading: the value of voxel (i, j, k) is the
+ * field's density sigma = exp(min(o_0, 15)) at the voxel centre
+ * ((i+1/2)/R, (j+1/2)/R, (k+1/2)/R), x fastest -- the convention of the
+ * trilinear lookup of Eq. 3. */
+void orc_density_grid(const orc_arch *a, const double *theta, int R, double *grid)
+{
+    const int IN = a->L * a->F, W = a->width, H = a->hidden;
+    double *enc = (double *)malloc(sizeof(double) * (size_t)IN);
+    double *acts = (double *)malloc(sizeof(double) * (size_t)H * W);
+    double out[4];
+    for (int k = 0; k < R; ++k)
+        for (int j = 0; j < R; ++j)
+            for (int i = 0; i < R; ++i) {
+                const double p[3] = {(i + 0.5) / R, (j + 0.5) / R, (k + 0.5) / R};
+                orc_encode(a, theta, p, enc);
+                orc_mlp_forward(a, theta, enc, acts, out);
+                grid[((int64_t)k * R + j) * R + i] = exp(out[0] < 15.0 ? out[0] : 15.0);
+            }
+    free(enc);
+    free(acts);
+}
+
+/* §III-B "Object State Canonicalization", Eq. 3: for each sampled yaw
+ * gamma_g = 2 pi g / n_gamma the object cloud P (n points, object-centred frame,
+ * z up) is rotated about z by gamma_g, its extents S_gamma measured, and the
+ * normalised cloud P_gamma / S_gamma + 1/2 scored by the summed prior density
+ * (trilinear, orc_prior_lookup); the chosen yaw maximises the score.  Reading:
+ * "P_gamma / S_gamma + 1/2" centres P_gamma at the midpoint of its extents
+ * before the division, so the cloud fills [0, 1]^3; an axis of zero extent
+ * maps to 1/2.  Returns the first index of the largest score. */
+int orc_canonical_yaw(const double *grid, int R, const double *P, int n, int n_gamma, double *score)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double *q = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    int best = 0;
+    for (int g = 0; g < n_gamma; ++g) {
+        const double gamma = two_pi * (double)g / (double)n_gamma;
+        const double c = cos(gamma), s = sin(gamma);
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int j = 0; j < n; ++j) {
+            const double *x = P + 3 * (int64_t)j;
+            double *y = q + 3 * (int64_t)j;
+            y[0] = c * x[0] - s * x[1];
+            y[1] = s * x[0] + c * x[1];
+            y[2] = x[2];
+            for (int a = 0; a < 3; ++a) {
+                if (y[a] < lo[a]) lo[a] = y[a];
+                if (y[a] > hi[a]) hi[a] = y[a];
+            }
+        }
+        double sum = 0.0;
+        for (int j = 0; j < n; ++j) {
+            double pn[3];
+            for (int a = 0; a < 3; ++a) {
+                const double S = hi[a] - lo[a];
+                pn[a] = S > 0.0 ? (q[3 * (int64_t)j + a] - 0.5 * (lo[a] + hi[a])) / S + 0.5 : 0.5;
+            }
+            sum += orc_prior_lookup(grid, R, pn);
+        }
+        score[g] = sum;
+        if (sum > score[best])
+            best = g;
+    }
+    free(q);
+    return best;
+}
+
 /* ============================================================== Reptile
  * §III-A, Eq. 2: after q inner steps on task i, the meta-parameters move toward
  * the task's parameters, theta <- theta + beta (theta_i^(q) - theta).  Reading

@@ -19,7 +19,9 @@
  *   - reverse-mode gradients of that loss and the Adam update that the
  *     paper's last sentence of §III-B names;
  *   - §III-A "Meta-learning": the Reptile outer update (Eq. 2) after inner
- *     training steps (Eq. 1).
+ *     training steps (Eq. 1);
+ *   - §III-A "Normalized mesh generation" / §III-B: the prior density grid
+ *     from the field, and the yaw canonicalisation of Eq. 3.
  * Readings of points the paper leaves open are listed beside each routine.
  *
  * Parameter vector layout (shared by contract with the library's interface,
@@ -99,6 +101,10 @@ double orc_batch(const orc_arch *a, const double *theta, const double *grid, int
 /* ---- Adam (§III-B, last sentence) ---- */
 void orc_adam(int64_t n, double *theta, double *m, double *v, const double *g, int step,
               double lr, double beta1, double beta2, double eps);
+
+/* ---- prior density grid (§III-A mesh generation, §III-B refresh) and Eq. 3 ---- */
+void orc_density_grid(const orc_arch *a, const double *theta, int R, double *grid);
+int  orc_canonical_yaw(const double *grid, int R, const double *P, int n, int n_gamma, double *score);
 
 /* ---- Reptile outer update (§III-A, Eq. 2; batched over n_tasks) ---- */
 void orc_reptile(int64_t n, double *theta, const double *const *tasks, int n_tasks, double beta);

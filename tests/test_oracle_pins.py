@@ -545,3 +545,81 @@ def test_meta_step_composes_inner_training_and_outer_update(orc):
     # theta + 1 (x - theta) equals x up to one rounding of the subtraction and the sum
     np.testing.assert_allclose(th, ob.theta, rtol=0, atol=4 * np.finfo(np.float64).eps * np.abs(ob.theta).max())
     assert losses == [[l0, l1]] and l1 < l0
+
+
+# ------------------------------------------------------------- prior grid refresh and Eq. 3
+def _affine_field_arch(orc):
+    # two dense levels (N = 4, 8: (N+1)^3 <= 2^12), one hidden layer of 16
+    return orc.Arch(L=2, F=2, log2T=12, n_min=4, n_max=8, width=16, hidden=1, lambda_d=0.1, lambda_sigma=0.0)
+
+
+def test_density_grid_closed_forms(orc):
+    a = _affine_field_arch(orc)
+    theta = np.zeros(orc.param_count(a))
+    R = 6
+    # zero output weights: o_0 = 0, sigma = 1 everywhere
+    np.testing.assert_array_equal(orc.density_grid(a, theta, R), np.ones((R, R, R)))
+    # features affine in the vertex position (reproduced exactly by trilinear
+    # interpolation), positive so ReLU passes them: level 0 = (1+x, 1+y),
+    # level 1 = (1+z, 1); hidden units copy the first three features; o_0 mixes them
+    for l in range(2):
+        N = orc.level_res(a, l)
+        off = orc.level_offset(a, l)
+        for cz in range(N + 1):
+            for cy in range(N + 1):
+                for cx in range(N + 1):
+                    e = orc.grid_index(a, l, cx, cy, cz)
+                    f = (1 + cx / N, 1 + cy / N) if l == 0 else (1 + cz / N, 1.0)
+                    theta[off + 2 * e: off + 2 * e + 2] = f
+    w1 = orc.mlp_offset(a, 0)
+    for h in range(3):
+        theta[w1 + h * 4 + h] = 1.0  # W_1 [16][4]: h0 = e0, h1 = e1, h2 = e2
+    wo = orc.mlp_offset(a, 1)
+    theta[wo: wo + 3] = [0.5, 0.25, 0.125]  # row 0 of W_out [4][16]
+    g = orc.density_grid(a, theta, R)
+    c = (np.arange(R) + 0.5) / R
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    np.testing.assert_allclose(g, np.exp(0.5 * (1 + x) + 0.25 * (1 + y) + 0.125 * (1 + z)), rtol=1e-13)
+
+
+def _l_shape(n=600, seed=0):
+    """Points of an L with unequal arms in the x-y plane (no rotational symmetry), z in [-0.2, 0.2]."""
+    rng = np.random.default_rng(seed)
+    a = np.c_[rng.uniform(-0.5, 0.5, n // 2), rng.uniform(-0.5, -0.3, n // 2)]  # long arm along x
+    b = np.c_[rng.uniform(-0.5, -0.3, n // 2), rng.uniform(-0.3, 0.2, n // 2)]  # short arm along y
+    xy = np.r_[a, b]
+    return np.c_[xy, rng.uniform(-0.2, 0.2, xy.shape[0])]
+
+
+def _splat(P, R):
+    """Density grid of a cloud already in [0,1]^3: points per voxel (a prior of that exact pose)."""
+    g = np.zeros((R, R, R))
+    idx = np.clip((P * R).astype(int), 0, R - 1)
+    np.add.at(g, (idx[:, 2], idx[:, 1], idx[:, 0]), 1.0)
+    return g
+
+
+def _normalise(P):
+    lo, hi = P.min(0), P.max(0)
+    return (P - 0.5 * (lo + hi)) / (hi - lo) + 0.5
+
+
+def test_canonical_yaw_recovers_the_prior_pose(orc):
+    P = _l_shape()
+    grid = _splat(_normalise(P), 16)
+    n_gamma = 36
+    # a constant prior scores every yaw alike: c x |P|
+    best, score = orc.canonical_yaw(np.full((8, 8, 8), 2.5), P, n_gamma)
+    assert best == 0
+    np.testing.assert_allclose(score, 2.5 * P.shape[0], rtol=1e-13)
+    for g0 in (0, 5, 13, 27):
+        ang = -2 * np.pi * g0 / n_gamma  # the observed cloud is the canonical one turned by -gamma_g0
+        c, s = np.cos(ang), np.sin(ang)
+        Q = P @ np.array([[c, -s, 0], [s, c, 0], [0, 0, 1]]).T
+        best, score = orc.canonical_yaw(grid, Q, n_gamma)
+        assert best == g0, (g0, best)
+        # turning the cloud by one more yaw step shifts the scores by one sample
+        c1, s1 = np.cos(-2 * np.pi / n_gamma), np.sin(-2 * np.pi / n_gamma)
+        Q1 = Q @ np.array([[c1, -s1, 0], [s1, c1, 0], [0, 0, 1]]).T
+        _, score1 = orc.canonical_yaw(grid, Q1, n_gamma)
+        np.testing.assert_allclose(score1, np.roll(score, 1), rtol=1e-9, atol=1e-9 * score.max())
