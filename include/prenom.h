@@ -271,6 +271,33 @@ PRENOM_API int prenom_reptile_update(prenom_ctx *ctx, int32_t meta, const int32_
 PRENOM_API int prenom_reptile_task_sum(prenom_ctx *ctx, const int32_t *tasks, int32_t n_tasks, float *sum);
 PRENOM_API int prenom_reptile_apply(prenom_ctx *ctx, int32_t meta, const float *sum, int32_t n_total, float beta);
 
+/* ------------------------------------------- prior density grid (§III-A, §III-B)
+ * prenom_density_grid: the object's density field sampled at the centres of
+ * an res^3 grid over the unit cube (§III-A "Normalized mesh generation": the
+ * NeRF's density output over a cubic grid of resolution R is the prior density
+ * grid): grid_out[(k res + j) res + i] = exp(min(o_0, 15)) at
+ * ((i+1/2)/res, (j+1/2)/res, (k+1/2)/res), x fastest -- the layout
+ * prenom_set_prior_grid takes.  grid_out: device, res^3 floats, caller-owned;
+ * 4 <= res <= 64.  Computed by the object's own forward kernel (a mixed-
+ * precision object evaluates its MLP in its 16-bit format).  Stream-ordered.
+ * prenom_refresh_prior: the same density written over the object's prior
+ * grid (§III-B updates the prior every m iterations so that sampling follows
+ * the object as it is learnt); the grid is reallocated if res changes.
+ *
+ * prenom_canonical_yaw: Eq. 3 (§III-B "Object State Canonicalization") with
+ * the object's prior grid: for gamma_g = 2 pi g / n_gamma, g < n_gamma, the
+ * cloud points (device, [n_points][3] FP32, object frame centred on the
+ * object, z up) is turned about z by gamma_g, centred at the midpoint of its
+ * extents and divided by them (+1/2, an axis of zero extent maps to 1/2), and
+ * scored by the sum of the prior's trilinear density over its points (each
+ * lookup FP32, the sum FP64 in a fixed order).  best (host) receives the first
+ * g of largest score; scores (host or device, n_gamma floats) may be NULL.
+ * Blocking (reads the scores back).  n_gamma <= 65536. */
+PRENOM_API int prenom_density_grid(prenom_ctx *ctx, int32_t obj, int32_t res, float *grid_out);
+PRENOM_API int prenom_refresh_prior(prenom_ctx *ctx, int32_t obj, int32_t res);
+PRENOM_API int prenom_canonical_yaw(prenom_ctx *ctx, int32_t obj, const float *points, int32_t n_points,
+                                    int32_t n_gamma, float *scores, int32_t *best);
+
 /* The autotuner's record as text (one line per group signature: the step
  * times in ms of each timed call, "cK" = candidate K, and the chosen candidate
  * after "->"; candidates of a mixed-precision group: c0 split form, c1..c3 the

@@ -206,6 +206,28 @@ class Context:
         """The autotuner's measured candidates and choices, one line per group signature."""
         return _abi.prenom_tuning_report(self._ctx)
 
+    # ---- prior density grid (§III-A mesh generation, §III-B refresh) and Eq. 3
+    def density_grid(self, obj: int, res: int):
+        """[res, res, res] (z, y, x) CUDA tensor: the field's density at the voxel centres."""
+        import torch
+
+        out = torch.empty((res, res, res), device="cuda")
+        _abi.prenom_density_grid(self._ctx, obj, res, out.data_ptr())
+        return out
+
+    def refresh_prior(self, obj: int, res: int):
+        """Replaces the object's prior grid by its own density at resolution res."""
+        _abi.prenom_refresh_prior(self._ctx, obj, res)
+
+    def canonical_yaw(self, obj: int, points, n_gamma: int):
+        """Eq. 3 with the object's prior grid: (best yaw index, scores [n_gamma])."""
+        import torch
+
+        scores = torch.empty(n_gamma, device="cuda")
+        best = _abi.prenom_canonical_yaw(self._ctx, obj, _dptr(points, torch.float32, "points"), points.shape[0],
+                                         n_gamma, scores.data_ptr())
+        return best, scores
+
     # ---- Reptile meta step (§III-A, Eq. 1-2)
     def reptile_begin(self, meta: int, tasks):
         """Every task object <- the meta object's parameters, fresh Adam state."""

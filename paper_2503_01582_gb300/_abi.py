@@ -91,6 +91,9 @@ _SIGS = {
     "prenom_set_step": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "prenom_zero_grads": (C.c_int, [_CTX, C.c_int32]),
     "prenom_tuning_report": (C.c_int, [_CTX, C.c_char_p, C.c_size_t]),
+    "prenom_density_grid": (C.c_int, [_CTX, C.c_int32, C.c_int32, _P]),
+    "prenom_refresh_prior": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
+    "prenom_canonical_yaw": (C.c_int, [_CTX, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.POINTER(C.c_int32)]),
     "prenom_reptile_begin": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
     "prenom_reptile_update": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_float]),
     "prenom_reptile_task_sum": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.c_int32, _P]),
@@ -234,6 +237,21 @@ def prenom_tuning_report(ctx) -> str:
     buf = C.create_string_buffer(1 << 16)
     check(lib().prenom_tuning_report(ctx, buf, len(buf)), ctx)
     return buf.value.decode()
+
+
+def prenom_density_grid(ctx, obj: int, res: int, out_ptr: int):
+    check(lib().prenom_density_grid(ctx, obj, res, _P(out_ptr)), ctx)
+
+
+def prenom_refresh_prior(ctx, obj: int, res: int):
+    check(lib().prenom_refresh_prior(ctx, obj, res), ctx)
+
+
+def prenom_canonical_yaw(ctx, obj: int, points_ptr: int, n_points: int, n_gamma: int, scores_ptr: int) -> int:
+    best = C.c_int32()
+    check(lib().prenom_canonical_yaw(ctx, obj, _P(points_ptr), n_points, n_gamma, _P(scores_ptr or None),
+                                     C.byref(best)), ctx)
+    return best.value
 
 
 def _ids(tasks):

@@ -413,6 +413,8 @@ __device__ __forceinline__ float composite_warp(const ObjDesc &od, const BatchDe
             const int s = r * nr + k;
             o0[q] = OT[s];
             sig[q] = expf(fminf(o0[q], 15.f));
+            if (bd.out_sigma)
+                bd.out_sigma[(size_t)gr * nr + k] = sig[q];
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 col[q][c] = 1.f / (1.f + expf(-OT[(1 + c) * SP + s]));

@@ -115,6 +115,9 @@ extern "C" int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, 
         const int S = fused_fp32_pick_tile(od.W, od.IN, od.H, (size_t)optin);
         if (S == 0)
             return err(PRENOM_ERR_INVALID_ARG, "noalloc step: the architecture does not fit in shared memory");
+        if (opts->nr > S)
+            return err(PRENOM_ERR_INVALID_ARG, "noalloc step: nr = %lld exceeds the %lld-sample tile of this architecture",
+                       (long long)opts->nr, (long long)S);
         BatchDesc bd{};
         bd.n_rays = b.n_rays;
         bd.nc = opts->nc;

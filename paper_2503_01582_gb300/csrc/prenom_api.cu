@@ -75,6 +75,9 @@ struct prenom_ctx {
     // split form of mixed-precision training: the buffers its kernels hand over
     unsigned char *split_buf = nullptr;
     size_t split_cap = 0;
+    // density-grid queries and yaw scores
+    unsigned char *query_buf = nullptr;
+    size_t query_cap = 0;
 };
 
 namespace {
@@ -373,6 +376,8 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
     const int S = fused_fp32_pick_tile(od.W, od.IN, od.H, c->smem_optin);
     if (S == 0)
         return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
+    if (bd.nr > S)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "nr = %d exceeds the %d-sample tile of this architecture", bd.nr, S);
     bd.rays_per_tile = S / bd.nr;
     bd.n_tiles = (bd.n_rays + bd.rays_per_tile - 1) / bd.rays_per_tile;
     const int grid = std::min(bd.n_tiles, c->n_sm);
@@ -501,6 +506,9 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
             S = fused_fp32_pick_tile(o.arch.width, o.IN, o.arch.hidden, c->smem_optin);
             if (S == 0)
                 return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
+            if (op.nr > S)
+                return fail(c, PRENOM_ERR_INVALID_ARG, "nr = %d exceeds the %d-sample tile of this architecture",
+                            op.nr, S);
         }
         keys[i] = {o.arch.precision, o.arch.width, o.IN, S};
     }
@@ -885,6 +893,7 @@ void prenom_destroy(prenom_ctx *c)
     }
     cudaFree(c->d_work);
     cudaFree(c->split_buf);
+    cudaFree(c->query_buf);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -1301,6 +1310,122 @@ int prenom_reptile_apply(prenom_ctx *c, int32_t meta, const float *sum, int32_t 
     a.beta = beta;
     a.nf = (float)n_total;
     return reptile_launch(c, a, kReptileApply);
+}
+
+// ------------------------------------------------- prior grid and Eq. 3
+static int ensure_query(prenom_ctx *c, size_t bytes)
+{
+    if (bytes <= c->query_cap)
+        return PRENOM_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream");
+    cudaFree(c->query_buf);
+    c->query_buf = nullptr;
+    c->query_cap = 0;
+    e = cudaMalloc(&c->query_buf, bytes);
+    if (e != cudaSuccess)
+        return fail(c, PRENOM_ERR_OOM, "query buffers of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    c->query_cap = bytes;
+    return PRENOM_OK;
+}
+
+int prenom_density_grid(prenom_ctx *c, int32_t obj, int32_t res, float *grid_out)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    if (!grid_out || res < kMinNr || res > 64)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "grid_out must be non-NULL with %d <= res <= 64", kMinNr);
+    const size_t rays = (size_t)res * res, pts = rays * res;
+    int rc = ensure_query(c, (2 * 3 * rays + pts) * sizeof(float));
+    if (rc)
+        return rc;
+    float *qo = reinterpret_cast<float *>(c->query_buf), *qd = qo + 3 * rays, *qt = qd + 3 * rays;
+    cudaError_t e = launch_density_rays(res, qo, qd, qt, c->stream);
+    c->launches++;
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "density query rays");
+    prenom_ray_batch b{};
+    b.obj = obj;
+    b.n_rays = (int32_t)rays;
+    b.o = qo;
+    b.d = qd;
+    b.t_in = qt;
+    prenom_train_opts op{};
+    op.nc = res;
+    op.nr = res;
+    op.escape_eps = 1e-4f;
+    ObjDesc od = make_objdesc(*o, nullptr);
+    BatchDesc bd = make_batchdesc(c, *o, b, op, kRender, 128);
+    bd.out_sigma = grid_out;
+    bd.loss = c->scratch;
+    return launch_fused(c, *o, od, bd, PRENOM_KERNEL_RENDER);
+}
+
+int prenom_refresh_prior(prenom_ctx *c, int32_t obj, int32_t res)
+{
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    if (res < kMinNr || res > 64)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "res must lie in %d..64", kMinNr);
+    if (o->R != res) {  // the sampler may still read the old grid: wait for the stream
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "stream");
+        cudaFree(o->grid);
+        o->grid = nullptr;
+        o->R = 0;
+        e = cudaMalloc(&o->grid, (size_t)res * res * res * sizeof(float));
+        if (e != cudaSuccess)
+            return fail(c, PRENOM_ERR_OOM, "prior grid %d^3: %s", res, cudaGetErrorString(e));
+        o->R = res;
+    }
+    // the query renders with given sample depths, so the grid being replaced is never read
+    return prenom_density_grid(c, obj, res, o->grid);
+}
+
+int prenom_canonical_yaw(prenom_ctx *c, int32_t obj, const float *points, int32_t n_points, int32_t n_gamma,
+                         float *scores, int32_t *best)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    if (!o->grid)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "object %d has no prior grid", obj);
+    if (!points || n_points < 1 || n_gamma < 1 || n_gamma > 65536 || !best)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "points, n_points >= 1, 1 <= n_gamma <= 65536 and best are required");
+    int rc = ensure_query(c, (size_t)n_gamma * sizeof(double));
+    if (rc)
+        return rc;
+    double *d_score = reinterpret_cast<double *>(c->query_buf);
+    cudaError_t e = launch_yaw_scores(o->grid, o->R, points, n_points, n_gamma, d_score, c->stream);
+    c->launches++;
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "yaw score kernel launch");
+    std::vector<double> h(n_gamma);
+    e = cudaMemcpyAsync(h.data(), d_score, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "yaw scores");
+    int b = 0;
+    for (int g = 1; g < n_gamma; ++g)
+        if (h[g] > h[b])
+            b = g;
+    *best = b;
+    if (scores) {
+        std::vector<float> f(h.begin(), h.end());
+        e = cudaMemcpy(scores, f.data(), f.size() * sizeof(float), cudaMemcpyDefault);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "yaw scores copy");
+    }
+    return PRENOM_OK;
 }
 
 int prenom_tuning_report(prenom_ctx *c, char *buf, size_t cap)

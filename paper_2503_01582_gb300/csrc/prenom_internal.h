@@ -46,6 +46,7 @@ struct BatchDesc {
     const float *upstream;  // [n][5] for kRenderBwd
     float *loss;            // device scalar, accumulated (kTrain)
     float *out_rgb, *out_depth, *out_acc, *out_t;
+    float *out_sigma;       // optional [n][nr] density of every sample (render modes)
     int32_t *out_bins;
     uint64_t seed;
     uint32_t step, obj_id;
@@ -164,6 +165,12 @@ struct ReptileArgs {
     float *theta[kMaxReptileTasks];  // each task's arena: theta, grad, m, v at n_pad strides
 };
 cudaError_t launch_reptile(const ReptileArgs &a, int op, int grid, cudaStream_t st);
+
+// Prior density grid support: query rays of an R^3 grid of voxel centres, and
+// the yaw scores of Eq. 3 (one block per yaw sample, FP64 sums).
+cudaError_t launch_density_rays(int R, float *o, float *d, float *t, cudaStream_t st);
+cudaError_t launch_yaw_scores(const float *grid, int R, const float *P, int n, int n_gamma, double *score,
+                              cudaStream_t st);
 
 // Random initialisation of theta: hash entries U(-1e-4, 1e-4), MLP Xavier-uniform.
 cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_shape /*[2*(H+1)]*/,
