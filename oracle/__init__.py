@@ -121,6 +121,8 @@ def lib():
             "orc_philox4x32_10": (None, [_U32, _U32, _U32]),
             "orc_reptile": (None, [C.c_int64, _D, C.POINTER(_D), C.c_int, C.c_double]),
             "orc_density_grid": (None, [A, _D, C.c_int, _D]),
+            "orc_make_rays": (C.c_int64, [C.POINTER(_Keyframe), C.c_int, C.POINTER(_ObjState), C.c_int,
+                                          C.POINTER(C.c_uint32), _F, _F, _F, _F, C.POINTER(C.c_uint8)]),
             "orc_canonical_yaw": (C.c_int, [_D, C.c_int, _D, C.c_int, C.c_int, _D]),
             "orc_philox_uniforms": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, _F]),
             "orc_philox_colours": (None, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, _F]),
@@ -313,6 +315,49 @@ def adam(theta, m, v, g, step: int, lr: float, beta1: float = 0.9, beta2: float 
         assert x.dtype == np.float64 and x.flags.c_contiguous
     g = _d(g)
     lib().orc_adam(theta.size, _p(theta), _p(m), _p(v), _p(g), step, lr, beta1, beta2, eps)
+
+
+class _Keyframe(C.Structure):
+    _fields_ = [("width", C.c_int), ("height", C.c_int), ("rgb", C.POINTER(C.c_uint8)), ("depth", C.POINTER(C.c_float)),
+                ("mask", C.POINTER(C.c_int32)), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("R_wc", C.c_float * 9), ("t_wc", C.c_float * 3)]
+
+
+class _ObjState(C.Structure):
+    _fields_ = [("instance", C.c_int), ("R_wo", C.c_float * 9), ("centre", C.c_float * 3), ("size", C.c_float * 3)]
+
+
+def make_rays(keyframes, state, draws):
+    """Training rays from RGB-D keyframes (§III-B "Training Data").  keyframes:
+    dicts with rgb uint8 [H,W,3], depth float32 [H,W], mask int32 [H,W], fx, fy,
+    cx, cy, R_wc [3,3], t_wc [3]; state: dict(instance, R_wo [3,3], centre [3],
+    size [3]); draws: uint32 [n].  Returns (rays dict, number of candidates)."""
+    keep = []
+    arr = (_Keyframe * max(len(keyframes), 1))()
+    for i, k in enumerate(keyframes):
+        rgb = np.ascontiguousarray(k["rgb"], np.uint8)
+        dep = np.ascontiguousarray(k["depth"], np.float32)
+        msk = np.ascontiguousarray(k["mask"], np.int32)
+        keep += [rgb, dep, msk]
+        h, w = dep.shape
+        arr[i] = _Keyframe(w, h, rgb.ctypes.data_as(C.POINTER(C.c_uint8)), dep.ctypes.data_as(C.POINTER(C.c_float)),
+                           msk.ctypes.data_as(C.POINTER(C.c_int32)), k["fx"], k["fy"], k["cx"], k["cy"],
+                           (C.c_float * 9)(*np.asarray(k["R_wc"], np.float32).ravel()),
+                           (C.c_float * 3)(*np.asarray(k["t_wc"], np.float32).ravel()))
+    st = _ObjState(int(state["instance"]), (C.c_float * 9)(*np.asarray(state["R_wo"], np.float32).ravel()),
+                   (C.c_float * 3)(*np.asarray(state["centre"], np.float32).ravel()),
+                   (C.c_float * 3)(*np.asarray(state["size"], np.float32).ravel()))
+    dr = np.ascontiguousarray(draws, np.uint32)
+    n = dr.size
+    o = np.zeros((n, 3), np.float32)
+    d = np.zeros((n, 3), np.float32)
+    rgb = np.zeros((n, 3), np.float32)
+    depth = np.zeros(n, np.float32)
+    is_obj = np.zeros(n, np.uint8)
+    f = lambda a: a.ctypes.data_as(_F)  # noqa: E731
+    count = lib().orc_make_rays(arr, len(keyframes), C.byref(st), n, dr.ctypes.data_as(C.POINTER(C.c_uint32)), f(o),
+                                f(d), f(rgb), f(depth), is_obj.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return dict(o=o, d=d, rgb=rgb, depth=depth, is_obj=is_obj), int(count)
 
 
 def density_grid(a: Arch, theta, R: int):

@@ -608,6 +608,119 @@ void orc_adam(int64_t n, double *theta, double *m, double *v, const double *g, i
     }
 }
 
+/* ======================================================== training rays
+ * §III-B "Training Data": RGB-D images, instance masks and camera poses of
+ * the keyframes supervise the object's NeRF; "Probabilistic Ray Sampling":
+ * camera rays are transformed into the object frame with the estimated object
+ * pose and bounded by the object's box.  Readings: the object frame is the
+ * normalised one of Eq. 3, p_n = R_wo^T (p_w - c) / S + 1/2, so the box is
+ * the unit cube and the world ray parameter t (distance along the unit world
+ * direction) is kept: o_n = R_wo^T (o_w - c) / S + 1/2, d_n = R_wo^T d_w / S;
+ * a pixel (x, y) shoots through its centre (x + 1/2, y + 1/2) of a pinhole
+ * camera; its ray is a candidate when it meets the box, and, for a pixel of
+ * the object's instance, when its depth is valid (> 0, finite); the depth
+ * target of an object ray is the z-depth times the length of the
+ * unnormalised camera direction (x', y', 1), i.e. the distance t along the
+ * ray; a background ray (inside the box, not the instance) has no depth
+ * target.  Rays are drawn uniformly from all candidates of all keyframes
+ * (keyframe-major, row-major order): index = floor(r 2^-32 n_candidates) for a
+ * 32-bit random word r.
+ * Precision: these are geometric decisions that pick integers (candidate or
+ * not, which pixel), so they are taken in FP32 with the kernel's operation
+ * order (each operation rounded, no contraction); every output is then
+ * identical on both sides. */
+static int orc_ray_box_f(const float *o, const float *d)
+{
+    float t0 = 0.0f, t1 = INFINITY;
+    for (int i = 0; i < 3; ++i) {
+        if (d[i] != 0.0f) {
+            const float ta = (0.0f - o[i]) / d[i];
+            const float tb = (1.0f - o[i]) / d[i];
+            const float lo = ta < tb ? ta : tb, hi = ta < tb ? tb : ta;
+            if (lo > t0)
+                t0 = lo;
+            if (hi < t1)
+                t1 = hi;
+        } else if (o[i] < 0.0f || o[i] > 1.0f) {
+            t1 = -INFINITY;
+        }
+    }
+    return t1 > t0;
+}
+
+int orc_pixel_ray(const orc_keyframe *kf, const orc_object_state *st, int x, int y, float *o, float *d, float *rgb,
+                  float *depth, uint8_t *is_obj)
+{
+    const float u = (float)x + 0.5f, v = (float)y + 0.5f;
+    const float dc[3] = {(u - kf->cx) / kf->fx, (v - kf->cy) / kf->fy, 1.0f};
+    const float *R = kf->R_wc;
+    float dw[3];
+    for (int a = 0; a < 3; ++a)
+        dw[a] = (R[3 * a] * dc[0] + R[3 * a + 1] * dc[1]) + R[3 * a + 2];
+    const float nrm = sqrtf((dw[0] * dw[0] + dw[1] * dw[1]) + dw[2] * dw[2]);
+    float dh[3], rel[3];
+    for (int a = 0; a < 3; ++a) {
+        dh[a] = dw[a] / nrm;
+        rel[a] = kf->t_wc[a] - st->centre[a];
+    }
+    const float *Q = st->R_wo;  /* object-to-world; its transpose maps world to object */
+    for (int a = 0; a < 3; ++a) {
+        o[a] = ((Q[a] * rel[0] + Q[3 + a] * rel[1]) + Q[6 + a] * rel[2]) / st->size[a] + 0.5f;
+        d[a] = ((Q[a] * dh[0] + Q[3 + a] * dh[1]) + Q[6 + a] * dh[2]) / st->size[a];
+    }
+    const int64_t pix = (int64_t)y * kf->width + x;
+    const int obj = kf->mask[pix] == st->instance;
+    const float D = kf->depth[pix];
+    const int valid = D > 0.0f && isfinite(D);
+    for (int c = 0; c < 3; ++c)
+        rgb[c] = (float)kf->rgb[3 * pix + c] / 255.0f;
+    *depth = obj ? D * nrm : 0.0f;
+    *is_obj = (uint8_t)obj;
+    return orc_ray_box_f(o, d) && (!obj || valid);
+}
+
+int64_t orc_make_rays(const orc_keyframe *kfs, int n_kf, const orc_object_state *st, int n, const uint32_t *draws,
+                      float *o, float *d, float *rgb, float *depth, uint8_t *is_obj)
+{
+    int64_t total = 0;
+    for (int k = 0; k < n_kf; ++k)
+        total += (int64_t)kfs[k].width * kfs[k].height;
+    int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * (size_t)(total > 0 ? total : 1));
+    int64_t count = 0, base = 0;
+    float to[3], td[3], tc[3], tdep;
+    uint8_t tob;
+    for (int k = 0; k < n_kf; ++k) {
+        for (int y = 0; y < kfs[k].height; ++y)
+            for (int x = 0; x < kfs[k].width; ++x)
+                if (orc_pixel_ray(&kfs[k], st, x, y, to, td, tc, &tdep, &tob))
+                    cand[count++] = base + (int64_t)y * kfs[k].width + x;
+        base += (int64_t)kfs[k].width * kfs[k].height;
+    }
+    for (int j = 0; j < n; ++j) {
+        if (count == 0) {  /* nothing to draw: a ray that misses the box and renders to zero */
+            for (int a = 0; a < 3; ++a) {
+                o[3 * j + a] = -1.0f;
+                d[3 * j + a] = 0.0f;
+                rgb[3 * j + a] = 0.0f;
+            }
+            depth[j] = 0.0f;
+            is_obj[j] = 0;
+            continue;
+        }
+        const int64_t pick = cand[(int64_t)(((uint64_t)draws[j] * (uint64_t)count) >> 32)];
+        int k = 0;
+        int64_t off = pick;
+        while (off >= (int64_t)kfs[k].width * kfs[k].height) {
+            off -= (int64_t)kfs[k].width * kfs[k].height;
+            ++k;
+        }
+        orc_pixel_ray(&kfs[k], st, (int)(off % kfs[k].width), (int)(off / kfs[k].width), o + 3 * j, d + 3 * j,
+                      rgb + 3 * j, depth + j, is_obj + j);
+    }
+    free(cand);
+    return count;
+}
+
 /* ========================================================= prior grid
  * §III-A "Normalized mesh generation": the prior density grid is the density
  * output of the NeRF over a cubic grid of resolution R; §III-B refreshes it the

@@ -21,7 +21,9 @@
  *   - §III-A "Meta-learning": the Reptile outer update (Eq. 2) after inner
  *     training steps (Eq. 1);
  *   - §III-A "Normalized mesh generation" / §III-B: the prior density grid
- *     from the field, and the yaw canonicalisation of Eq. 3.
+ *     from the field, and the yaw canonicalisation of Eq. 3;
+ *   - §III-B "Training Data": object-frame training rays from RGB-D
+ *     keyframes, masks and poses.
  * Readings of points the paper leaves open are listed beside each routine.
  *
  * Parameter vector layout (shared by contract with the library's interface,
@@ -101,6 +103,27 @@ double orc_batch(const orc_arch *a, const double *theta, const double *grid, int
 /* ---- Adam (§III-B, last sentence) ---- */
 void orc_adam(int64_t n, double *theta, double *m, double *v, const double *g, int step,
               double lr, double beta1, double beta2, double eps);
+
+/* ---- training rays from RGB-D keyframes (§III-B "Training Data") ---- */
+typedef struct {
+    int width, height;
+    const uint8_t *rgb;   /* [H][W][3] */
+    const float *depth;   /* [H][W] z-depth */
+    const int32_t *mask;  /* [H][W] instance ids */
+    float fx, fy, cx, cy;
+    float R_wc[9];        /* camera-to-world rotation, row-major */
+    float t_wc[3];        /* camera centre */
+} orc_keyframe;
+typedef struct {
+    int instance;
+    float R_wo[9];        /* object-to-world rotation, row-major */
+    float centre[3];
+    float size[3];
+} orc_object_state;
+int     orc_pixel_ray(const orc_keyframe *kf, const orc_object_state *st, int x, int y, float *o, float *d,
+                      float *rgb, float *depth, uint8_t *is_obj);
+int64_t orc_make_rays(const orc_keyframe *kfs, int n_kf, const orc_object_state *st, int n, const uint32_t *draws,
+                      float *o, float *d, float *rgb, float *depth, uint8_t *is_obj);
 
 /* ---- prior density grid (§III-A mesh generation, §III-B refresh) and Eq. 3 ---- */
 void orc_density_grid(const orc_arch *a, const double *theta, int R, double *grid);

@@ -18,6 +18,9 @@ from .scenes import (  # noqa: F401
     cameras_on_sphere,
     RayPool,
     make_ray_pool,
+    object_pose,
+    keyframe_cameras,
+    render_keyframe,
     prior_grid,
     stratified_uniforms,
     random_colours,

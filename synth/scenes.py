@@ -344,3 +344,63 @@ def sample_batch(pool: RayPool, n: int, seed: int) -> dict:
         depth=np.ascontiguousarray(pool.depth[idx]),
         is_obj=np.ascontiguousarray(pool.is_obj[idx]),
     )
+
+
+# ------------------------------------------------------------ RGB-D keyframes
+def object_pose(centre, yaw: float, size):
+    """World placement of the unit-cube scene: p_w = R_wo ((p - 1/2) * size) + centre,
+    R_wo a turn by `yaw` about the world z axis."""
+    c, s = np.cos(yaw), np.sin(yaw)
+    R = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    return R, np.asarray(centre, np.float64), np.asarray(size, np.float64)
+
+
+def keyframe_cameras(n: int, centre, radius: float, seed: int):
+    """n camera-to-world poses (R_wc with columns right, down, forward; t_wc) on a
+    ring above `centre`, looking at it (pinhole convention: x right, y down)."""
+    rng = np.random.default_rng(seed)
+    poses = []
+    for _ in range(n):
+        az = rng.uniform(0.0, 2.0 * np.pi)
+        el = rng.uniform(0.2, 0.9)
+        eye = np.asarray(centre) + radius * np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+        fwd = np.asarray(centre) - eye
+        fwd /= np.linalg.norm(fwd)
+        right = np.cross(fwd, np.array([0.0, 0.0, 1.0]))
+        right /= np.linalg.norm(right)
+        down = np.cross(fwd, right)
+        poses.append((np.stack([right, down, fwd], axis=1), eye))
+    return poses
+
+
+def render_keyframe(scene: Scene, pose, obj, height: int, width: int, fov_deg: float, instance: int,
+                    depth_noise: float = 0.0, seed: int = 0) -> dict:
+    """RGB (uint8), z-depth (float32, 0 where nothing is hit) and instance mask
+    (int32, `instance` on the object, 0 elsewhere) of the scene placed in the
+    world by obj = (R_wo, centre, size), seen by a pinhole camera pose = (R_wc, t_wc)."""
+    R_wc, t_wc = pose
+    R_wo, c, S = obj
+    f = 0.5 * height / np.tan(np.deg2rad(fov_deg) * 0.5)
+    cx, cy = 0.5 * width, 0.5 * height
+    ys, xs = np.mgrid[0:height, 0:width]
+    dc = np.stack([(xs + 0.5 - cx) / f, (ys + 0.5 - cy) / f, np.ones_like(xs, dtype=np.float64)], -1).reshape(-1, 3)
+    dw = dc @ R_wc.T
+    nrm = np.linalg.norm(dw, axis=-1)
+    dh = dw / nrm[:, None]
+    o_n = ((t_wc - c) @ R_wo) / S + 0.5
+    d_n = (dh @ R_wo) / S
+    dl = np.linalg.norm(d_n, axis=-1)
+    t, nrm_n, alb = scene.cast(np.broadcast_to(o_n, d_n.shape).copy(), d_n / dl[:, None])
+    hit = np.isfinite(t)
+    t_w = np.where(hit, t / dl, 0.0)  # the object-frame distance back to world units
+    n_w = (nrm_n / S) @ R_wo.T  # normals transform with the inverse transpose
+    n_w /= np.maximum(np.linalg.norm(n_w, axis=-1, keepdims=True), 1e-12)
+    shade = 0.2 + 0.8 * np.maximum(0.0, n_w @ LIGHT_DIR)
+    rgb = np.where(hit[:, None], np.clip(alb * shade[:, None], 0.0, 1.0), 0.1)
+    z = np.where(hit, t_w / nrm, 0.0)
+    if depth_noise > 0:
+        z = np.where(hit, z + np.random.default_rng(seed).normal(0.0, depth_noise, z.shape), 0.0)
+    return dict(rgb=np.round(rgb * 255).astype(np.uint8).reshape(height, width, 3),
+                depth=z.astype(np.float32).reshape(height, width),
+                mask=np.where(hit, instance, 0).astype(np.int32).reshape(height, width),
+                fx=f, fy=f, cx=cx, cy=cy, R_wc=R_wc.astype(np.float32), t_wc=t_wc.astype(np.float32))

@@ -623,3 +623,71 @@ def test_canonical_yaw_recovers_the_prior_pose(orc):
         Q1 = Q @ np.array([[c1, -s1, 0], [s1, c1, 0], [0, 0, 1]]).T
         _, score1 = orc.canonical_yaw(grid, Q1, n_gamma)
         np.testing.assert_allclose(score1, np.roll(score, 1), rtol=1e-9, atol=1e-9 * score.max())
+
+
+# ------------------------------------------------------------ training rays (§III-B "Training Data")
+def _kf_scene(seed=3, H=90, W=120, n_kf=2, yaw=0.7):
+    import synth
+
+    sc = synth.scene_random_csg(seed)
+    obj = synth.object_pose([1.0, 2.0, 0.4], yaw, [0.6, 0.5, 0.4])
+    kfs = [synth.render_keyframe(sc, p, obj, H, W, 50, 7) for p in synth.keyframe_cameras(n_kf, obj[1], 2.0, seed)]
+    state = dict(instance=7, R_wo=obj[0], centre=obj[1], size=obj[2])
+    return sc, obj, kfs, state
+
+
+def test_rays_identity_pose_and_principal_ray(orc):
+    H, W = 9, 11
+    kf = dict(rgb=np.full((H, W, 3), 51, np.uint8), depth=np.full((H, W), 2.25, np.float32),
+              mask=np.full((H, W), 3, np.int32), fx=100.0, fy=100.0, cx=5.5, cy=4.5,
+              R_wc=np.eye(3), t_wc=np.array([0.5, 0.5, -2.0]))
+    state = dict(instance=3, R_wo=np.eye(3), centre=[0.5, 0.5, 0.5], size=[1.0, 1.0, 1.0])
+    # pixel (5, 4) has its centre on the principal point: the ray is the camera axis
+    count = H * W
+    draw = np.array([int(((4 * W + 5) << 32) // count) + 1], np.uint32)  # the candidate index 4 W + 5
+    rays, n = orc.make_rays([kf], state, draw)
+    assert n == count  # every pixel's ray meets the unit cube 2 units away (offsets <= 2 x 0.055)
+    np.testing.assert_array_equal(rays["o"][0], [0.5, 0.5, -2.0])
+    np.testing.assert_array_equal(rays["d"][0], [0.0, 0.0, 1.0])
+    assert rays["depth"][0] == np.float32(2.25) and rays["is_obj"][0] == 1
+    np.testing.assert_array_equal(rays["rgb"][0], np.float32(51) / np.float32(255))
+    # the first and the last candidate are reached by the extreme draws
+    rays, _ = orc.make_rays([kf], state, np.array([0, 2 ** 32 - 1], np.uint32))
+    np.testing.assert_allclose(rays["d"][0], np.array([-5.0, -4.0, 100.0]) / np.sqrt(10041.0), rtol=1e-6)
+    np.testing.assert_allclose(rays["d"][1], np.array([5.0, 4.0, 100.0]) / np.sqrt(10041.0), rtol=1e-6)
+    # nothing in front of the camera: no candidate, the null ray
+    kf2 = dict(kf, t_wc=np.array([0.5, 0.5, 3.0]))
+    rays, n = orc.make_rays([kf2], state, np.array([7], np.uint32))
+    assert n == 0 and np.all(rays["o"][0] == -1) and np.all(rays["d"][0] == 0) and rays["is_obj"][0] == 0
+
+
+def test_rays_depth_target_lands_on_the_surface(orc):
+    """o + depth d of an object ray is the rendered surface point in the object
+    frame; every object pixel with depth is a candidate; background rays meet the box."""
+    sc, obj, kfs, state = _kf_scene()
+    rng = np.random.default_rng(0)
+    draws = rng.integers(0, 2 ** 32, 4000, dtype=np.uint64).astype(np.uint32)
+    rays, n = orc.make_rays(kfs, state, draws)
+    n_obj_pixels = sum(int((k["mask"] == 7).sum()) for k in kfs)
+    assert n_obj_pixels > 100 and n > n_obj_pixels
+    m = rays["is_obj"] == 1
+    assert 0 < m.sum() < len(m)
+    p = rays["o"][m].astype(np.float64) + rays["depth"][m, None] * rays["d"][m].astype(np.float64)
+    assert np.all(np.abs(sc.sdf(p)) < 2e-4)  # on the union's surface (FP32 inputs)
+    # background rays enter the unit cube (the box) and miss the shape
+    from synth.scenes import _hits_unit_cube
+
+    assert np.mean(_hits_unit_cube(rays["o"][~m].astype(np.float64), rays["d"][~m].astype(np.float64))) > 0.99
+    # the candidate count agrees with an FP64 count of box-hitting pixels up to grazing rays
+    brute = 0
+    for k in kfs:
+        H, W = k["depth"].shape
+        ys, xs = np.mgrid[0:H, 0:W]
+        dc = np.stack([(xs + 0.5 - k["cx"]) / k["fx"], (ys + 0.5 - k["cy"]) / k["fy"], np.ones((H, W))], -1)
+        dw = dc.reshape(-1, 3) @ np.asarray(k["R_wc"], np.float64).T
+        dh = dw / np.linalg.norm(dw, axis=1, keepdims=True)
+        R, c, S = obj
+        o_n = ((np.asarray(k["t_wc"], np.float64) - c) @ R) / S + 0.5
+        d_n = (dh @ R) / S
+        brute += int(_hits_unit_cube(np.broadcast_to(o_n, d_n.shape), d_n).sum())
+    assert abs(n - brute) <= 0.002 * brute + 4
