@@ -271,6 +271,59 @@ PRENOM_API int prenom_reptile_update(prenom_ctx *ctx, int32_t meta, const int32_
 PRENOM_API int prenom_reptile_task_sum(prenom_ctx *ctx, const int32_t *tasks, int32_t n_tasks, float *sum);
 PRENOM_API int prenom_reptile_apply(prenom_ctx *ctx, int32_t meta, const float *sum, int32_t n_total, float beta);
 
+/* ------------------------------------------------ training rays (§III-B)
+ * §III-B "Training Data": RGB-D images, instance masks and camera poses of the
+ * keyframes supervise the object; "Probabilistic Ray Sampling": camera rays
+ * are transformed into the object frame with the estimated object pose and
+ * bounded by the object's box.  prenom_make_rays turns keyframes into a ray
+ * batch of prenom_ray_batch's layout:
+ *   - object frame: p_n = R_wo^T (p_w - centre) / size + 1/2 (the normalised
+ *     frame of Eq. 3: the box is the unit cube); the world ray parameter t is
+ *     kept, so o = R_wo^T (t_wc - centre) / size + 1/2 and d = R_wo^T d_w / size
+ *     with d_w the unit world direction of the pixel;
+ *   - pixel (x, y) shoots through (x + 1/2, y + 1/2) of a pinhole camera:
+ *     camera direction ((x+1/2-cx)/fx, (y+1/2-cy)/fy, 1), rotated by R_wc;
+ *   - a pixel is a candidate when its ray meets the box and, when its mask
+ *     equals state->instance (an object ray, is_obj = 1), its depth is > 0 and
+ *     finite; other candidates are background rays (is_obj = 0);
+ *   - rgb target = rgb / 255; depth target of an object ray = z-depth times
+ *     |(x', y', 1)| (the distance t along the ray), 0 for background rays;
+ *   - n_rays rays are drawn uniformly from all candidates of all keyframes
+ *     (keyframe-major, row-major order): ray j takes candidate
+ *     floor(r_j n_candidates / 2^32), r_j = draws[j] (device uint32) or, with
+ *     draws NULL, word j mod 4 of Philox4x32-10(ctr = (j / 4, 0, call,
+ *     0x52415953), key = the context seed), call counting this context's
+ *     prenom_make_rays calls from 0;
+ *   - with no candidate every ray is o = (-1, -1, -1), d = 0, which misses
+ *     the box and renders to zero.
+ * The geometry is FP32 with every operation rounded (no contraction), in the
+ * order the formulas above are written.  keyframes and state: host; image
+ * pointers inside: device (rgb [height][width][3] u8, depth [height][width]
+ * FP32 z-depth, mask [height][width] int32).  o, d, rgb: device [n_rays][3];
+ * depth: device [n_rays]; is_obj: device [n_rays] u8 (all caller-owned).
+ * n_candidates: host, receives the candidate count when non-NULL (the call
+ * then waits for the stream).  At most 4096 keyframes and 2^31 - 1 pixels. */
+typedef struct {
+    int32_t width, height;
+    const uint8_t *rgb;
+    const float *depth;
+    const int32_t *mask;
+    float fx, fy, cx, cy; /* pinhole intrinsics in pixels */
+    float R_wc[9];        /* camera-to-world rotation, row-major (columns: camera x, y, viewing axis) */
+    float t_wc[3];        /* camera centre in the world */
+} prenom_keyframe;
+
+typedef struct {
+    int32_t instance;     /* mask id of the object */
+    float R_wo[9];        /* object-to-world rotation, row-major */
+    float centre[3];      /* world position of the box centre */
+    float size[3];        /* box extents along the object axes (> 0) */
+} prenom_object_state;
+
+PRENOM_API int prenom_make_rays(prenom_ctx *ctx, const prenom_keyframe *keyframes, int32_t n_keyframes,
+                                const prenom_object_state *state, int32_t n_rays, const uint32_t *draws, float *o,
+                                float *d, float *rgb, float *depth, uint8_t *is_obj, int64_t *n_candidates);
+
 /* ------------------------------------------- prior density grid (§III-A, §III-B)
  * prenom_density_grid: the object's density field sampled at the centres of
  * an res^3 grid over the unit cube (§III-A "Normalized mesh generation": the

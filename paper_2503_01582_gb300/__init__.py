@@ -206,6 +206,42 @@ class Context:
         """The autotuner's measured candidates and choices, one line per group signature."""
         return _abi.prenom_tuning_report(self._ctx)
 
+    # ---- training rays from RGB-D keyframes (§III-B "Training Data")
+    def make_rays(self, keyframes, state, n_rays: int, draws=None, count: bool = False):
+        """Ray batch (dict of CUDA tensors: o, d, rgb, depth, is_obj) drawn from the
+        keyframes' candidate pixels.  keyframes: dicts with CUDA tensors rgb (uint8
+        [H,W,3]), depth (float32 [H,W]), mask (int32 [H,W]) and fx, fy, cx, cy,
+        R_wc [3,3], t_wc [3]; state: dict(instance, R_wo [3,3], centre [3], size [3]);
+        draws: optional CUDA int32/uint32 words [n_rays].  With count=True also returns the
+        number of candidates (waits for the stream)."""
+        import numpy as np
+        import torch
+
+        kfs, keep = [], []
+        for k in keyframes:
+            rgb, dep, msk = (k["rgb"].contiguous(), k["depth"].contiguous(), k["mask"].contiguous())
+            keep += [rgb, dep, msk]
+            h, w = dep.shape
+            kfs.append(_abi.prenom_keyframe(
+                w, h, _dptr(rgb, torch.uint8, "rgb"), _dptr(dep, torch.float32, "depth"),
+                _dptr(msk, torch.int32, "mask"), float(k["fx"]), float(k["fy"]), float(k["cx"]), float(k["cy"]),
+                (_abi.C.c_float * 9)(*np.asarray(k["R_wc"], np.float32).ravel()),
+                (_abi.C.c_float * 3)(*np.asarray(k["t_wc"], np.float32).ravel())))
+        st = _abi.prenom_object_state(int(state["instance"]),
+                                      (_abi.C.c_float * 9)(*np.asarray(state["R_wo"], np.float32).ravel()),
+                                      (_abi.C.c_float * 3)(*np.asarray(state["centre"], np.float32).ravel()),
+                                      (_abi.C.c_float * 3)(*np.asarray(state["size"], np.float32).ravel()))
+        out = dict(o=torch.empty((n_rays, 3), device="cuda"), d=torch.empty((n_rays, 3), device="cuda"),
+                   rgb=torch.empty((n_rays, 3), device="cuda"), depth=torch.empty(n_rays, device="cuda"),
+                   is_obj=torch.empty(n_rays, dtype=torch.uint8, device="cuda"))
+        if draws is not None and (draws.is_floating_point() or draws.element_size() != 4):
+            raise TypeError("draws must hold 32-bit integer words (int32 or uint32)")
+        n = _abi.prenom_make_rays(self._ctx, kfs, st, n_rays, _dptr(draws, None, "draws"), out["o"].data_ptr(),
+                                  out["d"].data_ptr(), out["rgb"].data_ptr(), out["depth"].data_ptr(),
+                                  out["is_obj"].data_ptr(), count)
+        del keep
+        return (out, n) if count else out
+
     # ---- prior density grid (§III-A mesh generation, §III-B refresh) and Eq. 3
     def density_grid(self, obj: int, res: int):
         """[res, res, res] (z, y, x) CUDA tensor: the field's density at the voxel centres."""

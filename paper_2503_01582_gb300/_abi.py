@@ -52,6 +52,18 @@ class prenom_arch(C.Structure):
     ]
 
 
+class prenom_keyframe(C.Structure):
+    _fields_ = [
+        ("width", C.c_int32), ("height", C.c_int32), ("rgb", C.c_void_p), ("depth", C.c_void_p),
+        ("mask", C.c_void_p), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+        ("R_wc", C.c_float * 9), ("t_wc", C.c_float * 3),
+    ]
+
+
+class prenom_object_state(C.Structure):
+    _fields_ = [("instance", C.c_int32), ("R_wo", C.c_float * 9), ("centre", C.c_float * 3), ("size", C.c_float * 3)]
+
+
 class prenom_train_opts(C.Structure):
     _fields_ = [
         ("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
@@ -92,6 +104,8 @@ _SIGS = {
     "prenom_zero_grads": (C.c_int, [_CTX, C.c_int32]),
     "prenom_tuning_report": (C.c_int, [_CTX, C.c_char_p, C.c_size_t]),
     "prenom_density_grid": (C.c_int, [_CTX, C.c_int32, C.c_int32, _P]),
+    "prenom_make_rays": (C.c_int, [_CTX, C.POINTER(prenom_keyframe), C.c_int32, C.POINTER(prenom_object_state),
+                                   C.c_int32, _P, _P, _P, _P, _P, _P, C.POINTER(C.c_int64)]),
     "prenom_refresh_prior": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "prenom_canonical_yaw": (C.c_int, [_CTX, C.c_int32, _P, C.c_int32, C.c_int32, _P, C.POINTER(C.c_int32)]),
     "prenom_reptile_begin": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
@@ -237,6 +251,15 @@ def prenom_tuning_report(ctx) -> str:
     buf = C.create_string_buffer(1 << 16)
     check(lib().prenom_tuning_report(ctx, buf, len(buf)), ctx)
     return buf.value.decode()
+
+
+def prenom_make_rays(ctx, keyframes, state, n_rays: int, draws_ptr: int, o: int, d: int, rgb: int, depth: int,
+                     is_obj: int, want_count: bool) -> int:
+    arr = (prenom_keyframe * len(keyframes))(*keyframes)
+    cnt = C.c_int64(-1)
+    check(lib().prenom_make_rays(ctx, arr, len(keyframes), C.byref(state), n_rays, _P(draws_ptr or None), _P(o),
+                                 _P(d), _P(rgb), _P(depth), _P(is_obj), C.byref(cnt) if want_count else None), ctx)
+    return cnt.value
 
 
 def prenom_density_grid(ctx, obj: int, res: int, out_ptr: int):

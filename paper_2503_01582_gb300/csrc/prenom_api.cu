@@ -78,6 +78,10 @@ struct prenom_ctx {
     // density-grid queries and yaw scores
     unsigned char *query_buf = nullptr;
     size_t query_cap = 0;
+    // training-ray generation
+    unsigned char *rays_buf = nullptr;
+    size_t rays_cap = 0;
+    uint32_t ray_calls = 0;
 };
 
 namespace {
@@ -894,6 +898,7 @@ void prenom_destroy(prenom_ctx *c)
     cudaFree(c->d_work);
     cudaFree(c->split_buf);
     cudaFree(c->query_buf);
+    cudaFree(c->rays_buf);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -1321,12 +1326,75 @@ static int ensure_query(prenom_ctx *c, size_t bytes)
     if (e != cudaSuccess)
         return cuda_fail(c, e, "stream");
     cudaFree(c->query_buf);
+    cudaFree(c->rays_buf);
     c->query_buf = nullptr;
     c->query_cap = 0;
     e = cudaMalloc(&c->query_buf, bytes);
     if (e != cudaSuccess)
         return fail(c, PRENOM_ERR_OOM, "query buffers of %zu bytes: %s", bytes, cudaGetErrorString(e));
     c->query_cap = bytes;
+    return PRENOM_OK;
+}
+
+int prenom_make_rays(prenom_ctx *c, const prenom_keyframe *kfs, int32_t n_kf, const prenom_object_state *st,
+                     int32_t n_rays, const uint32_t *draws, float *o, float *d, float *rgb, float *depth,
+                     uint8_t *is_obj, int64_t *n_candidates)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!kfs || n_kf < 1 || n_kf > 4096 || !st || n_rays < 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "1..4096 keyframes, an object state and n_rays >= 0 are required");
+    if (n_rays > 0 && (!o || !d || !rgb || !depth || !is_obj))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "o, d, rgb, depth and is_obj are required");
+    for (int a = 0; a < 3; ++a)
+        if (!(st->size[a] > 0.f) || !isfinite(st->size[a]))
+            return fail(c, PRENOM_ERR_INVALID_ARG, "object size must be finite and > 0");
+    std::vector<int64_t> off(n_kf + 1, 0);
+    for (int k = 0; k < n_kf; ++k) {
+        const prenom_keyframe &f = kfs[k];
+        if (f.width < 1 || f.height < 1 || !f.rgb || !f.depth || !f.mask || !(f.fx != 0.f) || !(f.fy != 0.f))
+            return fail(c, PRENOM_ERR_INVALID_ARG, "keyframe %d: size, images and intrinsics are required", k);
+        off[k + 1] = off[k] + (int64_t)f.width * f.height;
+    }
+    const int64_t n_pix = off[n_kf];
+    if (n_pix >= ((int64_t)1 << 31))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "at most 2^31 - 1 pixels per call");
+    const size_t kf_bytes = ((size_t)n_kf * sizeof(prenom_keyframe) + 255) / 256 * 256;
+    const size_t off_bytes = ((size_t)(n_kf + 1) * sizeof(int64_t) + 255) / 256 * 256;
+    const size_t need = kf_bytes + off_bytes + make_rays_scratch(n_pix);
+    if (need > c->rays_cap) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "stream");
+        cudaFree(c->rays_buf);
+        c->rays_buf = nullptr;
+        c->rays_cap = 0;
+        e = cudaMalloc(&c->rays_buf, need);
+        if (e != cudaSuccess)
+            return fail(c, PRENOM_ERR_OOM, "ray-generation buffers of %zu bytes: %s", need, cudaGetErrorString(e));
+        c->rays_cap = need;
+    }
+    prenom_keyframe *d_kf = reinterpret_cast<prenom_keyframe *>(c->rays_buf);
+    int64_t *d_off = reinterpret_cast<int64_t *>(c->rays_buf + kf_bytes);
+    cudaError_t e = cudaMemcpyAsync(d_kf, kfs, (size_t)n_kf * sizeof(prenom_keyframe), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream);
+    int64_t *d_count = nullptr;
+    if (e == cudaSuccess)
+        e = launch_make_rays(d_kf, d_off, n_kf, n_pix, *st, c->rays_buf + kf_bytes + off_bytes, n_rays, draws,
+                             c->seed, c->ray_calls, o, d, rgb, depth, is_obj, &d_count, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "ray generation");
+    c->ray_calls += 1;
+    c->launches += n_pix > 0 ? 3 + (n_rays > 0) : (n_rays > 0);
+    if (n_candidates) {
+        e = cudaMemcpyAsync(n_candidates, d_count, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "candidate count");
+    }
     return PRENOM_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "prenom.h"
+
 namespace prenom {
 
 constexpr int kMaxLevels = 16;
@@ -165,6 +167,13 @@ struct ReptileArgs {
     float *theta[kMaxReptileTasks];  // each task's arena: theta, grad, m, v at n_pad strides
 };
 cudaError_t launch_reptile(const ReptileArgs &a, int op, int grid, cudaStream_t st);
+
+// Training rays from keyframes: candidate count, scan, compaction and the draws.
+size_t make_rays_scratch(int64_t n_pix);
+cudaError_t launch_make_rays(const prenom_keyframe *d_kf, const int64_t *d_pix_off, int n_kf, int64_t n_pix,
+                             const prenom_object_state &st, unsigned char *scratch, int n_rays, const uint32_t *draws,
+                             uint64_t seed, uint32_t call, float *o, float *d, float *rgb, float *depth,
+                             uint8_t *is_obj, int64_t **d_count, cudaStream_t st_);
 
 // Prior density grid support: query rays of an R^3 grid of voxel centres, and
 // the yaw scores of Eq. 3 (one block per yaw sample, FP64 sums).
