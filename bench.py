@@ -373,6 +373,59 @@ def _meta_compare(pkg, ctx, stream, prec):
             "value": n_smp * steps / (ms / 1e3), "unit": "samples/s", "ms_per_meta_step": ms / steps}
 
 
+def _ablation_compare(pkg, ctx, stream, prec, steps=300):
+    """Sampling ablation (the analogue of the paper's Table IV row on
+    probabilistic sampling): the small scene (sphere + box, 8 views of 64x64)
+    trained for `steps` Adam steps of 256 rays x 32 samples with prior sampling
+    over the 32^3 prior grid (as given, and refreshed from the field every 50
+    steps as §III-B does) and with uniform sampling (a zero grid: every ray
+    escapes, so the flat CDF of the escape rule applies), on the same rays; then
+    colour MSE (all pixels, black background) and depth L1 (object pixels) on 4
+    held-out 64x64 views, sampled the way each was trained."""
+    import torch
+    from synth import (cameras_on_sphere, init_params, make_ray_pool, prior_grid, sample_batch, scene_sphere_box)
+
+    sc = scene_sphere_box()
+    pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 40, 64, 64, 0), 65536, 0)
+    held = make_ray_pool(sc, cameras_on_sphere(4, 2.0, 40, 64, 64, 99), 4096, 99)
+    hb = {k: torch.from_numpy(np.ascontiguousarray(getattr(held, k))).cuda() for k in ("o", "d")}
+    tgt = np.where(held.is_obj[:, None] == 1, held.rgb, 0.0)
+    objm = held.is_obj == 1
+    arch = pkg.make_arch(L=8, log2T=14, n_min=16, n_max=256, width=32, hidden=2, lambda_d=0.1, lambda_sigma=0.0,
+                         precision=PRECISION[prec])
+    probe = ctx.create_object(arch)
+    n = ctx.param_count(probe)
+    ctx.destroy_object(probe)
+    theta = init_params(n - (32 * 16 + 32 * 32 + 4 * 32), [(32, 16), (32, 32), (4, 32)], 5).astype(np.float32)
+    batches = [_device_batches([sample_batch(pool, 256, 7000 + i)], 0, stream)[0] for i in range(steps)]
+    opts = pkg.make_opts(nc=32, nr=32, lr=1e-2)
+    loss = torch.zeros(1, device="cuda")
+    out = {}
+    prior = prior_grid(sc, 32, 0)
+    for name, grid, refresh in (("prior_sampling", prior, 0), ("prior_sampling_refresh_every_50", prior, 50),
+                                ("uniform_sampling", np.zeros((32, 32, 32), np.float32), 0)):
+        obj = ctx.create_object(arch, theta)
+        ctx.set_prior_grid(obj, grid)
+        for b in batches:
+            b["obj"] = obj
+
+        def step(i, obj=obj, refresh=refresh):
+            if refresh and i > 0 and i % refresh == 0:  # §III-B: the prior follows the field every m iterations
+                ctx.refresh_prior(obj, 32)
+            ctx.train_step([batches[i]], opts, loss)
+
+        ms = _time(stream, step, steps, 0)
+        r = ctx.render(dict(hb, obj=obj), opts)
+        rgb, depth = r["rgb"].cpu().numpy(), r["depth"].cpu().numpy()
+        out[name] = {"colour_mse": float(np.mean((rgb - tgt) ** 2)),
+                     "depth_l1": float(np.mean(np.abs(depth - held.depth)[objm])),
+                     "final_loss": float(loss.item()), "ms_per_step": ms / steps}
+        ctx.destroy_object(obj)
+    out["workload"] = ("sphere+box scene, %d Adam steps x 256 rays x 32 samples (Nc 32), L=8 T=2^14 res 16..256, "
+                       "MLP 16-32-32-4, same rays for both; 4 held-out 64x64 views" % steps)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -486,6 +539,7 @@ def run_ours(args):
 
     if world == 1 and not args.no_compare:
         compare["reptile_meta_step"] = _meta_compare(pkg, ctx, stream, prec)
+        compare["sampling_ablation"] = _ablation_compare(pkg, ctx, stream, prec)
 
     if world > 1 and not args.no_compare:
         # the 32-object workload split over the ranks (longest processing time
