@@ -599,7 +599,7 @@ def run_ours(args):
     if split:
         recs.append(hbm("sample_encode_kernel", pkg.PRENOM_KERNEL_SAMPLE_ENCODE, samples_per_step * feat_bytes,
                         f"{feat_bytes} B/sample hash gather x {samples_per_step} samples"))
-        recs.append(mlp("fused_tc_kernel", pkg.PRENOM_KERNEL_TRAIN))
+        recs.append(mlp("fused_tc_kernel_split", pkg.PRENOM_KERNEL_TRAIN))
         recs.append(hbm("hash_scatter_kernel", pkg.PRENOM_KERNEL_SCATTER, samples_per_step * feat_bytes,
                         f"{feat_bytes} B/sample hash scatter (FP32 reductions) x {samples_per_step} samples"))
     else:
