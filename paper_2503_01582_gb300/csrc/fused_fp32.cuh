@@ -547,14 +547,12 @@ __device__ __forceinline__ void stage_item(const WorkItem &src, WorkItem &dst)
     __syncthreads();
 }
 
-// A tile's ray data into shared memory (kRayStride floats per ray): four
-// threads per ray load the origin, the direction, the object targets and the
-// background colour in parallel, so the tile pays about one memory latency.
-__device__ __forceinline__ void load_ray_tile(const BatchDesc &bd, int ray0, int nrt, float *rayf)
+// One ray's data into its kRayStride shared-memory floats, in four parts
+// (f = 0 origin, 1 direction, 2 object targets, 3 background colour), so that
+// four threads load a ray in parallel and a tile pays about one memory latency.
+__device__ __forceinline__ void load_ray_fields(const BatchDesc &bd, int g, float *rf, int f)
 {
-    for (int i = threadIdx.x; i < nrt * 4; i += blockDim.x) {
-        const int r = i >> 2, f = i & 3, g = ray0 + r;
-        float *rf = rayf + r * kRayStride;
+    {
         if (f < 2) {
             const float *src = (f == 0 ? bd.o : bd.d) + (size_t)g * 3;
 #pragma unroll
@@ -582,6 +580,12 @@ __device__ __forceinline__ void load_ray_tile(const BatchDesc &bd, int ray0, int
             }
         }
     }
+}
+
+__device__ __forceinline__ void load_ray_tile(const BatchDesc &bd, int ray0, int nrt, float *rayf)
+{
+    for (int i = threadIdx.x; i < nrt * 4; i += blockDim.x)
+        load_ray_fields(bd, ray0 + (i >> 2), rayf + (i >> 2) * kRayStride, i & 3);
 }
 
 // Index of the work item owning launch-wide tile t (items sorted by tile_begin).

@@ -48,12 +48,15 @@ __device__ __forceinline__ void fp32_flush_object(const ObjDesc &od, const Batch
         red_add_f(bd.loss, loss_acc);
     loss_acc = 0.f;
     if (bd.mode != kRender) {
+        // nW is a multiple of 4 and the MLP block is 16-byte aligned (the hash levels are
+        // padded to 8 two-feature entries): 16-byte reductions, a quarter of the requests
         const int nW = IN * W + (od.H - 1) * W * W + 4 * W;
-        float *gw = od.grad + od.mlp_off;
-        for (int i = threadIdx.x; i < nW; i += kThreads) {
-            const float v = dWs[i];
-            if (v != 0.f)
-                red_add_f(gw + i, v);
+        float4 *gw = reinterpret_cast<float4 *>(od.grad + od.mlp_off);
+        const float4 *src = reinterpret_cast<const float4 *>(dWs);
+        for (int i = threadIdx.x; i < nW / 4; i += kThreads) {
+            const float4 v = src[i];
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+                red_add_f4(gw + i, v.x, v.y, v.z, v.w);
         }
     }
     __syncthreads();

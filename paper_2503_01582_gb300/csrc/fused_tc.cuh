@@ -248,12 +248,14 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
         constexpr int SL = kThreads / (W / 2);
         const int pair = tid / SL;
         const int o = pair / (W / 8), i0 = (pair % (W / 8)) * 8;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (tid % SL == 0 && dwo_acc[j] != 0.f)
-                red_add_f(gw + IN * W + (H - 1) * W * W + o * W + i0 + j, dwo_acc[j]);
-            dwo_acc[j] = 0.f;
+        if (tid % SL == 0) {  // 16-byte reductions: the 304-way contention per address is per request
+            float4 *p = reinterpret_cast<float4 *>(gw + IN * W + (H - 1) * W * W + o * W + i0);
+            red_add_f4(p, dwo_acc[0], dwo_acc[1], dwo_acc[2], dwo_acc[3]);
+            red_add_f4(p + 1, dwo_acc[4], dwo_acc[5], dwo_acc[6], dwo_acc[7]);
         }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            dwo_acc[j] = 0.f;
     }
     if (!have_dw)
         return;
@@ -265,11 +267,11 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
             float v[8];
             tmem_ld8(lane_base + dw_col<W, IN>(l) + c0, v);
             const int row = 16 * quad + lane;
-            if (lane < 16 && row < W)
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (c0 + j < nin && v[j] != 0.f)
-                        red_add_f(dst + row * nin + c0 + j, v[j] * inv_scale);
+            if (lane < 16 && row < W && c0 < nin) {  // nin and c0 are multiples of 8: two aligned quads
+                float4 *p = reinterpret_cast<float4 *>(dst + row * nin + c0);
+                red_add_f4(p, v[0] * inv_scale, v[1] * inv_scale, v[2] * inv_scale, v[3] * inv_scale);
+                red_add_f4(p + 1, v[4] * inv_scale, v[5] * inv_scale, v[6] * inv_scale, v[7] * inv_scale);
+            }
         }
     }
 }
@@ -377,30 +379,15 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int nrt = min(NR, bd.n_rays - ray0);
         const int ns = nrt * nr;
         // ---- ray data and sampling (FP32, shared with the FP32 kernel)
-        load_ray_tile(bd, ray0, nrt, rayf);
-        __syncthreads();
         const bool split = bd.sp_x != nullptr;  // sampling, encoding and scatter run in kernels of their own
         if (split) {
-            for (int r = warp; r < nrt; r += kThreads / 32) {
-                float *rf = rayf + r * kRayStride;
-                if (lane == 0) {
-                    const float o[3] = {rf[RF_O], rf[RF_O + 1], rf[RF_O + 2]};
-                    const float d[3] = {rf[RF_D], rf[RF_D + 1], rf[RF_D + 2]};
-                    float tn, tf;
-                    ray_box(o, d, tn, tf);
-                    rf[RF_TN] = tn;
-                    rf[RF_TF] = tf;
-                }
-                for (int k = lane; k < nr; k += 32)
-                    ts[r * nr + k] = bd.sp_t[(size_t)(ray0 + r) * nr + k];
-            }
-        } else {
-            for (int r = warp; r < nrt; r += kThreads / 32)
-                sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
-        }
-        __syncthreads();
-        // ---- encoding -> XA (16-bit, interleaved [128][INP])
-        if (split) {  // the tile's image from the sampling-encoding kernel; rows past the samples zeroed
+            // the tile's ray data, sample depths and encoding image from the sampling-encoding
+            // kernel, in one pass (rows of the image past the samples zeroed)
+            const float *rsrc = bd.sp_rays + (size_t)tile * kSplitRayFloats;
+            for (int i = tid; i < nrt * kRayStride; i += kThreads)
+                rayf[i] = rsrc[i];
+            for (int i = tid; i < ns; i += kThreads)
+                ts[i] = bd.sp_t[(size_t)ray0 * nr + i];
             const uint4 *src = bd.sp_x + (size_t)tile * (kSplitXBytes / 16);
             for (int i = tid; i < kTcTile * INP * 2 / 16; i += kThreads) {
                 const int row = ((i >> 3) / (INP >> 3)) * 8 + (i & 7);
@@ -411,6 +398,12 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int c = 0; c < 4; ++c)
                     dOT[c * SP + tid] = 0.f;
         } else {
+            load_ray_tile(bd, ray0, nrt, rayf);
+            __syncthreads();
+            for (int r = warp; r < nrt; r += kThreads / 32)
+                sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
+            __syncthreads();
+            // ---- encoding -> XA (16-bit, interleaved [128][INP])
             const int s = tid % kTcTile, part = tid / kTcTile;
             if (s >= ns) {
                 for (int l = part; l < INP / 2; l += 2)

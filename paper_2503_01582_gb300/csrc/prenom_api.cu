@@ -313,6 +313,7 @@ size_t assign_split(BatchDesc &bd, unsigned char *base)
     bd.sp_t = reinterpret_cast<float *>(base);
     bd.sp_x = reinterpret_cast<uint4 *>(base + t_bytes);
     bd.sp_dx = reinterpret_cast<float2 *>(base + t_bytes + (size_t)bd.n_tiles * kSplitXBytes);
+    bd.sp_rays = reinterpret_cast<float *>(base + t_bytes + (size_t)bd.n_tiles * (kSplitXBytes + kSplitDx * 8));
     return split_bytes(bd.n_rays, bd.nr, bd.n_tiles);
 }
 

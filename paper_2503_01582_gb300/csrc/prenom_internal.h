@@ -59,6 +59,7 @@ struct BatchDesc {
     // split execution of a mixed-precision training step (all NULL otherwise):
     // the three kernels hand over these per-batch buffers
     float *sp_t;    // [n_rays][nr] sample depths
+    float *sp_rays; // [n_tiles][kTcRayMax][16] each ray's data as the tensor-core kernel keeps it
     uint4 *sp_x;    // [n_tiles][kSplitXBytes / 16] 16-bit encoding of each tile, in the MMA operand layout
     float2 *sp_dx;  // [n_tiles][kMaxLevels][kSplitTile] dL/d(encoding), FP32, level-major
 };
@@ -66,6 +67,8 @@ struct BatchDesc {
 constexpr int kSplitTile = 128;                      // samples per tile of the mixed-precision kernels
 constexpr int kSplitXBytes = kSplitTile * 32 * 2;    // encoding image of a tile (width <= 32, 16-bit)
 constexpr int kSplitDx = kMaxLevels * kSplitTile;    // float2 per tile of dL/d(encoding)
+constexpr int kTcRayMax = kSplitTile / kMinNr;       // rays per tile at most
+constexpr int kSplitRayFloats = kTcRayMax * 16;      // floats per tile of ray data
 
 // Dynamic loss-scaling state of one mixed-precision object (device memory).
 struct LossScaleState {
@@ -93,7 +96,7 @@ cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int gri
 inline size_t split_bytes(int n_rays, int nr, int n_tiles)
 {
     const size_t t = ((size_t)n_rays * nr * sizeof(float) + 255) / 256 * 256;
-    return t + (size_t)n_tiles * (kSplitXBytes + kSplitDx * 8);
+    return t + (size_t)n_tiles * (kSplitXBytes + kSplitDx * 8 + kSplitRayFloats * 4);
 }
 // Loss-scale bookkeeping after the Adam step of a mixed-precision object.
 cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st);

@@ -6,10 +6,11 @@
 // as kernels of their own at several times the occupancy and hands the tile
 // data over through L2-sized buffers:
 //   1. sample_encode_kernel: one warp per ray: prior sampling (a1-a5) and the
-//      hash encoding (a6) of its samples; writes the sample depths [ray][nr]
-//      and each tile's 16-bit encoding as the exact image of the tensor-core
-//      kernel's A operand (no-swizzle interleaved core matrices);
-//   2. fused_tc_kernel in split mode: copies the image in, runs the MLP,
+//      hash encoding (a6) of its samples; writes each ray's data as the
+//      tensor-core kernel keeps it, the sample depths [ray][nr] and each
+//      tile's 16-bit encoding as the exact image of the tensor-core kernel's
+//      A operand (no-swizzle interleaved core matrices);
+//   2. fused_tc_kernel in split mode: copies all three in, runs the MLP,
 //      compositing, loss and MLP backward (a7-a10) and writes dL/d(encoding)
 //      per tile, FP32, level-major, instead of scattering it;
 //   3. hash_scatter_kernel: the hash-grid scatter (a10) of those gradients.
@@ -48,12 +49,12 @@ __global__ void __launch_bounds__(kThreads, 4)
         const int gr = tile * NR + rr;
         if (gr >= bd.n_rays)  // ray slot past the batch's last ray (the tile's rows stay unread)
             continue;
-        if (lane < 3) {
-            rf[RF_O + lane] = bd.o[(size_t)gr * 3 + lane];
-            rf[RF_D + lane] = bd.d[(size_t)gr * 3 + lane];
-        }
+        if (lane < 4)
+            load_ray_fields(bd, gr, rf, lane);
         __syncwarp();
-        sample_ray_warp(od, bd, 0, gr, rf, ts, cdf, lane);
+        sample_ray_warp(od, bd, 0, gr, rf, ts, cdf, lane);  // also sets rf[RF_TN], rf[RF_TF]
+        if (lane < kRayStride)  // the ray's data for the tensor-core kernel
+            bd.sp_rays[((size_t)tile * kTcRayMax + rr) * kRayStride + lane] = rf[lane];
         const int nr = bd.nr, NL = od.IN / 2, INP = od.IN < 16 ? 16 : od.IN;
         const float2 *tab = reinterpret_cast<const float2 *>(od.theta);
         unsigned char *img = reinterpret_cast<unsigned char *>(bd.sp_x) + (size_t)tile * kSplitXBytes;

@@ -130,8 +130,8 @@ def test_mixed_training_tracks_fp32(pkg, precision):
 def test_equal_error_after_training(pkg):
     """The metric compares forms at equal error: after the same training
     budget, the mixed-precision forms' held-out colour MSE (all pixels; the
-    target of a background pixel is black) and depth L1 (object pixels) are
-    within max(5 %, 2 x the FP32 seed-to-seed std) of the FP32 form's."""
+    target of a background pixel is black) and depth L1 (object pixels) exceed
+    the FP32 form's by at most max(5 %, 2 x the FP32 seed-to-seed std)."""
     import torch
     from helpers import pool_cfg1
     from synth import cameras_on_sphere, init_params, make_ray_pool, sample_batch
@@ -170,7 +170,8 @@ def test_equal_error_after_training(pkg):
         m = np.array(metrics[precision]).mean(0)
         print(f"\nprecision={precision}: colour MSE {m[0]:.5f} depth L1 {m[1]:.5f}; FP32 {ref.mean(0)[0]:.5f} "
               f"{ref.mean(0)[1]:.5f} (tolerance {tol[0]:.5f}, {tol[1]:.5f})")
-        assert np.all(np.abs(m - ref.mean(0)) <= tol)
+        # equal error means no loss of accuracy: a 16-bit form may come out ahead of FP32
+        assert np.all(m - ref.mean(0) <= tol)
 
 
 def test_mixed_full_size_sampled(pkg):
