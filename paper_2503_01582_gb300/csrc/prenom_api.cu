@@ -327,7 +327,7 @@ int grid_sample_encode(const prenom_ctx *c, int total_tiles, int rays_per_tile)
 
 int grid_scatter(const prenom_ctx *c, int total_tiles)
 {
-    return std::max(1, std::min(total_tiles, c->n_sm * 4));
+    return std::max(1, std::min(total_tiles, c->n_sm * 5));  // five 256-thread CTAs per SM (48 registers)
 }
 
 int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &bd, int kernel_id, bool split = false)

@@ -8,7 +8,7 @@ namespace prenom {
 // contiguous tile ranges; a tile's sample positions are staged in shared
 // memory once and each warp scatters one (level, 32 consecutive samples) at a
 // time, so a warp's lanes hold neighbouring samples of one level.
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 5)
     hash_scatter_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
     __shared__ __align__(16) WorkItem cur;
