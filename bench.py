@@ -328,6 +328,58 @@ def _batched_workload(pkg, ctx, stream, precision, seed, theta_from=None, only=N
     return objs, dev_sets, n_samples
 
 
+STRESS_OBJECTS, STRESS_RAYS, STRESS_NR = 64, 1 << 20, 64
+
+
+def _stress_compare(pkg, ctx, stream, steps=200, warmup=20):
+    """Real-time mapping stress: 64 objects of the category table in BF16 (MLP
+    on the tensor cores; the hash features stay FP32, which is their master
+    copy), 2^20 rays per step in total split by a projected-area share
+    2^(5a), a ~ U[0,1), 64 samples per ray from each object's 64^3 prior,
+    rays from 480x640 views, the internal Philox uniforms and background
+    colours; the whole step (all objects, backward, Adam) is one batched call,
+    and each step's latency is timed with its own CUDA events."""
+    import torch
+    from synth import cameras_on_sphere, make_ray_pool, prior_grid, sample_batch, scene_random_csg
+
+    rng = np.random.default_rng(17)
+    w = 2.0 ** (5 * rng.random(STRESS_OBJECTS))
+    rays = [max(32, 32 * int(round(STRESS_RAYS * x / w.sum() / 32))) for x in w]
+    objs, sets = [], [[], []]
+    for i in range(STRESS_OBJECTS):
+        log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
+        arch = pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
+                             lambda_sigma=1e-3, precision=PRECISION["bf16"])
+        sc = scene_random_csg(5000 + i)
+        obj = ctx.create_object(arch)
+        ctx.set_prior_grid(obj, prior_grid(sc, GRID_RES, i))
+        pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 50, 480, 640, 100 + i), 2 * rays[i], 100 + i,
+                             depth_noise=0.004)
+        for j in range(2):
+            sets[j].append(_device_batches([sample_batch(pool, rays[i], 50 * i + j)], obj, stream)[0])
+        objs.append(obj)
+    n_smp = sum(rays) * STRESS_NR
+    opts = pkg.make_opts(nc=STRESS_NR, nr=STRESS_NR, lr=1e-2)
+    loss = torch.zeros(STRESS_OBJECTS, device="cuda")
+    for i in range(warmup):
+        ctx.train_step(sets[i % 2], opts, loss)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        ev[i][0].record(stream)
+        ctx.train_step(sets[i % 2], opts, loss)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = np.array([a.elapsed_time(b) for a, b in ev])
+    for o in objs:
+        ctx.destroy_object(o)
+    return {"workload": "64 objects of the category table, BF16 MLP, %d rays x 64 samples per step "
+                        "(%d samples), 64^3 priors, one batched step" % (sum(rays), n_smp),
+            "value": n_smp / (float(np.mean(ms)) / 1e3), "unit": "samples/s",
+            "latency_ms_p50": float(np.percentile(ms, 50)), "latency_ms_p99": float(np.percentile(ms, 99)),
+            "steps": steps, "warmup": warmup}
+
+
 META_TASKS, META_INNER, META_RAYS, META_NR = 16, 16, 2048, 48
 
 
@@ -540,6 +592,7 @@ def run_ours(args):
     if world == 1 and not args.no_compare:
         compare["reptile_meta_step"] = _meta_compare(pkg, ctx, stream, prec)
         compare["sampling_ablation"] = _ablation_compare(pkg, ctx, stream, prec)
+        compare["mapping_stress_64_objects"] = _stress_compare(pkg, ctx, stream)
 
     if world > 1 and not args.no_compare:
         # the 32-object workload split over the ranks (longest processing time

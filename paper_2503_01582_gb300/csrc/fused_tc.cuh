@@ -159,6 +159,47 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8])
         v[i] = __uint_as_float(r[i]);
 }
 
+// N (8, 16 or 32) consecutive FP32 columns of this thread's TMEM lane: every
+// 8-column load is issued before the one wait, whose register operands tie
+// the loaded values to it so that no use moves above it.
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[N])
+{
+    static_assert(N == 8 || N == 16 || N == 32, "columns");
+    uint32_t r[N];
+#pragma unroll
+    for (int q = 0; q < N / 8; ++q)
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[8 * q]), "=r"(r[8 * q + 1]), "=r"(r[8 * q + 2]), "=r"(r[8 * q + 3]),
+                       "=r"(r[8 * q + 4]), "=r"(r[8 * q + 5]), "=r"(r[8 * q + 6]), "=r"(r[8 * q + 7])
+                     : "r"(taddr + 8 * q));
+    if constexpr (N == 8) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                     :
+                     : "memory");
+    } else if constexpr (N == 16) {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                       "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                       "+r"(r[15])
+                     :
+                     : "memory");
+    } else {
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                       "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                       "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                       "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                       "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                     :
+                     : "memory");
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4])
 {
     uint32_t r[4];
@@ -455,17 +496,19 @@ __global__ void __launch_bounds__(kThreads, 2)
             ok = mbar_wait(mbar, parity, bd.status);
             parity ^= 1u;
             // epilogue: relu -> 16-bit -> HA[l]; warp half h takes columns [h W/2, (h+1) W/2)
+            {
+                float v[W / 2];
+                tmem_ld_cols<W / 2>(lane_base + half * (W / 2), v);
 #pragma unroll
-            for (int c0 = 0; c0 < W / 2; c0 += 8) {
-                const int col = half * (W / 2) + c0;
-                float v[8];
-                tmem_ld8(lane_base + col, v);
-                uint4 pk;
-                pk.x = (uint32_t)Hf::bits(fmaxf(v[0], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[1], 0.f)) << 16);
-                pk.y = (uint32_t)Hf::bits(fmaxf(v[2], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[3], 0.f)) << 16);
-                pk.z = (uint32_t)Hf::bits(fmaxf(v[4], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[5], 0.f)) << 16);
-                pk.w = (uint32_t)Hf::bits(fmaxf(v[6], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[7], 0.f)) << 16);
-                *reinterpret_cast<uint4 *>(HA + l * L::ha + il_off(srow, col, W)) = pk;
+                for (int c0 = 0; c0 < W / 2; c0 += 8) {
+                    const int col = half * (W / 2) + c0;
+                    uint4 pk;
+                    pk.x = (uint32_t)Hf::bits(fmaxf(v[c0], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 1], 0.f)) << 16);
+                    pk.y = (uint32_t)Hf::bits(fmaxf(v[c0 + 2], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 3], 0.f)) << 16);
+                    pk.z = (uint32_t)Hf::bits(fmaxf(v[c0 + 4], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 5], 0.f)) << 16);
+                    pk.w = (uint32_t)Hf::bits(fmaxf(v[c0 + 6], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 7], 0.f)) << 16);
+                    *reinterpret_cast<uint4 *>(HA + l * L::ha + il_off(srow, col, W)) = pk;
+                }
             }
             tc_sync();
         }
@@ -547,11 +590,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             parity ^= 1u;
             // epilogue: mask by H_l > 0 -> 16-bit -> DA (columns [0, W))
             const unsigned char *hl = HA + l * L::ha;
+            float vb[W / 2];
+            tmem_ld_cols<W / 2>(lane_base + half * (W / 2), vb);
 #pragma unroll
             for (int c0 = 0; c0 < W / 2; c0 += 8) {
                 const int col = half * (W / 2) + c0;
-                float v[8];
-                tmem_ld8(lane_base + col, v);
+                const float *v = vb + c0;
                 const uint4 hv = *reinterpret_cast<const uint4 *>(hl + il_off(srow, col, W));
                 const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
                 uint32_t pk[4];
