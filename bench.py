@@ -530,26 +530,38 @@ def run_ours(args):
         ms = t.item()
     value = samples_per_step * args.steps * world / (ms / 1e3)
 
-    # ---- end to end through the public API with host buffers (pinned H2D, loss D2H every step)
+    # ---- end to end through the public API with host buffers: every step copies its
+    # batch from pinned host memory (on a copy stream, double-buffered, so the copy
+    # of step i+1 overlaps step i) and reads its loss back into pinned memory
     pinned = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in b.items()} for b in batches_np]
     h2d = sum(t.numel() * t.element_size() for t in pinned[0].values())
-    loss_host = torch.zeros(1).pin_memory()
-    staging = [{k: torch.empty_like(v, device="cuda") for k, v in p.items()} for p in pinned[:2]]
     e2e_steps = max(args.steps // 2, 5)
+    loss_host = torch.zeros(e2e_steps).pin_memory()
+    staging = [{k: torch.empty_like(v, device="cuda") for k, v in p.items()} for p in pinned[:2]]
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        src, dst = pinned[i % len(pinned)], staging[i % 2]
-        with torch.cuda.stream(stream):
+        slot = i % 2
+        src, dst = pinned[i % len(pinned)], staging[slot]
+        if i >= 2:
+            copy_stream.wait_event(consumed[slot])  # the step that read this buffer is done
+        with torch.cuda.stream(copy_stream):
             for k in src:
                 dst[k].copy_(src[k], non_blocking=True)
+            copied[slot].record(copy_stream)
+        stream.wait_event(copied[slot])
         ctx.train_step([dict(dst, obj=obj)], opts, loss)
         with torch.cuda.stream(stream):
-            loss_host.copy_(loss, non_blocking=True)
-        stream.synchronize()
-        _ = float(loss_host.item())
+            loss_host[i].copy_(loss[0], non_blocking=True)
+            consumed[slot].record(stream)
+    stream.synchronize()
+    e2e_losses = loss_host.numpy().copy()
     e2e_s = time.perf_counter() - t0
+    assert np.all(np.isfinite(e2e_losses))
     if world > 1:
         t = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
