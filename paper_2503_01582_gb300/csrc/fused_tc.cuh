@@ -108,8 +108,10 @@ __device__ __forceinline__ void mma_commit(uint64_t *mbar)
         smem_addr(mbar)));
 }
 
-// Bounded wait for the mbarrier phase; false (and status set) when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int32_t *status)
+// Bounded poll of the mbarrier phase by this thread alone (no barrier): false
+// (and status set) when it gave up.  Every caller combines the answers of
+// all threads at its next tc_sync_and, so that no thread leaves a loop alone.
+__device__ __forceinline__ bool mbar_poll(uint64_t *mbar, uint32_t parity, int32_t *status)
 {
     uint32_t done = 0;
     for (int it = 0; it < (1 << 24) && !done; ++it) {
@@ -121,7 +123,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int32
     if (!done && status)
         atomicExch(status, 1);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return __syncthreads_and(done != 0) != 0;  // the same answer in every thread of the block
+    return done != 0;
+}
+
+// tc_sync that also returns, to every thread, whether all threads passed `ok`.
+__device__ __forceinline__ bool tc_sync_and(bool ok)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const bool all = __syncthreads_and(ok) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return all;
 }
 
 __device__ __forceinline__ void tc_sync()
@@ -493,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 mma_gemm(tmem, a, b, l == 0 ? INP : W, id_fwd, false);
                 mma_commit(mbar);
             }
-            ok = mbar_wait(mbar, parity, bd.status);
+            const bool done = mbar_poll(mbar, parity, bd.status);
             parity ^= 1u;
             // epilogue: relu -> 16-bit -> HA[l]; warp half h takes columns [h W/2, (h+1) W/2)
             {
@@ -510,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     *reinterpret_cast<uint4 *>(HA + l * L::ha + il_off(srow, col, W)) = pk;
                 }
             }
-            tc_sync();
+            ok = tc_sync_and(done);
         }
         if (!ok)
             break;
@@ -518,16 +530,20 @@ __global__ void __launch_bounds__(kThreads, 2)
             mma_gemm(tmem, kmajor(HA + (H - 1) * L::ha, W), kmajor(WtO, W), W, id_out, false);
             mma_commit(mbar);
         }
-        ok = mbar_wait(mbar, parity, bd.status);
-        parity ^= 1u;
-        if (half == 0) {
-            float v[4];
-            tmem_ld4(lane_base, v);
+        {
+            const bool done = mbar_poll(mbar, parity, bd.status);
+            parity ^= 1u;
+            if (half == 0) {
+                float v[4];
+                tmem_ld4(lane_base, v);
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                OT[c * SP + srow] = v[c];
+                for (int c = 0; c < 4; ++c)
+                    OT[c * SP + srow] = v[c];
+            }
+            ok = tc_sync_and(done);
         }
-        tc_sync();
+        if (!ok)
+            break;
         // ---- compositing, loss and its adjoint (FP32)
         for (int r = warp; r < nrt; r += kThreads / 32) {
             const float lr = composite_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane);
@@ -586,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     mma_gemm(tmem, kmajor(DA, kDaCols), mnmajor(WtH + l * L::wh, W), W, id_dh, false);
                 mma_commit(mbar);
             }
-            ok = mbar_wait(mbar, parity, bd.status);
+            const bool done = mbar_poll(mbar, parity, bd.status);
             parity ^= 1u;
             // epilogue: mask by H_l > 0 -> 16-bit -> DA (columns [0, W))
             const unsigned char *hl = HA + l * L::ha;
@@ -612,9 +628,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                     atomicExch(bd.overflow, 1);
                 *reinterpret_cast<uint4 *>(DA + il_off(srow, col, kDaCols)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
-            tc_sync();
+            ok = tc_sync_and(done);
             // dW_l += dH_l^T A_l (M = 64 rows of DA, N = width of A_l, K = 128 samples)
-            if (tid == 0) {
+            if (tid == 0 && ok) {
                 if (l > 0)
                     mma_gemm(tmem + dw_col<W, IN>(l), mnmajor(DA, kDaCols), mnmajor(HA + (l - 1) * L::ha, W),
                              kTcTile, id_dw, !first_dw);
@@ -630,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             mma_gemm(tmem, kmajor(DA, kDaCols), mnmajor(Wt0, INP), W, id_dx, false);
             mma_commit(mbar);
         }
-        ok = mbar_wait(mbar, parity, bd.status);
+        const bool done_dx = mbar_poll(mbar, parity, bd.status);
         parity ^= 1u;
         first_dw = false;
         {
@@ -645,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int j = 0; j < 8; ++j)
                     g[j] = g8[j];
             }
-            const bool active = s < ns;  // the whole warp scatters together
+            const bool active = s < ns && done_dx;  // the whole warp scatters together
             if (split) {  // dL/d(encoding) to the scatter kernel, unscaled FP32, level-major
                 if (active) {
                     float2 *dst = bd.sp_dx + (size_t)tile * kSplitDx;
@@ -655,7 +671,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                         if (l0 + j < NL)
                             dst[(l0 + j) * kTcTile + s] = make_float2(g[2 * j] * inv_scale, g[2 * j + 1] * inv_scale);
                 }
-                tc_sync();
+                ok = tc_sync_and(done_dx);
                 continue;
             }
             float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
@@ -680,7 +696,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                                    lane);
             }
         }
-        tc_sync();
+        ok = tc_sync_and(done_dx);
     }
 
     if (k >= 0 && ok)
