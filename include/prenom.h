@@ -201,12 +201,14 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * form: sampling + encoding, the tensor-core MLP and the hash scatter as three
  * launches over the same list); one Adam launch then updates every object.
  * A single batch takes the same path.  The first calls of a new group
- * signature (one untimed call, then two rounds over the candidates) try the
+ * signature (kernel variant, and batch and tile counts rounded down to powers
+ * of two; one untimed call, then two rounds over the candidates) try the
  * split form and several work-chunk sizes (tiles per CTA) and keep the
- * fastest; afterwards,
- * on a non-default stream and with timing off, the whole step is captured
- * once per signature as a CUDA graph and replayed (PRENOM_FLAG_NO_GRAPH
- * disables the graph).  A step synchronises with the step before the previous
+ * fastest; afterwards, on a non-default stream and with timing off, the whole
+ * step is captured once per exact signature as a CUDA graph and replayed
+ * (PRENOM_FLAG_NO_GRAPH disables the graph); a context keeps at most 64
+ * graphs, evicting the least recently used after waiting for its stream.
+ * A step synchronises with the step before the previous
  * one (two staging buffers are in flight), allocates its work-list and split
  * buffers on first use and when they must grow, and updates at most 128
  * objects.  With PRENOM_FLAG_CHECK_FINITE the batches run one launch each,

@@ -68,7 +68,12 @@ struct prenom_ctx {
     size_t h_stage_cap = 0;
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     int stage_idx = 0;
-    std::map<std::string, cudaGraphExec_t> graphs;
+    struct CachedGraph {
+        cudaGraphExec_t exec;
+        uint64_t last_use;
+    };
+    std::map<std::string, CachedGraph> graphs;  // at most kMaxGraphs, least recently used evicted
+    uint64_t graph_tick = 0;
     std::map<std::string, std::vector<float>> tune_ms;  // measured ms per candidate
     std::map<std::string, int> tune_best;               // chosen candidate index
     std::set<std::string> tune_warm;                    // signatures past their untimed first call
@@ -475,6 +480,7 @@ constexpr int kTuneTpc[] = {0, 16, 8, 4};
 constexpr int kTuneTpcTc[] = {0, 0, 16, 8};
 constexpr int kTuneN = 4;
 constexpr int kTuneRounds = 2;  // each candidate is timed this many times (one whole step each)
+constexpr size_t kMaxGraphs = 64;  // captured step graphs kept per context
 
 bool cand_split(const Group &g, int cand, bool split_allowed)
 {
@@ -497,6 +503,17 @@ std::string group_key(const Group &g)
 {
     char buf[128];
     snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", g.precision, g.W, g.IN, g.S, g.hmax, g.count, g.total_tiles);
+    return buf;
+}
+
+// The autotuner's signature of a group: the kernel variant and the sizes in
+// powers of two, so that steps whose ray counts vary a little share one tuning.
+std::string tune_key(const Group &g)
+{
+    auto lg = [](int x) { int b = 0; while (x > 1) { x >>= 1; ++b; } return b; };
+    char buf[128];
+    snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/n%d/t%d", g.precision, g.W, g.IN, g.S, g.hmax, lg(g.count),
+             lg(g.total_tiles));
     return buf;
 }
 
@@ -658,7 +675,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
     const bool split_forced = split_allowed && (op.flags & PRENOM_FLAG_SPLIT);
     std::vector<std::string> gkeys;
     for (Group &g : p.groups) {
-        gkeys.push_back(group_key(g) + (split_allowed ? "/s" : "/f"));
+        gkeys.push_back(tune_key(g) + (split_allowed ? "/s" : "/f"));
         auto it = c->tune_best.find(gkeys.back());
         int cand;
         if (split_forced && g.precision != PRENOM_PRECISION_FP32) {
@@ -711,7 +728,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
             c->d_work_cap = e == cudaSuccess ? cap : 0;
         }
         for (auto &kv : c->graphs)  // captured graphs point at the old buffers
-            cudaGraphExecDestroy(kv.second);
+            cudaGraphExecDestroy(kv.second.exec);
         c->graphs.clear();
     }
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)
@@ -783,9 +800,19 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
                 cudaGraphDestroy(graph);
             if (e != cudaSuccess)
                 return cuda_fail(c, e, "batched step graph capture");
-            it = c->graphs.emplace(key, exec).first;
+            if (c->graphs.size() >= kMaxGraphs) {  // evict the least recently used signature
+                auto old = c->graphs.begin();
+                for (auto g = c->graphs.begin(); g != c->graphs.end(); ++g)
+                    if (g->second.last_use < old->second.last_use)
+                        old = g;
+                cudaStreamSynchronize(c->stream);  // it may still be running
+                cudaGraphExecDestroy(old->second.exec);
+                c->graphs.erase(old);
+            }
+            it = c->graphs.emplace(key, prenom_ctx::CachedGraph{exec, 0}).first;
         }
-        e = cudaGraphLaunch(it->second, c->stream);
+        it->second.last_use = ++c->graph_tick;
+        e = cudaGraphLaunch(it->second.exec, c->stream);
     } else {
         const int64_t before = c->launches;  // timed launches count themselves; the total is set below
         e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing);
@@ -890,7 +917,7 @@ void prenom_destroy(prenom_ctx *c)
     }
     cudaFree(c->status);
     for (auto &kv : c->graphs)
-        cudaGraphExecDestroy(kv.second);
+        cudaGraphExecDestroy(kv.second.exec);
     for (int i = 0; i < 2; ++i) {
         cudaFreeHost(c->h_stage[i]);
         if (c->stage_ev[i])

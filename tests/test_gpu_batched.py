@@ -212,3 +212,32 @@ def test_stress_scale_batch_of_64_bf16_objects(pkg):
             c_min, l2_max = (0.995, 0.15) if W == 16 else (0.9995, 5e-2)
             assert cos >= c_min and l2 <= l2_max, (k, W, cos, l2)
     ctx.close()
+
+
+def test_varying_ray_counts_bound_the_graph_cache(pkg):
+    """70 steps with 70 different ray counts (70 step signatures, more than the
+    64 graphs a context keeps) on a side stream: every step's loss follows the
+    same object stepped without graphs or tuning (PRENOM_FLAG_CHECK_FINITE)."""
+    import torch
+
+    arch = dict(CFG1, log2T=14)
+    a, theta, grid, rays, u, cr = case(arch, 400, 32, 32, seed=77, hash_range=0.5)
+    o = dict(arch=arch, prec=0, a=a, theta=theta, grid=grid, rays=rays, cr=cr, t_in=oracle_t(grid, rays, u, 32, 32))
+    stream = torch.cuda.Stream()
+    ctx_g, (id_g,) = _make(pkg, [o], stream=stream)
+    ctx_s, (id_s,) = _make(pkg, [o])
+    opts = pkg.make_opts(nc=32, nr=32, lr=1e-2)
+    opts_s = pkg.make_opts(nc=32, nr=32, lr=1e-2, flags=pkg.PRENOM_FLAG_CHECK_FINITE)
+    full = _batch(o, id_g)
+    full_s = _batch(o, id_s)
+    lg, ls = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    for step in range(70):
+        n = 4 * (20 + step) - 1  # 4 rays per tile: 70 distinct tile counts, 70 step signatures
+        with torch.cuda.stream(stream):
+            ctx_g.train_step([{k: (v[:n] if torch.is_tensor(v) else v) for k, v in full.items()}], opts, lg)
+        stream.synchronize()
+        ctx_s.train_step([{k: (v[:n] if torch.is_tensor(v) else v) for k, v in full_s.items()}], opts_s, ls)
+        assert abs(lg.item() - ls.item()) <= 1e-3 * abs(ls.item()), (step, lg.item(), ls.item())
+    ctx_g.sync()
+    ctx_g.close()
+    ctx_s.close()
