@@ -405,6 +405,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
     const int t0 = (int)blockIdx.x * per, t1 = min(total, t0 + per);
     int k = -1;
+    // split mode: the next tile's copy-in, loaded into registers during this
+    // tile's backward pass (image chunks, ray data, depths of two passes each)
+    constexpr int kChunks = kTcTile * INP * 2 / 16;
+    static_assert(kChunks <= 2 * kThreads && kTcRayMax * kRayStride <= 2 * kThreads && kTcTile <= kThreads,
+                  "two registers per thread carry a tile");
+    uint4 px0 = make_uint4(0u, 0u, 0u, 0u), px1 = px0;
+    float pr0 = 0.f, pr1 = 0.f, pt0 = 0.f;
+    int pre_t = -1;
     for (int t = t0; t < t1 && ok; ++t) {
         int nk = k < 0 ? item_of_tile(list, n_items, t) : k;
         while (nk + 1 < n_items && list[nk + 1].tile_begin <= t)
@@ -433,7 +441,22 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int ns = nrt * nr;
         // ---- ray data and sampling (FP32, shared with the FP32 kernel)
         const bool split = bd.sp_x != nullptr;  // sampling, encoding and scatter run in kernels of their own
-        if (split) {
+        if (split && pre_t == t) {  // prefetched during the previous tile
+            if (tid < kChunks)
+                reinterpret_cast<uint4 *>(XA)[tid] = px0;
+            if (tid + kThreads < kChunks)
+                reinterpret_cast<uint4 *>(XA)[tid + kThreads] = px1;
+            if (tid < nrt * kRayStride)
+                rayf[tid] = pr0;
+            if (tid + kThreads < nrt * kRayStride)
+                rayf[tid + kThreads] = pr1;
+            if (tid < ns)
+                ts[tid] = pt0;
+            if (tid < kTcTile && tid >= ns)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dOT[c * SP + tid] = 0.f;
+        } else if (split) {
             // the tile's ray data, sample depths and encoding image from the sampling-encoding
             // kernel, in one pass (rows of the image past the samples zeroed)
             const float *rsrc = bd.sp_rays + (size_t)tile * kSplitRayFloats;
@@ -553,6 +576,21 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
         if (!train)
             continue;
+        pre_t = -1;
+        if (split && t + 1 < t1 && tile + 1 < bd.n_tiles) {  // the next tile of this item: issue its loads now
+            const int tile2 = tile + 1, ray02 = tile2 * NR;
+            const int ns2 = min(NR, bd.n_rays - ray02) * nr, nr2 = min(NR, bd.n_rays - ray02) * kRayStride;
+            const uint4 *src = bd.sp_x + (size_t)tile2 * (kSplitXBytes / 16);
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+            const int i1 = tid + kThreads;
+            px0 = tid < kChunks && ((tid >> 3) / (INP >> 3)) * 8 + (tid & 7) < ns2 ? src[tid] : z;
+            px1 = i1 < kChunks && ((i1 >> 3) / (INP >> 3)) * 8 + (i1 & 7) < ns2 ? src[i1] : z;
+            const float *rsrc = bd.sp_rays + (size_t)tile2 * kSplitRayFloats;
+            pr0 = tid < nr2 ? rsrc[tid] : 0.f;
+            pr1 = i1 < nr2 ? rsrc[i1] : 0.f;
+            pt0 = tid < ns2 ? bd.sp_t[(size_t)ray02 * nr + tid] : 0.f;
+            pre_t = t + 1;
+        }
         // ---- scaled 16-bit dL/dO, and dW_out on the CUDA cores
         if (tid < kTcTile) {
             uint32_t lo = (uint32_t)Hf::bits(dOT[tid] * scale) | ((uint32_t)Hf::bits(dOT[SP + tid] * scale) << 16);
