@@ -69,10 +69,10 @@ extern "C" {
 #define PRENOM_FLAG_NO_ADAM 1u      /* accumulate gradients, skip Adam (step count unchanged) */
 #define PRENOM_FLAG_CHECK_FINITE 2u /* synchronise and fail with NONFINITE on a NaN/inf loss (per-object path) */
 #define PRENOM_FLAG_NO_GRAPH 4u     /* batched steps: launch directly instead of replaying a captured graph */
-#define PRENOM_FLAG_FUSED 8u        /* mixed-precision training: one fused kernel per step instead of the
-                                       split form (sampling+encoding, tensor-core MLP, hash scatter as
-                                       three kernels); the results agree to rounding order */
-#define PRENOM_FLAG_SPLIT 16u       /* mixed-precision training: always the split form (not tuned) */
+#define PRENOM_FLAG_FUSED 8u        /* training: one fused kernel per step and group instead of the split
+                                       form (sampling+encoding, the MLP kernel, hash scatter as three
+                                       kernels); the results agree to rounding order */
+#define PRENOM_FLAG_SPLIT 16u       /* training: always the split form (not tuned) */
 
 /* prenom_get_state / prenom_set_state: which buffer */
 #define PRENOM_STATE_THETA 0
@@ -197,9 +197,9 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * Several batches form the batched form (§IV-A trains objects in parallel):
  * the batches are grouped by kernel variant (precision, width, encoding
  * width) and each group runs as ONE persistent launch over a work list
- * spanning all its objects (a mixed-precision group may instead run the split
- * form: sampling + encoding, the tensor-core MLP and the hash scatter as three
- * launches over the same list); one Adam launch then updates every object.
+ * spanning all its objects (or, in the split form, sampling + encoding, the
+ * MLP kernel and the hash scatter as three launches over the same list); one
+ * Adam launch then updates every object.
  * A single batch takes the same path.  The first calls of a new group
  * signature (kernel variant, and batch and tile counts rounded down to powers
  * of two; one untimed call, then two rounds over the candidates) try the
@@ -355,9 +355,9 @@ PRENOM_API int prenom_canonical_yaw(prenom_ctx *ctx, int32_t obj, const float *p
 
 /* The autotuner's record as text (one line per group signature: the step
  * times in ms of each timed call, "cK" = candidate K, and the chosen candidate
- * after "->"; candidates of a mixed-precision group: c0 split form, c1..c3 the
- * fused kernel in one wave / 16 / 8 tiles per CTA; of an FP32 group: one wave
- * / 16 / 8 / 4 tiles per CTA).  buf: host, cap bytes, NUL-terminated,
+ * after "->"; candidates: c0 the split form, c1..c3 the fused kernel in one
+ * wave / 16 / 8 tiles per CTA; with PRENOM_FLAG_FUSED: one wave / 16 / 8 / 4
+ * tiles per CTA).  buf: host, cap bytes, NUL-terminated,
  * truncated to fit. */
 PRENOM_API int prenom_tuning_report(prenom_ctx *ctx, char *buf, size_t cap);
 

@@ -111,16 +111,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ray0 = tile * NR;
         const int nrt = min(NR, bd.n_rays - ray0);
         const int ns = nrt * nr;
-        // (1) ray data
-        load_ray_tile(bd, ray0, nrt, rayf);
-        __syncthreads();
-        // (2) sampling
-        for (int r = warp; r < nrt; r += kThreads / 32)
-            sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
-        __syncthreads();
-        // (3) encoding
-        encode_or_scatter<IN, S, false>(od, bd, rayf, ts, XT, dOT, ns);
-        __syncthreads();
+        const bool split = bd.sp_x != nullptr;  // sampling, encoding and scatter run in kernels of their own
+        if (split) {
+            // (1-3) the tile's ray data, sample depths and FP32 encoding from the
+            // sampling-encoding kernel (rows past the tile's samples zeroed)
+            const float *rsrc = bd.sp_rays + (size_t)tile * kSplitRayFloats;
+            for (int i = tid; i < nrt * kRayStride; i += kThreads)
+                rayf[i] = rsrc[i];
+            for (int i = tid; i < ns; i += kThreads)
+                ts[i] = bd.sp_t[(size_t)ray0 * nr + i];
+            const float *img = reinterpret_cast<const float *>(bd.sp_x) + (size_t)tile * (kSplitXBytes / 4);
+            for (int i = tid; i < IN * S; i += kThreads) {
+                const int c = i / S, s = i % S;
+                XT[c * SP + s] = s < ns ? img[c * kSplitTile + s] : 0.f;
+            }
+            if (tid < S && tid >= ns)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    dOT[c * SP + tid] = 0.f;
+            __syncthreads();
+        } else {
+            // (1) ray data
+            load_ray_tile(bd, ray0, nrt, rayf);
+            __syncthreads();
+            // (2) sampling
+            for (int r = warp; r < nrt; r += kThreads / 32)
+                sample_ray_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, cdfs + warp * (kMaxNc + 1), lane);
+            __syncthreads();
+            // (3) encoding
+            encode_or_scatter<IN, S, false>(od, bd, rayf, ts, XT, dOT, ns);
+            __syncthreads();
+        }
         // (4) MLP forward
         gemm_sn<S, W, kRelu>(XT, Wf, IN, HT);
         __syncthreads();
@@ -154,8 +175,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         gemm_sn<S, IN, kStore>(HT, Wb, W, XT);
         __syncthreads();
-        // (7) hash-grid scatter
-        encode_or_scatter<IN, S, true>(od, bd, rayf, ts, XT, dOT, ns);
+        // (7) hash-grid scatter, or dL/d(encoding) to the scatter kernel (level-major pairs)
+        if (split) {
+            float2 *dx = bd.sp_dx + (size_t)tile * kSplitDx;
+            for (int i = tid; i < (IN / 2) * S; i += kThreads) {
+                const int l = i / S, s = i % S;
+                if (s < ns)
+                    dx[l * kSplitTile + s] = make_float2(XT[(2 * l) * SP + s], XT[(2 * l + 1) * SP + s]);
+            }
+        } else {
+            encode_or_scatter<IN, S, true>(od, bd, rayf, ts, XT, dOT, ns);
+        }
         __syncthreads();
     }
     if (k >= 0)

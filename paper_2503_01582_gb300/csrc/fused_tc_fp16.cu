@@ -10,7 +10,7 @@ cudaError_t launch_fused_tc_fp16(const WorkItem &one, const WorkList &wl, int W,
 
 cudaError_t launch_sample_encode_fp16(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
-    return launch_sample_encode_t<false>(one, wl, grid, st);
+    return launch_sample_encode_t<0>(one, wl, grid, st);
 }
 
 }  // namespace prenom

@@ -391,6 +391,34 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
     bd.rays_per_tile = S / bd.nr;
     bd.n_tiles = (bd.n_rays + bd.rays_per_tile - 1) / bd.rays_per_tile;
     const int grid = std::min(bd.n_tiles, c->n_sm);
+    if (split && bd.mode == kTrain) {
+        int rc = ensure_split(c, split_bytes(bd.n_rays, bd.nr, bd.n_tiles));
+        if (rc)
+            return rc;
+        assign_split(bd, c->split_buf);
+        WorkItem one{};
+        one.od = od;
+        one.bd = bd;
+        const WorkList wl{nullptr, 1, bd.n_tiles, od.H};
+        cudaEvent_t ev;
+        timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
+        cudaError_t e = launch_sample_encode(one, wl, PRENOM_PRECISION_FP32,
+                                             grid_sample_encode(c, bd.n_tiles, bd.rays_per_tile), c->stream);
+        timed_end(c, PRENOM_KERNEL_SAMPLE_ENCODE, ev);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "sampling-encoding kernel launch");
+        timed_begin(c, kernel_id, &ev);
+        e = launch_fused_fp32(od, bd, S, grid, c->stream);
+        timed_end(c, kernel_id, ev);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "fused kernel launch");
+        timed_begin(c, PRENOM_KERNEL_SCATTER, &ev);
+        e = launch_hash_scatter(one, wl, grid_scatter(c, bd.n_tiles), c->stream);
+        timed_end(c, PRENOM_KERNEL_SCATTER, ev);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "hash scatter kernel launch");
+        return PRENOM_OK;
+    }
     cudaEvent_t ev;
     timed_begin(c, kernel_id, &ev);
     const cudaError_t e = launch_fused_fp32(od, bd, S, grid, c->stream);
@@ -473,18 +501,18 @@ struct Plan {
 };
 
 // Candidates of the autotuner: tiles per CTA of the training kernel (0 = one
-// persistent wave of resident CTAs).  A mixed-precision group tries the split
-// form first (its tensor-core kernel in one wave), then the fused kernel with
-// three work-chunk sizes.
+// persistent wave of resident CTAs).  A group tries the split form first (its
+// MLP kernel in one wave), then the fused kernel with three work-chunk sizes;
+// with the split form excluded, the fused kernel with four.
 constexpr int kTuneTpc[] = {0, 16, 8, 4};
 constexpr int kTuneTpcTc[] = {0, 0, 16, 8};
 constexpr int kTuneN = 4;
 constexpr int kTuneRounds = 2;  // each candidate is timed this many times (one whole step each)
 constexpr size_t kMaxGraphs = 64;  // captured step graphs kept per context
 
-bool cand_split(const Group &g, int cand, bool split_allowed)
+bool cand_split(const Group &, int cand, bool split_allowed)
 {
-    return g.precision != PRENOM_PRECISION_FP32 && split_allowed && cand == 0;
+    return split_allowed && cand == 0;
 }
 
 int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed)
@@ -493,7 +521,7 @@ int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed
     if (g.precision != PRENOM_PRECISION_FP32 && 2 * (fused_tc_smem(g.W, g.IN, g.hmax) + 1024) <= 228 * 1024)
         per_sm = 2;
     const int wave = c->n_sm * per_sm;
-    const int tpc = (g.precision != PRENOM_PRECISION_FP32 && split_allowed) ? kTuneTpcTc[cand] : kTuneTpc[cand];
+    const int tpc = split_allowed ? kTuneTpcTc[cand] : kTuneTpc[cand];
     if (tpc == 0)
         return std::max(1, std::min(g.total_tiles, wave));
     return std::max(1, std::min(g.total_tiles, std::max(wave, (g.total_tiles + tpc - 1) / tpc)));
@@ -678,7 +706,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         gkeys.push_back(tune_key(g) + (split_allowed ? "/s" : "/f"));
         auto it = c->tune_best.find(gkeys.back());
         int cand;
-        if (split_forced && g.precision != PRENOM_PRECISION_FP32) {
+        if (split_forced) {
             cand = 0;  // the split form, untuned
         } else if (it != c->tune_best.end()) {
             cand = it->second;
@@ -756,7 +784,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         cudaEventDestroy(t1);
         for (size_t gi = 0; gi < p.groups.size(); ++gi) {  // whole-step time, charged to each tuned group
             std::vector<float> &v = c->tune_ms[gkeys[gi]];
-            if (c->tune_best.count(gkeys[gi]) || (split_forced && p.groups[gi].precision != PRENOM_PRECISION_FP32))
+            if (c->tune_best.count(gkeys[gi]) || split_forced)
                 continue;
             if (!c->tune_warm.count(gkeys[gi])) {  // the first call loads modules and buffers: not timed
                 c->tune_warm.insert(gkeys[gi]);

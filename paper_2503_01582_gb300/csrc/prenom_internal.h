@@ -60,12 +60,13 @@ struct BatchDesc {
     // the three kernels hand over these per-batch buffers
     float *sp_t;    // [n_rays][nr] sample depths
     float *sp_rays; // [n_tiles][kTcRayMax][16] each ray's data as the tensor-core kernel keeps it
-    uint4 *sp_x;    // [n_tiles][kSplitXBytes / 16] 16-bit encoding of each tile, in the MMA operand layout
+    uint4 *sp_x;    // [n_tiles][kSplitXBytes / 16] each tile's encoding: 16-bit in the MMA operand
+                    // layout (tensor-core kernel) or FP32 feature-major [IN][kSplitTile] (FP32 kernel)
     float2 *sp_dx;  // [n_tiles][kMaxLevels][kSplitTile] dL/d(encoding), FP32, level-major
 };
 
 constexpr int kSplitTile = 128;                      // samples per tile of the mixed-precision kernels
-constexpr int kSplitXBytes = kSplitTile * 32 * 2;    // encoding image of a tile (width <= 32, 16-bit)
+constexpr int kSplitXBytes = kSplitTile * 32 * 4;    // encoding image of a tile (width <= 32, up to FP32)
 constexpr int kSplitDx = kMaxLevels * kSplitTile;    // float2 per tile of dL/d(encoding)
 constexpr int kTcRayMax = kSplitTile / kMinNr;       // rays per tile at most
 constexpr int kSplitRayFloats = kTcRayMax * 16;      // floats per tile of ray data

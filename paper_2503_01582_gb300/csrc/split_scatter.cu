@@ -1,5 +1,5 @@
-// Hash-grid scatter kernel of the split mixed-precision training step, and the
-// launchers of the split form's two extra kernels.
+// Hash-grid scatter kernel of the split training step, and the launchers of
+// the split form's two extra kernels (the FP32 encoder is instantiated here).
 #include "split_tc.cuh"
 
 namespace prenom {
@@ -76,6 +76,8 @@ cudaError_t launch_sample_encode_bf16(const WorkItem &one, const WorkList &wl, i
 
 cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int precision, int grid, cudaStream_t st)
 {
+    if (precision == 0)
+        return launch_sample_encode_t<2>(one, wl, grid, st);
     return precision == 2 ? launch_sample_encode_bf16(one, wl, grid, st) : launch_sample_encode_fp16(one, wl, grid, st);
 }
 

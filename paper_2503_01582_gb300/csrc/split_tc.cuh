@@ -1,20 +1,20 @@
-// Split execution of the mixed-precision training step.
+// Split execution of the training step.
 //
-// Inside the tensor-core kernel (two 80 KB CTAs, 16 warps per SM) the hash
-// gathers of the encoding and the reductions of its adjoint are latency-bound:
-// too few warps are in flight to cover L2 latency.  The split form runs them
-// as kernels of their own at several times the occupancy and hands the tile
-// data over through L2-sized buffers:
+// Inside the fused kernels (two 80 KB tensor-core CTAs, or one 176 KB FP32 CTA,
+// per SM) the hash gathers of the encoding and the reductions of its adjoint
+// are latency-bound: too few warps are in flight to cover L2 latency.  The
+// split form runs them as kernels of their own at several times the occupancy
+// and hands the tile data over through L2-sized buffers:
 //   1. sample_encode_kernel: one warp per ray: prior sampling (a1-a5) and the
-//      hash encoding (a6) of its samples; writes each ray's data as the
-//      tensor-core kernel keeps it, the sample depths [ray][nr] and each
-//      tile's 16-bit encoding as the exact image of the tensor-core kernel's
-//      A operand (no-swizzle interleaved core matrices);
-//   2. fused_tc_kernel in split mode: copies all three in, runs the MLP,
-//      compositing, loss and MLP backward (a7-a10) and writes dL/d(encoding)
-//      per tile, FP32, level-major, instead of scattering it;
+//      hash encoding (a6) of its samples; writes each ray's data as the MLP
+//      kernel keeps it, the sample depths [ray][nr] and each tile's encoding as
+//      the exact image the MLP kernel works on (16-bit: its tcgen05 A operand,
+//      no-swizzle interleaved core matrices; FP32: feature-major rows);
+//   2. fused_tc_kernel / fused_fp32_kernel in split mode: copy all three in,
+//      run the MLP, compositing, loss and MLP backward (a7-a10) and write
+//      dL/d(encoding) per tile, FP32, level-major, instead of scattering it;
 //   3. hash_scatter_kernel: the hash-grid scatter (a10) of those gradients.
-// The arithmetic of every step is the fused kernel's own code.
+// The arithmetic of every step is the fused kernels' own code.
 #pragma once
 
 #include "fused_tc.cuh"
@@ -23,11 +23,13 @@ namespace prenom {
 
 constexpr int kEncWarps = kThreads / 32;
 
-template <bool BF16>
+// FMT: 0 FP16 or 1 BF16 image in the tensor-core kernel's operand layout, 2 FP32
+// feature-major image [IN][kSplitTile] for the FP32 kernel.
+template <int FMT>
 __global__ void __launch_bounds__(kThreads, 4)
     sample_encode_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
-    using Hf = Half<BF16>;
+    using Hf = Half<FMT == 1>;
     __shared__ float s_rf[kEncWarps][kRayStride];
     __shared__ float s_ts[kEncWarps][kMaxNr];
     __shared__ float s_cdf[kEncWarps][kMaxNc + 1];
@@ -83,25 +85,33 @@ __global__ void __launch_bounds__(kThreads, 4)
                         e0 = fmaf(cs.wt[c], f[c].x, e0);
                         e1 = fmaf(cs.wt[c], f[c].y, e1);
                     }
-                    pk[l] = (uint32_t)Hf::bits(e0) | ((uint32_t)Hf::bits(e1) << 16);
+                    if constexpr (FMT == 2) {  // consecutive lanes write consecutive samples of a feature
+                        float *fimg = reinterpret_cast<float *>(img);
+                        fimg[(2 * l) * kSplitTile + rr * nr + k] = e0;
+                        fimg[(2 * l + 1) * kSplitTile + rr * nr + k] = e1;
+                    } else {
+                        pk[l] = (uint32_t)Hf::bits(e0) | ((uint32_t)Hf::bits(e1) << 16);
+                    }
                 }
             }
-            // row s of the tile image: INP / 8 chunks of 8 columns (16 bytes each)
-            const int s = rr * nr + k;
+            if constexpr (FMT != 2) {
+                // row s of the tile image: INP / 8 chunks of 8 columns (16 bytes each)
+                const int s = rr * nr + k;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < INP / 8)
-                    *reinterpret_cast<uint4 *>(img + il_off(s, 8 * q, INP)) =
-                        make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                for (int q = 0; q < 4; ++q)
+                    if (q < INP / 8)
+                        *reinterpret_cast<uint4 *>(img + il_off(s, 8 * q, INP)) =
+                            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+            }
         }
         __syncwarp();  // rf and ts are rewritten for the next ray
     }
 }
 
-template <bool BF16>
+template <int FMT>
 cudaError_t launch_sample_encode_t(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
-    sample_encode_kernel<BF16><<<grid, kThreads, 0, st>>>(one, wl);
+    sample_encode_kernel<FMT><<<grid, kThreads, 0, st>>>(one, wl);
     return cudaGetLastError();
 }
 
