@@ -637,7 +637,7 @@ def run_ours(args):
     peaks = load_peaks()
     feat_bytes = 8 * ARCH["L"] * ARCH["F"] * 4  # corners x levels x features x FP32, per sample
     flops = samples_per_step * mlp_macs(ARCH) * 6  # MLP: 2 MAC forward + 4 MAC backward flops per sample
-    split = prec != "fp32" and ktimes[pkg.PRENOM_KERNEL_SAMPLE_ENCODE][1] > 0
+    split = ktimes[pkg.PRENOM_KERNEL_SAMPLE_ENCODE][1] > 0
 
     def avg_s(k):
         ms, n = ktimes[k]
@@ -664,7 +664,7 @@ def run_ours(args):
     if split:
         recs.append(hbm("sample_encode_kernel", pkg.PRENOM_KERNEL_SAMPLE_ENCODE, samples_per_step * feat_bytes,
                         f"{feat_bytes} B/sample hash gather x {samples_per_step} samples"))
-        recs.append(mlp("fused_tc_kernel_split", pkg.PRENOM_KERNEL_TRAIN))
+        recs.append(mlp("fused_fp32_kernel_split" if prec == "fp32" else "fused_tc_kernel_split", pkg.PRENOM_KERNEL_TRAIN))
         recs.append(hbm("hash_scatter_kernel", pkg.PRENOM_KERNEL_SCATTER, samples_per_step * feat_bytes,
                         f"{feat_bytes} B/sample hash scatter (FP32 reductions) x {samples_per_step} samples"))
     else:
@@ -694,11 +694,10 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
                 "config": {"workload": WORKLOAD,
-                           "form": FORM[prec] + ("" if prec == "fp32" else
-                                                 {"auto": ", fused or split form as autotuned",
-                                                  "fused": ", one fused kernel",
-                                                  "split": ", split: sampling+encoding / tensor-core MLP / "
-                                                           "hash scatter"}[args.form]),
+                           "form": FORM[prec] + {"auto": ", fused or split form as autotuned",
+                                                 "fused": ", one fused kernel",
+                                                 "split": ", split: sampling+encoding / MLP kernel / "
+                                                          "hash scatter"}[args.form],
                            "rays_per_step": N_RAYS, "samples_per_ray": NR,
                            "probes": NC, "params": n_params, "autotuner": tuning,
                            "parallelism": f"{world} independent objects (one per GPU)" if world > 1 else "1 object",
