@@ -255,6 +255,39 @@ def _device_batches(batches_np, obj, stream):
     return out
 
 
+def _pack_batches(batches_np):
+    """Each host batch as one pinned byte block: its arrays at 256-byte aligned
+    offsets, in a layout shared by all batches (the same keys, shapes and dtypes)."""
+    import torch
+
+    layout, off = [], 0
+    for k, v in batches_np[0].items():
+        a = np.ascontiguousarray(v)
+        layout.append((k, off, a.shape, a.dtype))
+        off += -(-a.nbytes // 256) * 256
+    blocks = []
+    for b in batches_np:
+        buf = np.zeros(off, np.uint8)
+        for k, o, shape, dtype in layout:
+            a = np.ascontiguousarray(b[k], dtype=dtype)
+            assert a.shape == shape
+            buf[o:o + a.nbytes] = a.reshape(-1).view(np.uint8)
+        blocks.append(torch.from_numpy(buf).pin_memory())
+    return blocks, layout
+
+
+def _unpack(buf, layout):
+    """Typed views of a packed block (host or device) by the layout of _pack_batches."""
+    import torch
+
+    tdt = {np.dtype(np.float32): torch.float32, np.dtype(np.uint8): torch.uint8, np.dtype(np.int32): torch.int32}
+    out = {}
+    for k, o, shape, dtype in layout:
+        n = int(np.prod(shape)) * np.dtype(dtype).itemsize
+        out[k] = buf[o:o + n].view(tdt[np.dtype(dtype)]).view(shape)
+    return out
+
+
 def _setup_single(pkg, ctx, precision, seed, stream):
     arch = pkg.make_arch(**ARCH, precision=PRECISION[precision])
     probe = ctx.create_object(arch)
@@ -531,13 +564,15 @@ def run_ours(args):
     value = samples_per_step * args.steps * world / (ms / 1e3)
 
     # ---- end to end through the public API with host buffers: every step copies its
-    # batch from pinned host memory (on a copy stream, double-buffered, so the copy
+    # batch from pinned host memory (one block per batch, its arrays at 256-byte
+    # offsets, so one copy per step; on a copy stream, double-buffered, so the copy
     # of step i+1 overlaps step i) and reads its loss back into pinned memory
-    pinned = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in b.items()} for b in batches_np]
-    h2d = sum(t.numel() * t.element_size() for t in pinned[0].values())
+    pinned, layout = _pack_batches(batches_np)
+    h2d = pinned[0].numel()
     e2e_steps = max(args.steps // 2, 5)
     loss_host = torch.zeros(e2e_steps).pin_memory()
-    staging = [{k: torch.empty_like(v, device="cuda") for k, v in p.items()} for p in pinned[:2]]
+    staging = [torch.empty_like(pinned[0], device="cuda") for _ in range(2)]
+    views = [dict(_unpack(buf, layout), obj=obj) for buf in staging]
     copy_stream = torch.cuda.Stream()
     copied = [torch.cuda.Event() for _ in range(2)]
     consumed = [torch.cuda.Event() for _ in range(2)]
@@ -546,15 +581,13 @@ def run_ours(args):
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         slot = i % 2
-        src, dst = pinned[i % len(pinned)], staging[slot]
         if i >= 2:
             copy_stream.wait_event(consumed[slot])  # the step that read this buffer is done
         with torch.cuda.stream(copy_stream):
-            for k in src:
-                dst[k].copy_(src[k], non_blocking=True)
+            staging[slot].copy_(pinned[i % len(pinned)], non_blocking=True)
             copied[slot].record(copy_stream)
         stream.wait_event(copied[slot])
-        ctx.train_step([dict(dst, obj=obj)], opts, loss)
+        ctx.train_step([views[slot]], opts, loss)
         with torch.cuda.stream(stream):
             loss_host[i].copy_(loss[0], non_blocking=True)
             consumed[slot].record(stream)

@@ -326,8 +326,8 @@ size_t assign_split(BatchDesc &bd, unsigned char *base)
 // runs one warp per ray slot, the scatter kernel one block per tile range.
 int grid_sample_encode(const prenom_ctx *c, int total_tiles, int rays_per_tile)
 {
-    const int64_t blocks = ((int64_t)total_tiles * rays_per_tile + kThreads / 32 - 1) / (kThreads / 32);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)c->n_sm * 4));
+    const int64_t slots = (int64_t)total_tiles * rays_per_tile;  // one block per slot at most
+    return (int)std::max<int64_t>(1, std::min<int64_t>(slots, (int64_t)c->n_sm * 4));
 }
 
 int grid_scatter(const prenom_ctx *c, int total_tiles)

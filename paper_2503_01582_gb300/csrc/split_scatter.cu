@@ -17,8 +17,9 @@ __global__ void __launch_bounds__(kThreads, 5)
     const int n_items = wl.items ? wl.n_items : 1;
     const int total = wl.items ? wl.total_tiles : one.bd.n_tiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int t0 = (int)blockIdx.x * per, t1 = min(total, t0 + per);
+    // contiguous tile ranges whose lengths differ by at most one
+    const int t0 = (int)((long long)blockIdx.x * total / gridDim.x);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
     int k = -1;
     for (int t = t0; t < t1; ++t) {
         int nk = k < 0 ? item_of_tile(list, n_items, t) : k;

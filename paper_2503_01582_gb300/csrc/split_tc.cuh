@@ -42,7 +42,10 @@ __global__ void __launch_bounds__(kThreads, 4)
     float *rf = s_rf[warp];
     float *ts = s_ts[warp];
     float *cdf = s_cdf[warp];
-    for (long long j = (long long)blockIdx.x * kEncWarps + warp; j < slots; j += (long long)gridDim.x * kEncWarps) {
+    // ray slot j = warp * gridDim.x + block (+ multiples of the grid's warp count):
+    // every block gets the same number of rays, to within one, so the SMs share
+    // the gathers evenly whatever the slot count
+    for (long long j = (long long)warp * gridDim.x + blockIdx.x; j < slots; j += (long long)gridDim.x * kEncWarps) {
         const int t = (int)(j / NR), rr = (int)(j % NR);
         const WorkItem &it = list[item_of_tile(list, n_items, t)];
         const ObjDesc &od = it.od;
