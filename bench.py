@@ -713,7 +713,7 @@ def run_ours(args):
     roofline = dict(dom)
     roofline["traffic"] = profiled_traffic(dom["kernel"] + "/" + prec)
     roofline["kernel"] = dom["kernel"] + ", " + prec
-    roofline["other_kernels"] = [r for r in recs if r is not dom]
+    roofline["other_kernels"] = [dict(r, traffic=profiled_traffic(r["kernel"] + "/" + prec)) for r in recs if r is not dom]
     roofline["step_kernels_us"] = round(sum(r["avg_us"] for r in recs), 2)
 
     if rank == 0:

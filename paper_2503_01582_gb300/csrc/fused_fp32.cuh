@@ -390,13 +390,16 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
 // Adjoint with v_k = gC.c_k + gD t_k + gA:
 //   dL/dsigma_k = delta_k (T_{k+1} v_k - sum_{j>k} w_j v_j).
 // Writes dL/do (o = raw MLP outputs) into dOT; returns the ray's loss (train mode).
-__device__ __forceinline__ float composite_warp(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
-                                                const float *rf, const float *ts, const float *OT, float *dOT,
-                                                int SP, int lane)
+// Q = ceil(nr / 32) samples per lane as a compile-time count (QS = 1 or 2, the
+// common sample counts), or QS = 0 for any count up to kMaxNr.
+template <int QS>
+__device__ __forceinline__ float composite_warp_q(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
+                                                  const float *rf, const float *ts, const float *OT, float *dOT,
+                                                  int SP, int lane)
 {
-    constexpr int QM = kMaxNr / 32;
+    constexpr int QM = QS > 0 ? QS : kMaxNr / 32;
     const int nr = bd.nr;
-    const int Q = (nr + 31) >> 5;
+    const int Q = QS > 0 ? QS : (nr + 31) >> 5;
     const float tf = rf[RF_TF];
     float sig[QM], col[QM][3], tk[QM], dl[QM], tau[QM], o0[QM], pre[QM];
     float run = 0.f;
@@ -534,6 +537,17 @@ __device__ __forceinline__ float composite_warp(const ObjDesc &od, const BatchDe
             after += wv[q];
     }
     return loss;
+}
+
+__device__ __forceinline__ float composite_warp(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
+                                                const float *rf, const float *ts, const float *OT, float *dOT,
+                                                int SP, int lane)
+{
+    switch ((bd.nr + 31) >> 5) {
+    case 1: return composite_warp_q<1>(od, bd, r, gr, rf, ts, OT, dOT, SP, lane);
+    case 2: return composite_warp_q<2>(od, bd, r, gr, rf, ts, OT, dOT, SP, lane);
+    default: return composite_warp_q<0>(od, bd, r, gr, rf, ts, OT, dOT, SP, lane);
+    }
 }
 
 // Block-wide copy of a work item into shared memory (the inner loops then

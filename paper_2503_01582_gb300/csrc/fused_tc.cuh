@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             pt0 = tid < ns2 ? bd.sp_t[(size_t)ray02 * nr + tid] : 0.f;
             pre_t = t + 1;
         }
-        // ---- scaled 16-bit dL/dO, and dW_out on the CUDA cores
+        // ---- scaled 16-bit dL/dO (dW_out is summed during the first backward product)
         if (tid < kTcTile) {
             uint32_t lo = (uint32_t)Hf::bits(dOT[tid] * scale) | ((uint32_t)Hf::bits(dOT[SP + tid] * scale) << 16);
             uint32_t hi = (uint32_t)Hf::bits(dOT[2 * SP + tid] * scale) |
@@ -600,34 +600,6 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (!(Hf::finite(lo & 0xFFFFu) && Hf::finite(lo >> 16) && Hf::finite(hi & 0xFFFFu) &&
                   Hf::finite(hi >> 16)) && bd.overflow)
                 atomicExch(bd.overflow, 1);
-        }
-        {  // dW_out[o][i0..i0+7] over the tile's samples: each thread sums an interleaved slice
-            // of the samples (conflict-free 16-byte rows of H), the slices meet by shuffles
-            constexpr int SL = kThreads / (W / 2);  // slices per output group (8, 16, 32 for W = 64, 32, 16)
-            const int pair = tid / SL, slice = tid % SL;
-            const int o = pair / (W / 8), i0 = (pair % (W / 8)) * 8;
-            const unsigned char *hl = HA + (H - 1) * L::ha;
-            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-            for (int k = 0; k < kTcTile / SL; ++k) {
-                const int s = k * SL + slice;
-                const float d = dOT[o * SP + s];
-                const uint4 hv = *reinterpret_cast<const uint4 *>(hl + il_off(s, i0, W));
-                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    acc[2 * j] = fmaf(d, Hf::value((uint16_t)(hw[j] & 0xFFFFu)), acc[2 * j]);
-                    acc[2 * j + 1] = fmaf(d, Hf::value((uint16_t)(hw[j] >> 16)), acc[2 * j + 1]);
-                }
-            }
-#pragma unroll
-            for (int off = SL / 2; off > 0; off >>= 1)
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    acc[j] += __shfl_xor_sync(kFull, acc[j], off);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                dwo_acc[j] += acc[j];  // meaningful in slice 0 of each group
         }
         tc_sync();
         // ---- backward through the hidden layers
@@ -639,6 +611,36 @@ __global__ void __launch_bounds__(kThreads, 2)
                 else
                     mma_gemm(tmem, kmajor(DA, kDaCols), mnmajor(WtH + l * L::wh, W), W, id_dh, false);
                 mma_commit(mbar);
+            }
+            if (l == H - 1) {
+                // dW_out[o][i0..i0+7] on the CUDA cores while the tensor cores form dH_{H-1}:
+                // each thread sums an interleaved slice of the tile's samples (conflict-free
+                // 16-byte rows of H), the slices meet by shuffles
+                constexpr int SL = kThreads / (W / 2);  // slices per output group (8, 16, 32 for W = 64, 32, 16)
+                const int pair = tid / SL, slice = tid % SL;
+                const int o = pair / (W / 8), i0 = (pair % (W / 8)) * 8;
+                const unsigned char *hl = HA + (H - 1) * L::ha;
+                float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+                for (int k = 0; k < kTcTile / SL; ++k) {
+                    const int s = k * SL + slice;
+                    const float d = dOT[o * SP + s];
+                    const uint4 hv = *reinterpret_cast<const uint4 *>(hl + il_off(s, i0, W));
+                    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        acc[2 * j] = fmaf(d, Hf::value((uint16_t)(hw[j] & 0xFFFFu)), acc[2 * j]);
+                        acc[2 * j + 1] = fmaf(d, Hf::value((uint16_t)(hw[j] >> 16)), acc[2 * j + 1]);
+                    }
+                }
+#pragma unroll
+                for (int off = SL / 2; off > 0; off >>= 1)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        acc[j] += __shfl_xor_sync(kFull, acc[j], off);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    dwo_acc[j] += acc[j];  // meaningful in slice 0 of each group
             }
             const bool done = mbar_poll(mbar, parity, bd.status);
             parity ^= 1u;
