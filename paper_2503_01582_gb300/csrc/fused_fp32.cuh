@@ -385,13 +385,67 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
 }
 
 // ------------------------------------------------------------- compositing
+// The ray's loss (Eq. 8-9, divided by the batch's ray count) and its
+// gradients with respect to C-hat, D-hat and A (from the caller's upstream
+// gradients in kRenderBwd mode).  ssum_total() gives the ray's sum of sigma,
+// evaluated only for a background ray.
+template <typename SsumFn>
+__device__ __forceinline__ float ray_loss(const ObjDesc &od, const BatchDesc &bd, int gr, const float *rf,
+                                          const float (&Cr)[3], float D, float A, SsumFn ssum_total, float (&gC)[3],
+                                          float &gD, float &gA, bool &background)
+{
+    float loss = 0.f;
+    background = false;
+    if (bd.mode == kRenderBwd) {
+        const float *up = bd.upstream + (size_t)gr * 5;
+        gC[0] = up[0];
+        gC[1] = up[1];
+        gC[2] = up[2];
+        gD = up[3];
+        gA = up[4];
+        return 0.f;
+    }
+    background = rf[RF_OBJ] < 0.5f;
+    if (!background) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float e = Cr[c] - rf[RF_RGB + c];
+            loss = fmaf(e, e, loss);
+            gC[c] = 2.f * e;
+        }
+        const float ed = D - rf[RF_DEPTH];
+        loss += od.lambda_d * fabsf(ed);
+        gD = ed > 0.f ? od.lambda_d : (ed < 0.f ? -od.lambda_d : 0.f);
+        gA = 0.f;
+    } else {
+        float dot = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float crd = rf[RF_CR + c];
+            const float e = (Cr[c] + (1.f - A) * crd) - crd;
+            loss = fmaf(e, e, loss);
+            gC[c] = 2.f * e;
+            dot = fmaf(2.f * e, crd, dot);
+        }
+        gD = 0.f;
+        gA = -dot;
+        loss = fmaf(od.lambda_sigma, ssum_total(), loss);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        gC[c] *= bd.inv_r;
+    gD *= bd.inv_r;
+    gA *= bd.inv_r;
+    return loss * bd.inv_r;
+}
+
 // One warp per ray; lane holds samples lane*Q .. lane*Q+Q-1 (Q = ceil(nr/32)).
 // Forward: tau_k = sigma_k delta_k, T_k = exp(-sum_{j<k} tau_j), w_k = T_k (1 - exp(-tau_k)).
 // Adjoint with v_k = gC.c_k + gD t_k + gA:
 //   dL/dsigma_k = delta_k (T_{k+1} v_k - sum_{j>k} w_j v_j).
 // Writes dL/do (o = raw MLP outputs) into dOT; returns the ray's loss (train mode).
-// Q = ceil(nr / 32) samples per lane as a compile-time count (QS = 1 or 2, the
-// common sample counts), or QS = 0 for any count up to kMaxNr.
+// Q = QS samples per lane as a compile-time count, or QS = 0 for any count up to
+// kMaxNr (the tile routine below uses QS = 1 and spreads longer rays over warps).
 template <int QS>
 __device__ __forceinline__ float composite_warp_q(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
                                                   const float *rf, const float *ts, const float *OT, float *dOT,
@@ -462,49 +516,9 @@ __device__ __forceinline__ float composite_warp_q(const ObjDesc &od, const Batch
         }
         return 0.f;
     }
-    float gC[3], gD, gA, loss = 0.f;
-    bool background = false;
-    if (bd.mode == kRenderBwd) {
-        const float *up = bd.upstream + (size_t)gr * 5;
-        gC[0] = up[0];
-        gC[1] = up[1];
-        gC[2] = up[2];
-        gD = up[3];
-        gA = up[4];
-    } else {
-        background = rf[RF_OBJ] < 0.5f;
-        if (!background) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float e = Cr[c] - rf[RF_RGB + c];
-                loss = fmaf(e, e, loss);
-                gC[c] = 2.f * e;
-            }
-            const float ed = D - rf[RF_DEPTH];
-            loss += od.lambda_d * fabsf(ed);
-            gD = ed > 0.f ? od.lambda_d : (ed < 0.f ? -od.lambda_d : 0.f);
-            gA = 0.f;
-        } else {
-            float dot = 0.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float crd = rf[RF_CR + c];
-                const float e = (Cr[c] + (1.f - A) * crd) - crd;
-                loss = fmaf(e, e, loss);
-                gC[c] = 2.f * e;
-                dot = fmaf(2.f * e, crd, dot);
-            }
-            gD = 0.f;
-            gA = -dot;
-            loss = fmaf(od.lambda_sigma, warp_sum(ssum), loss);
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            gC[c] *= bd.inv_r;
-        gD *= bd.inv_r;
-        gA *= bd.inv_r;
-        loss *= bd.inv_r;
-    }
+    float gC[3], gD, gA;
+    bool background;
+    const float loss = ray_loss(od, bd, gr, rf, Cr, D, A, [&]() { return warp_sum(ssum); }, gC, gD, gA, background);
     // adjoint: suffix sums of w v
     float wv[QM], v[QM];
     float lsum = 0.f;
@@ -539,15 +553,157 @@ __device__ __forceinline__ float composite_warp_q(const ObjDesc &od, const Batch
     return loss;
 }
 
-__device__ __forceinline__ float composite_warp(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
-                                                const float *rf, const float *ts, const float *OT, float *dOT,
-                                                int SP, int lane)
+
+__device__ __forceinline__ void group_bar(int id, int nthreads)
 {
-    switch ((bd.nr + 31) >> 5) {
-    case 1: return composite_warp_q<1>(od, bd, r, gr, rf, ts, OT, dOT, SP, lane);
-    case 2: return composite_warp_q<2>(od, bd, r, gr, rf, ts, OT, dOT, SP, lane);
-    default: return composite_warp_q<0>(od, bd, r, gr, rf, ts, OT, dOT, SP, lane);
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The same compositing, loss and adjoint with a ray spread over G = ceil(nr / 32)
+// warps, one sample per lane: warp g of the group holds samples 32 g .. 32 g + 31.
+// The warps meet through named barrier `bar` (G x 32 threads) and 8 floats per
+// warp of `xs` (shared memory): the warp's sum of tau (slot 0), its partial sums
+// of w c, w t, w and sigma (slots 1-6) and its sum of w v (slot 7), each combined
+// in warp order.  Every warp of the group returns the ray's loss.
+template <int G>
+__device__ __forceinline__ float composite_group(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
+                                                 const float *rf, const float *ts, const float *OT, float *dOT,
+                                                 int SP, int lane, int wig, float *xs, int bar)
+{
+    const int nr = bd.nr;
+    const int k = 32 * wig + lane;
+    const bool valid = k < nr;
+    const int s = r * nr + k;
+    const float tf = rf[RF_TF];
+    float o0 = 0.f, sig = 0.f, col[3] = {0.f, 0.f, 0.f}, tk = 0.f, dl = 0.f, tau = 0.f;
+    if (valid) {
+        o0 = OT[s];
+        sig = expf(fminf(o0, 15.f));
+        if (bd.out_sigma)
+            bd.out_sigma[(size_t)gr * nr + k] = sig;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            col[c] = 1.f / (1.f + expf(-OT[(1 + c) * SP + s]));
+        tk = ts[s];
+        const float tnext = (k + 1 < nr) ? ts[s + 1] : tf;
+        dl = tnext - tk;
+        tau = sig * dl;
     }
+    const float incl = warp_incl_scan(tau, lane);
+    float excl = __shfl_up_sync(kFull, incl, 1);  // this warp's samples before this one
+    if (lane == 0)
+        excl = 0.f;
+    if (lane == 31)
+        xs[8 * wig] = incl;
+    group_bar(bar, 32 * G);
+    float pref = 0.f;  // earlier warps' samples
+#pragma unroll
+    for (int g = 0; g < G - 1; ++g)
+        if (g < wig)
+            pref += xs[8 * g];
+    const float T = expf(-(pref + excl));
+    const float w = T * (-expm1f(-tau));
+    float part[6] = {w * col[0], w * col[1], w * col[2], w * tk, w, sig};
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        part[i] = warp_sum(part[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            xs[8 * wig + 1 + i] = part[i];
+    group_bar(bar, 32 * G);
+    float tot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            tot[i] += xs[8 * g + 1 + i];
+    const float Cr[3] = {tot[0], tot[1], tot[2]};
+    const float D = tot[3], A = tot[4];
+    if (bd.mode == kRender) {
+        if (lane == 0 && wig == 0) {
+            if (bd.out_rgb) {
+                bd.out_rgb[(size_t)gr * 3 + 0] = Cr[0];
+                bd.out_rgb[(size_t)gr * 3 + 1] = Cr[1];
+                bd.out_rgb[(size_t)gr * 3 + 2] = Cr[2];
+            }
+            if (bd.out_depth)
+                bd.out_depth[gr] = D;
+            if (bd.out_acc)
+                bd.out_acc[gr] = A;
+        }
+        return 0.f;
+    }
+    float gC[3], gD, gA;
+    bool background;
+    const float loss = ray_loss(od, bd, gr, rf, Cr, D, A, [&]() { return tot[5]; }, gC, gD, gA, background);
+    // adjoint: suffix sums of w v over the ray
+    const float v = fmaf(gC[0], col[0], fmaf(gC[1], col[1], fmaf(gC[2], col[2], fmaf(gD, tk, gA))));
+    const float wv = w * v;
+    const float sincl = warp_incl_suffix(wv, lane);
+    if (lane == 0)
+        xs[8 * wig + 7] = sincl;
+    group_bar(bar, 32 * G);
+    float after = __shfl_down_sync(kFull, sincl, 1);  // later lanes of this warp
+    if (lane == 31)
+        after = 0.f;
+#pragma unroll
+    for (int g = G - 1; g > 0; --g)
+        if (g > wig)
+            after += xs[8 * g + 7];
+    if (valid) {
+        const float sig_reg = background ? od.lambda_sigma * bd.inv_r : 0.f;
+        const float Tn = expf(-(pref + excl + tau));
+        const float dsig = fmaf(dl, fmaf(Tn, v, -after), sig_reg);
+        dOT[s] = (o0 < 15.f) ? dsig * sig : 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float dc = w * gC[c];
+            dOT[(1 + c) * SP + s] = dc * col[c] * (1.f - col[c]);
+        }
+    }
+    return loss;
+}
+
+// Compositing of a tile's nrt rays by all warps of the block: one warp per ray
+// for rays of at most 32 samples, else G = ceil(nr / 32) warps per ray (G nrt
+// <= 8 warps, as a tile holds 128 samples at most).  xs: 64 floats of scratch
+// shared memory; named barriers 1 .. nrt.  Returns this thread's share of the
+// tile's loss (each ray counted once, on one lane).
+__device__ __forceinline__ float composite_tile(const ObjDesc &od, const BatchDesc &bd, int ray0, int nrt,
+                                               const float *rayf, const float *ts, const float *OT, float *dOT,
+                                               int SP, float *xs)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int G = (bd.nr + 31) >> 5;
+    float lsum = 0.f;
+    if (G == 1) {
+        for (int r = warp; r < nrt; r += kThreads / 32) {
+            const float lr = composite_warp_q<1>(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane);
+            if (lane == 0)
+                lsum += lr;
+        }
+        return lsum;
+    }
+    const int r = warp / G, wig = warp % G;
+    if (r >= nrt)
+        return 0.f;
+    float lr;
+    switch (G) {
+    case 2:
+        lr = composite_group<2>(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane, wig,
+                                xs + 8 * G * r, 1 + r);
+        break;
+    case 3:
+        lr = composite_group<3>(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane, wig,
+                                xs + 8 * G * r, 1 + r);
+        break;
+    default:
+        lr = composite_group<4>(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane, wig,
+                                xs + 8 * G * r, 1 + r);
+        break;
+    }
+    return (lane == 0 && wig == 0) ? lr : 0.f;
 }
 
 // Block-wide copy of a work item into shared memory (the inner loops then

@@ -568,11 +568,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (!ok)
             break;
         // ---- compositing, loss and its adjoint (FP32)
-        for (int r = warp; r < nrt; r += kThreads / 32) {
-            const float lr = composite_warp(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane);
-            if (lane == 0)
-                loss_acc += lr;
-        }
+        // (the sampler's CDF scratch serves as the compositing's exchange buffer)
+        loss_acc += composite_tile(od, bd, ray0, nrt, rayf, ts, OT, dOT, SP, cdfs);
         __syncthreads();
         if (!train)
             continue;
