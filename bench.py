@@ -458,7 +458,7 @@ def _meta_compare(pkg, ctx, stream, prec):
             "value": n_smp * steps / (ms / 1e3), "unit": "samples/s", "ms_per_meta_step": ms / steps}
 
 
-def _ablation_compare(pkg, ctx, stream, prec, steps=300):
+def _ablation_compare(pkg, ctx, stream, prec, steps=300, seeds=(0, 1, 2)):
     """Sampling ablation (the analogue of the paper's Table IV row on
     probabilistic sampling): the small scene (sphere + box, 8 views of 64x64)
     trained for `steps` Adam steps of 256 rays x 32 samples with prior sampling
@@ -466,7 +466,10 @@ def _ablation_compare(pkg, ctx, stream, prec, steps=300):
     steps as §III-B does) and with uniform sampling (a zero grid: every ray
     escapes, so the flat CDF of the escape rule applies), on the same rays; then
     colour MSE (all pixels, black background) and depth L1 (object pixels) on 4
-    held-out 64x64 views, sampled the way each was trained."""
+    held-out 64x64 views, sampled the way each was trained.  Each seed draws its
+    own initial parameters and ray batches; mean and standard deviation over the
+    seeds are reported (a single run moves by tens of percent with the rounding
+    of a kernel change)."""
     import torch
     from synth import (cameras_on_sphere, init_params, make_ray_pool, prior_grid, sample_batch, scene_sphere_box)
 
@@ -481,33 +484,43 @@ def _ablation_compare(pkg, ctx, stream, prec, steps=300):
     probe = ctx.create_object(arch)
     n = ctx.param_count(probe)
     ctx.destroy_object(probe)
-    theta = init_params(n - (32 * 16 + 32 * 32 + 4 * 32), [(32, 16), (32, 32), (4, 32)], 5).astype(np.float32)
-    batches = [_device_batches([sample_batch(pool, 256, 7000 + i)], 0, stream)[0] for i in range(steps)]
     opts = pkg.make_opts(nc=32, nr=32, lr=1e-2)
     loss = torch.zeros(1, device="cuda")
-    out = {}
     prior = prior_grid(sc, 32, 0)
-    for name, grid, refresh in (("prior_sampling", prior, 0), ("prior_sampling_refresh_every_50", prior, 50),
-                                ("uniform_sampling", np.zeros((32, 32, 32), np.float32), 0)):
-        obj = ctx.create_object(arch, theta)
-        ctx.set_prior_grid(obj, grid)
-        for b in batches:
-            b["obj"] = obj
+    variants = (("prior_sampling", prior, 0), ("prior_sampling_refresh_every_50", prior, 50),
+                ("uniform_sampling", np.zeros((32, 32, 32), np.float32), 0))
+    runs = {name: [] for name, _, _ in variants}
+    for seed in seeds:
+        theta = init_params(n - (32 * 16 + 32 * 32 + 4 * 32), [(32, 16), (32, 32), (4, 32)], 5 + seed)
+        theta = theta.astype(np.float32)
+        batches = [_device_batches([sample_batch(pool, 256, 7000 + 1000 * seed + i)], 0, stream)[0]
+                   for i in range(steps)]
+        for name, grid, refresh in variants:
+            obj = ctx.create_object(arch, theta)
+            ctx.set_prior_grid(obj, grid)
+            for b in batches:
+                b["obj"] = obj
 
-        def step(i, obj=obj, refresh=refresh):
-            if refresh and i > 0 and i % refresh == 0:  # §III-B: the prior follows the field every m iterations
-                ctx.refresh_prior(obj, 32)
-            ctx.train_step([batches[i]], opts, loss)
+            def step(i, obj=obj, refresh=refresh):
+                if refresh and i > 0 and i % refresh == 0:  # §III-B: the prior follows the field every m iterations
+                    ctx.refresh_prior(obj, 32)
+                ctx.train_step([batches[i]], opts, loss)
 
-        ms = _time(stream, step, steps, 0)
-        r = ctx.render(dict(hb, obj=obj), opts)
-        rgb, depth = r["rgb"].cpu().numpy(), r["depth"].cpu().numpy()
-        out[name] = {"colour_mse": float(np.mean((rgb - tgt) ** 2)),
-                     "depth_l1": float(np.mean(np.abs(depth - held.depth)[objm])),
-                     "final_loss": float(loss.item()), "ms_per_step": ms / steps}
-        ctx.destroy_object(obj)
+            ms = _time(stream, step, steps, 0)
+            r = ctx.render(dict(hb, obj=obj), opts)
+            rgb, depth = r["rgb"].cpu().numpy(), r["depth"].cpu().numpy()
+            runs[name].append((float(np.mean((rgb - tgt) ** 2)), float(np.mean(np.abs(depth - held.depth)[objm])),
+                               float(loss.item()), ms / steps))
+            ctx.destroy_object(obj)
+    out = {}
+    for name, rs in runs.items():
+        a = np.array(rs)
+        out[name] = {"colour_mse": float(a[:, 0].mean()), "colour_mse_std": float(a[:, 0].std(ddof=1)),
+                     "depth_l1": float(a[:, 1].mean()), "depth_l1_std": float(a[:, 1].std(ddof=1)),
+                     "final_loss": float(a[:, 2].mean()), "ms_per_step": float(a[:, 3].mean())}
     out["workload"] = ("sphere+box scene, %d Adam steps x 256 rays x 32 samples (Nc 32), L=8 T=2^14 res 16..256, "
-                       "MLP 16-32-32-4, same rays for both; 4 held-out 64x64 views" % steps)
+                       "MLP 16-32-32-4, same rays for every variant; 4 held-out 64x64 views; mean and std over "
+                       "%d seeds" % (steps, len(seeds)))
     return out
 
 
