@@ -87,13 +87,24 @@ __device__ __forceinline__ uint32_t mma_idesc(uint32_t fmt, int M, int N, uint32
            ((uint32_t)(M >> 4) << 24);
 }
 
-// D (+)= A * B^T over K (multiple of 16), issued by the calling thread.
-__device__ __forceinline__ void mma_gemm(uint32_t d_tmem, const Operand &a, const Operand &b, int K, uint32_t idesc,
+// D (+)= A * B^T over K (a multiple of 16, known at compile time), issued by
+// the calling thread.  The descriptors are built once; each further K = 16
+// slice only advances their start-address field (14 bits of address / 16: a
+// shared-memory address below 256 KB never carries out of it), so the single
+// issuing thread spends a few cycles per MMA instead of a dependent chain of
+// 64-bit shifts and masks.
+template <int K>
+__device__ __forceinline__ void mma_gemm(uint32_t d_tmem, const Operand &a, const Operand &b, uint32_t idesc,
                                          bool accumulate)
 {
+    static_assert(K % 16 == 0 && K > 0, "K is a multiple of 16");
+    const uint64_t ad0 = smem_desc(a.addr, a.kstr, a.mnstr);
+    const uint64_t bd0 = smem_desc(b.addr, b.kstr, b.mnstr);
+    const uint64_t astep = (uint64_t)((2u * a.kstr) >> 4), bstep = (uint64_t)((2u * b.kstr) >> 4);
+#pragma unroll
     for (int ks = 0; ks < K / 16; ++ks) {
-        const uint64_t ad = smem_desc(a.addr + ks * 2 * a.kstr, a.kstr, a.mnstr);
-        const uint64_t bd = smem_desc(b.addr + ks * 2 * b.kstr, b.kstr, b.mnstr);
+        const uint64_t ad = ad0 + (uint64_t)ks * astep;
+        const uint64_t bd = bd0 + (uint64_t)ks * bstep;
         const uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -525,7 +536,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (tid == 0) {
                 const Operand a = l == 0 ? kmajor(XA, INP) : kmajor(HA + (l - 1) * L::ha, W);
                 const Operand b = l == 0 ? kmajor(Wt0, INP) : kmajor(WtH + (l - 1) * L::wh, W);
-                mma_gemm(tmem, a, b, l == 0 ? INP : W, id_fwd, false);
+                if (l == 0)
+                    mma_gemm<INP>(tmem, a, b, id_fwd, false);
+                else
+                    mma_gemm<W>(tmem, a, b, id_fwd, false);
                 mma_commit(mbar);
             }
             const bool done = mbar_poll(mbar, parity, bd.status);
@@ -550,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (!ok)
             break;
         if (tid == 0) {
-            mma_gemm(tmem, kmajor(HA + (H - 1) * L::ha, W), kmajor(WtO, W), W, id_out, false);
+            mma_gemm<W>(tmem, kmajor(HA + (H - 1) * L::ha, W), kmajor(WtO, W), id_out, false);
             mma_commit(mbar);
         }
         {
@@ -604,9 +618,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             // dH_l = dOut_{l+1} W_{l+1}: for l = H-1 from the output layer
             if (tid == 0) {
                 if (l == H - 1)
-                    mma_gemm(tmem, kmajor(DOA, 16), mnmajor(WtO, W), 16, id_dh, false);
+                    mma_gemm<16>(tmem, kmajor(DOA, 16), mnmajor(WtO, W), id_dh, false);
                 else
-                    mma_gemm(tmem, kmajor(DA, kDaCols), mnmajor(WtH + l * L::wh, W), W, id_dh, false);
+                    mma_gemm<W>(tmem, kmajor(DA, kDaCols), mnmajor(WtH + l * L::wh, W), id_dh, false);
                 mma_commit(mbar);
             }
             if (l == H - 1) {
@@ -669,18 +683,18 @@ __global__ void __launch_bounds__(kThreads, 2)
             // dW_l += dH_l^T A_l (M = 64 rows of DA, N = width of A_l, K = 128 samples)
             if (tid == 0 && ok) {
                 if (l > 0)
-                    mma_gemm(tmem + dw_col<W, IN>(l), mnmajor(DA, kDaCols), mnmajor(HA + (l - 1) * L::ha, W),
-                             kTcTile, id_dw, !first_dw);
+                    mma_gemm<kTcTile>(tmem + dw_col<W, IN>(l), mnmajor(DA, kDaCols), mnmajor(HA + (l - 1) * L::ha, W),
+                                      id_dw, !first_dw);
                 else
-                    mma_gemm(tmem + dw_col<W, IN>(0), mnmajor(DA, kDaCols), mnmajor(XA, INP), kTcTile, id_dw0,
-                             !first_dw);
+                    mma_gemm<kTcTile>(tmem + dw_col<W, IN>(0), mnmajor(DA, kDaCols), mnmajor(XA, INP), id_dw0,
+                                      !first_dw);
             }
         }
         if (!ok)
             break;
         // dX = dH_0 W_0 -> TMEM R0 (N = INP), then the hash scatter
         if (tid == 0) {
-            mma_gemm(tmem, kmajor(DA, kDaCols), mnmajor(Wt0, INP), W, id_dx, false);
+            mma_gemm<W>(tmem, kmajor(DA, kDaCols), mnmajor(Wt0, INP), id_dx, false);
             mma_commit(mbar);
         }
         const bool done_dx = mbar_poll(mbar, parity, bd.status);
