@@ -642,25 +642,33 @@ def run_ours(args):
     loss_host = torch.zeros(e2e_steps).pin_memory()
     staging = [torch.empty_like(pinned[0], device="cuda") for _ in range(2)]
     views = [dict(_unpack(buf, layout), obj=obj) for buf in staging]
-    copy_stream = torch.cuda.Stream()
+    # the losses are double-buffered too, and read back on a stream of their own,
+    # so that neither copy direction waits in the training stream
+    losses = [torch.zeros(1, device="cuda") for _ in range(2)]
+    copy_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
     copied = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
+    stepped = [torch.cuda.Event() for _ in range(2)]
+    read = [torch.cuda.Event() for _ in range(2)]
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         slot = i % 2
         if i >= 2:
-            copy_stream.wait_event(consumed[slot])  # the step that read this buffer is done
+            copy_stream.wait_event(stepped[slot])  # the step that read this input buffer is done
         with torch.cuda.stream(copy_stream):
             staging[slot].copy_(pinned[i % len(pinned)], non_blocking=True)
             copied[slot].record(copy_stream)
         stream.wait_event(copied[slot])
-        ctx.train_step([views[slot]], opts, loss)
-        with torch.cuda.stream(stream):
-            loss_host[i].copy_(loss[0], non_blocking=True)
-            consumed[slot].record(stream)
-    stream.synchronize()
+        if i >= 2:
+            stream.wait_event(read[slot])  # this loss buffer's previous value has been read back
+        ctx.train_step([views[slot]], opts, losses[slot])
+        stepped[slot].record(stream)
+        d2h_stream.wait_event(stepped[slot])
+        with torch.cuda.stream(d2h_stream):
+            loss_host[i].copy_(losses[slot][0], non_blocking=True)
+            read[slot].record(d2h_stream)
+    torch.cuda.synchronize()
     e2e_losses = loss_host.numpy().copy()
     e2e_s = time.perf_counter() - t0
     assert np.all(np.isfinite(e2e_losses))

@@ -224,18 +224,18 @@ cudaError_t launch_zero_losses(const WorkItem *items, int n, cudaStream_t st)
     return cudaGetLastError();
 }
 
-size_t fused_tc_smem(int W, int IN, int H)
+size_t fused_tc_smem(int W, int IN, int H, bool split)
 {
     switch (W * 100 + IN) {
-    case 1608: return TcLayout<16, 8>::bytes(H);
-    case 1616: return TcLayout<16, 16>::bytes(H);
-    case 1632: return TcLayout<16, 32>::bytes(H);
-    case 3208: return TcLayout<32, 8>::bytes(H);
-    case 3216: return TcLayout<32, 16>::bytes(H);
-    case 3232: return TcLayout<32, 32>::bytes(H);
-    case 6408: return TcLayout<64, 8>::bytes(H);
-    case 6416: return TcLayout<64, 16>::bytes(H);
-    case 6432: return TcLayout<64, 32>::bytes(H);
+    case 1608: return TcLayout<16, 8>::bytes(H, split);
+    case 1616: return TcLayout<16, 16>::bytes(H, split);
+    case 1632: return TcLayout<16, 32>::bytes(H, split);
+    case 3208: return TcLayout<32, 8>::bytes(H, split);
+    case 3216: return TcLayout<32, 16>::bytes(H, split);
+    case 3232: return TcLayout<32, 32>::bytes(H, split);
+    case 6408: return TcLayout<64, 8>::bytes(H, split);
+    case 6416: return TcLayout<64, 16>::bytes(H, split);
+    case 6432: return TcLayout<64, 32>::bytes(H, split);
     default: return 0;
     }
 }
@@ -256,7 +256,8 @@ cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precisio
     one.od = od;
     one.bd = bd;
     one.tile_begin = 0;
-    return tc_dispatch(one, WorkList{nullptr, 1, bd.n_tiles, od.H}, od.W, od.IN, precision, grid, st);
+    return tc_dispatch(one, WorkList{nullptr, 1, bd.n_tiles, od.H, bd.sp_x != nullptr}, od.W, od.IN, precision, grid,
+                       st);
 }
 
 cudaError_t launch_fused_tc_list(const WorkList &wl, int W, int IN, int precision, int grid, cudaStream_t st)
@@ -297,7 +298,7 @@ cudaError_t launch_fused_fp32(const ObjDesc &od, const BatchDesc &bd, int S, int
     one.od = od;
     one.bd = bd;
     one.tile_begin = 0;
-    return fp32_dispatch(one, WorkList{nullptr, 1, bd.n_tiles, od.H}, od.W, od.IN, S, grid, st);
+    return fp32_dispatch(one, WorkList{nullptr, 1, bd.n_tiles, od.H, bd.sp_x != nullptr}, od.W, od.IN, S, grid, st);
 }
 
 cudaError_t launch_fused_fp32_list(const WorkList &wl, int W, int IN, int S, int grid, cudaStream_t st)

@@ -13,9 +13,11 @@
 // interleaved layout (8x8 core matrices of 128 contiguous bytes) and is used
 // K-major or MN-major by the descriptors, so no transposed copies exist.  The
 // weight gradients accumulate in tensor memory for the CTA's whole life and are
-// flushed with one atomic pass at the end; dW_out (4 x W) is summed on the
-// CUDA cores.  The backward gradients are multiplied by a loss scale before the
-// 16-bit cast (FP16 dynamic range) and divided by it in FP32 on the way out.
+// flushed with one atomic pass at the end; dW_out (4 x W) too, as rows 0..3 of
+// an M = 64 product, when its columns fit in the CTA's 256 (else it is summed
+// on the CUDA cores while the tensor cores form dH of the last hidden layer).
+// The backward gradients are multiplied by a loss scale before the 16-bit cast
+// (FP16 dynamic range) and divided by it in FP32 on the way out.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -239,17 +241,29 @@ constexpr int kTcTile = 128;       // samples per tile = MMA M
 constexpr int kTcCols = 256;       // TMEM columns allocated per CTA
 constexpr int kDaCols = 64;        // columns of the dH buffer (dW MMAs use M = 64)
 
+// dW_out (4 x W, rows 0..3 of an M = 64 accumulator at dw_col(H)) is formed on
+// the tensor cores when its W columns fit after the hidden layers' dW (for the
+// launch's deepest MLP), else summed on the CUDA cores.
+template <int W, int IN>
+__host__ __device__ __forceinline__ bool tc_dw_out(int H)
+{
+    return 64 + (IN < 16 ? 16 : IN) + H * W <= kTcCols;
+}
+
 template <int W, int IN>
 struct TcLayout {
     static constexpr int INP = IN < 16 ? 16 : IN;  // encoding width padded to the MMA N/K quantum
     static constexpr int SP = kTcTile + 4;
     // byte sizes of the 16-bit matrices
     static constexpr int w0 = W * INP * 2, wh = W * W * 2, wo = 16 * W * 2;
-    static constexpr int xa = kTcTile * INP * 2, ha = kTcTile * W * 2, da = kTcTile * kDaCols * 2,
-                         doa = kTcTile * 16 * 2;
-    static __host__ __device__ size_t bytes(int H)
+    static constexpr int xa = kTcTile * INP * 2, ha = kTcTile * W * 2, da = kTcTile * kDaCols * 2;
+    // dO: 4 of 16 columns (the K of the dH product), or of 64 when the dW_out
+    // product (M = 64) reads it too
+    static __host__ __device__ int doa_cols(int H, bool split) { return split && tc_dw_out<W, IN>(H) ? kDaCols : 16; }
+    static __host__ __device__ size_t bytes(int H, bool split)
     {
-        size_t b = (size_t)w0 + (size_t)(H - 1) * wh + wo + xa + (size_t)H * ha + da + doa;
+        size_t b = (size_t)w0 + (size_t)(H - 1) * wh + wo + xa + (size_t)H * ha + da;
+        b += (size_t)kTcTile * doa_cols(H, split) * 2;
         b += sizeof(float) * (8 * SP + SP + (size_t)(kTcTile / kMinNr) * kRayStride + 8 * (size_t)(kMaxNc + 1));
         return b + 64;  // TMEM slot and mbarrier
     }
@@ -264,6 +278,7 @@ __device__ __forceinline__ uint32_t dw_col(int layer)
     constexpr int INP = TcLayout<W, IN>::INP;
     return layer == 0 ? 64u : (uint32_t)(64 + INP + (layer - 1) * W);
 }
+
 
 // 16-bit weights of one object into the interleaved buffers (their padding
 // rows and columns were cleared once at kernel start and are never written).
@@ -296,7 +311,8 @@ __device__ __forceinline__ void tc_load_object(const ObjDesc &od, unsigned char 
 // warp quadrant q holds rows 16q .. 16q+15 in its lanes 0..15).
 template <int W, int IN>
 __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDesc &bd, uint32_t lane_base,
-                                                bool have_dw, float (&dwo_acc)[8], float &loss_acc, float inv_scale)
+                                                bool have_dw, bool tc_dwo, float (&dwo_acc)[8], float &loss_acc,
+                                                float inv_scale)
 {
     constexpr int INP = TcLayout<W, IN>::INP;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -308,14 +324,16 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
         return;
     const int H = od.H;
     float *gw = od.grad + od.mlp_off;
-    {  // dW_out: slice 0 of each (output, 8-column) group holds its sums
+    if (!tc_dwo) {  // dW_out from the CUDA cores: slice 0 of each (output, 8-column) group holds its sums
         constexpr int SL = kThreads / (W / 2);
         const int pair = tid / SL;
         const int o = pair / (W / 8), i0 = (pair % (W / 8)) * 8;
         if (tid % SL == 0) {  // 16-byte reductions: the 304-way contention per address is per request
             float4 *p = reinterpret_cast<float4 *>(gw + IN * W + (H - 1) * W * W + o * W + i0);
-            red_add_f4(p, dwo_acc[0], dwo_acc[1], dwo_acc[2], dwo_acc[3]);
-            red_add_f4(p + 1, dwo_acc[4], dwo_acc[5], dwo_acc[6], dwo_acc[7]);
+            red_add_f4(p, dwo_acc[0] * inv_scale, dwo_acc[1] * inv_scale, dwo_acc[2] * inv_scale,
+                       dwo_acc[3] * inv_scale);
+            red_add_f4(p + 1, dwo_acc[4] * inv_scale, dwo_acc[5] * inv_scale, dwo_acc[6] * inv_scale,
+                       dwo_acc[7] * inv_scale);
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -323,15 +341,16 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
     }
     if (!have_dw)
         return;
-    for (int l = 0; l < H; ++l) {
+    for (int l = 0; l < H + (tc_dwo ? 1 : 0); ++l) {  // layer H: dW_out, 4 rows
         const int ncol = l == 0 ? INP : W;
         const int nin = l == 0 ? IN : W;
+        const int nrow = l == H ? 4 : W;
         float *dst = gw + (l == 0 ? 0 : IN * W + (l - 1) * W * W);
         for (int c0 = half * 8; c0 < ncol; c0 += 16) {
             float v[8];
             tmem_ld8(lane_base + dw_col<W, IN>(l) + c0, v);
             const int row = 16 * quad + lane;
-            if (lane < 16 && row < W && c0 < nin) {  // nin and c0 are multiples of 8: two aligned quads
+            if (lane < 16 && row < nrow && c0 < nin) {  // nin and c0 are multiples of 8: two aligned quads
                 float4 *p = reinterpret_cast<float4 *>(dst + row * nin + c0);
                 red_add_f4(p, v[0] * inv_scale, v[1] * inv_scale, v[2] * inv_scale, v[3] * inv_scale);
                 red_add_f4(p + 1, v[4] * inv_scale, v[5] * inv_scale, v[6] * inv_scale, v[7] * inv_scale);
@@ -366,7 +385,12 @@ __global__ void __launch_bounds__(kThreads, 2)
     unsigned char *HA = XA + L::xa;                   // H buffers of ha bytes
     unsigned char *DA = HA + hmax * L::ha;
     unsigned char *DOA = DA + L::da;
-    float *OT = reinterpret_cast<float *>(DOA + L::doa);  // [4][SP] raw outputs
+    // dW_out on the tensor cores, for every object of the launch (H <= hmax): only in
+    // split mode, where the kernel gathers nothing and the wider dO buffer does not
+    // take L1 cache away from the hash gathers
+    const bool tc_dwo = wl.split && tc_dw_out<W, IN>(hmax);
+    const int doa_cols = L::doa_cols(hmax, wl.split);
+    float *OT = reinterpret_cast<float *>(DOA + kTcTile * doa_cols * 2);  // [4][SP] raw outputs
     float *dOT = OT + 4 * SP;                         // [4][SP] dL/d(raw outputs), unscaled
     float *ts = dOT + 4 * SP;
     float *rayf = ts + SP;
@@ -382,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         reinterpret_cast<uint32_t *>(WtO)[i] = 0u;
     for (int i = tid; i < L::da / 4; i += kThreads)
         reinterpret_cast<uint32_t *>(DA)[i] = 0u;
-    for (int i = tid; i < L::doa / 4; i += kThreads)
+    for (int i = tid; i < kTcTile * doa_cols / 2; i += kThreads)
         reinterpret_cast<uint32_t *>(DOA)[i] = 0u;
     __syncthreads();
     if (tid == 0) {
@@ -430,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             ++nk;
         if (nk != k) {  // entering another object: flush the previous one, load this one
             if (k >= 0)
-                tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, dwo_acc, loss_acc, inv_scale);
+                tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, tc_dwo, dwo_acc, loss_acc, inv_scale);
             __syncthreads();
             stage_item(list[nk], cur);
             tc_load_object<W, IN, BF16>(cur.od, Wt0, WtH, WtO);
@@ -607,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             uint32_t lo = (uint32_t)Hf::bits(dOT[tid] * scale) | ((uint32_t)Hf::bits(dOT[SP + tid] * scale) << 16);
             uint32_t hi = (uint32_t)Hf::bits(dOT[2 * SP + tid] * scale) |
                           ((uint32_t)Hf::bits(dOT[3 * SP + tid] * scale) << 16);
-            *reinterpret_cast<uint2 *>(DOA + il_off(tid, 0, 16)) = make_uint2(lo, hi);
+            *reinterpret_cast<uint2 *>(DOA + il_off(tid, 0, doa_cols)) = make_uint2(lo, hi);
             if (!(Hf::finite(lo & 0xFFFFu) && Hf::finite(lo >> 16) && Hf::finite(hi & 0xFFFFu) &&
                   Hf::finite(hi >> 16)) && bd.overflow)
                 atomicExch(bd.overflow, 1);
@@ -618,12 +642,15 @@ __global__ void __launch_bounds__(kThreads, 2)
             // dH_l = dOut_{l+1} W_{l+1}: for l = H-1 from the output layer
             if (tid == 0) {
                 if (l == H - 1)
-                    mma_gemm<16>(tmem, kmajor(DOA, 16), mnmajor(WtO, W), id_dh, false);
+                    mma_gemm<16>(tmem, kmajor(DOA, doa_cols), mnmajor(WtO, W), id_dh, false);
                 else
                     mma_gemm<W>(tmem, kmajor(DA, kDaCols), mnmajor(WtH + l * L::wh, W), id_dh, false);
                 mma_commit(mbar);
+                if (l == H - 1 && tc_dwo)  // dW_out += dO^T H_{H-1}, rows 0..3 of M = 64 (a later commit covers it)
+                    mma_gemm<kTcTile>(tmem + dw_col<W, IN>(H), mnmajor(DOA, kDaCols),
+                                      mnmajor(HA + (H - 1) * L::ha, W), id_dw, !first_dw);
             }
-            if (l == H - 1) {
+            if (l == H - 1 && !tc_dwo) {
                 // dW_out[o][i0..i0+7] on the CUDA cores while the tensor cores form dH_{H-1}:
                 // each thread sums an interleaved slice of the tile's samples (conflict-free
                 // 16-byte rows of H), the slices meet by shuffles
@@ -635,7 +662,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll 4
                 for (int k = 0; k < kTcTile / SL; ++k) {
                     const int s = k * SL + slice;
-                    const float d = dOT[o * SP + s];
+                    // the same 16-bit dO (scaled) the tensor-core form multiplies
+                    const float d = Hf::value(Hf::bits(dOT[o * SP + s] * scale));
                     const uint4 hv = *reinterpret_cast<const uint4 *>(hl + il_off(s, i0, W));
                     const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
 #pragma unroll
@@ -751,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 
     if (k >= 0 && ok)
-        tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, dwo_acc, loss_acc, inv_scale);
+        tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, tc_dwo, dwo_acc, loss_acc, inv_scale);
     tc_sync();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
@@ -760,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 template <int W, int IN, bool BF16>
 cudaError_t launch_tc_t(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
-    const size_t smem = TcLayout<W, IN>::bytes(wl.items ? wl.hmax : one.od.H);
+    const size_t smem = TcLayout<W, IN>::bytes(wl.items ? wl.hmax : one.od.H, wl.split != 0);
     cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<W, IN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess)

@@ -340,7 +340,7 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
     if (bd.n_rays == 0)
         return PRENOM_OK;
     if (o.arch.precision != PRENOM_PRECISION_FP32) {
-        const size_t smem = fused_tc_smem(od.W, od.IN, od.H);
+        const size_t smem = fused_tc_smem(od.W, od.IN, od.H, split && bd.mode == kTrain);
         if (smem == 0 || smem > c->smem_optin)
             return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
         bd.rays_per_tile = 128 / bd.nr;
@@ -355,7 +355,7 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
             WorkItem one{};
             one.od = od;
             one.bd = bd;
-            const WorkList wl{nullptr, 1, bd.n_tiles, od.H};
+            const WorkList wl{nullptr, 1, bd.n_tiles, od.H, 1};
             cudaEvent_t ev;
             timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
             cudaError_t e = launch_sample_encode(one, wl, o.arch.precision,
@@ -399,7 +399,7 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
         WorkItem one{};
         one.od = od;
         one.bd = bd;
-        const WorkList wl{nullptr, 1, bd.n_tiles, od.H};
+        const WorkList wl{nullptr, 1, bd.n_tiles, od.H, 1};
         cudaEvent_t ev;
         timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
         cudaError_t e = launch_sample_encode(one, wl, PRENOM_PRECISION_FP32,
@@ -518,7 +518,8 @@ bool cand_split(const Group &, int cand, bool split_allowed)
 int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed)
 {
     int per_sm = 1;
-    if (g.precision != PRENOM_PRECISION_FP32 && 2 * (fused_tc_smem(g.W, g.IN, g.hmax) + 1024) <= 228 * 1024)
+    if (g.precision != PRENOM_PRECISION_FP32 &&
+        2 * (fused_tc_smem(g.W, g.IN, g.hmax, cand_split(g, cand, split_allowed)) + 1024) <= 228 * 1024)
         per_sm = 2;
     const int wave = c->n_sm * per_sm;
     const int tpc = split_allowed ? kTuneTpcTc[cand] : kTuneTpc[cand];
@@ -586,7 +587,7 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
         }
         g.total_tiles = tiles;
         const size_t smem = g.precision == PRENOM_PRECISION_FP32 ? fused_fp32_smem(g.W, g.IN, g.hmax, g.S)
-                                                                 : fused_tc_smem(g.W, g.IN, g.hmax);
+                                                                 : fused_tc_smem(g.W, g.IN, g.hmax, true);
         if (smem == 0 || smem > c->smem_optin)
             return fail(c, PRENOM_ERR_INVALID_ARG, "architecture group needs more shared memory than the device offers");
         p.groups.push_back(g);
@@ -638,7 +639,7 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     for (const Group &g : p.groups) {
         if (e != cudaSuccess || g.total_tiles == 0)
             continue;
-        const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax};
+        const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax, g.split ? 1 : 0};
         cudaEvent_t ev;
         if (g.split) {
             if (timed)

@@ -83,7 +83,7 @@ struct WorkItem;
 struct WorkList;
 
 // Mixed-precision fused kernel (tcgen05 MLP); precision 1 = FP16, 2 = BF16.
-size_t fused_tc_smem(int W, int IN, int H);
+size_t fused_tc_smem(int W, int IN, int H, bool split);
 cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precision, int grid, cudaStream_t st);
 cudaError_t launch_fused_tc_list(const WorkList &wl, int W, int IN, int precision, int grid, cudaStream_t st);
 cudaError_t launch_fused_tc_bf16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st);
@@ -124,6 +124,7 @@ struct WorkItem {
 struct WorkList {
     const WorkItem *items;  // device memory
     int32_t n_items, total_tiles, hmax;
+    int32_t split;  // 1: sampling, encoding and the hash scatter run in kernels of their own
 };
 
 // Dynamic shared memory (bytes) of the fused FP32 kernel for (W, IN, H, S).
