@@ -210,6 +210,17 @@ def oracle_throughput(seed: int, budget_s: float):
     return dict(value=N_RAYS * NR / step_s, rays=done, t_rays=t_rays, t_adam=t_adam, step_s=step_s)
 
 
+def oracle_adam_seconds():
+    """Seconds of one full oracle Adam pass over the full-size object's parameters."""
+    import oracle as orc
+
+    n = orc.param_count(orc.Arch(**ARCH))
+    theta, m, v, g = (np.full(n, 1e-3) for _ in range(4))  # written once, so no first-touch page faults are timed
+    t0 = time.perf_counter()
+    orc.adam(theta, m, v, g, 1, 1e-2)
+    return time.perf_counter() - t0
+
+
 _BARRIER = None
 
 
@@ -796,10 +807,21 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            r = oracle_throughput(0, float(os.environ.get("PRENOM_ORACLE_BUDGET_S", "12")))
-            cpu = {"value": r["value"], "unit": "samples/s", "cores": 1, "kind": "oracle",
-                   "sample": (f"{r['rays']} of {N_RAYS} rays fwd+bwd ({r['t_rays']:.1f} s) + one full Adam pass "
-                              f"({r['t_adam']:.2f} s), FP64, 1 host thread, extrapolated to the 4096-ray step")}
+            budget = float(os.environ.get("PRENOM_ORACLE_BUDGET_S", "12"))
+            try:  # in a spawned process of its own: no CUDA context or bench threads beside it
+                r1 = oracle_throughput_all_cores(0, budget, 1)
+                t_adam = oracle_adam_seconds()
+                cpu = {"value": N_RAYS * NR / (N_RAYS / r1["rays_per_s"] + t_adam), "unit": "samples/s",
+                       "cores": 1, "kind": "oracle",
+                       "sample": (f"{r1['rays']} rays fwd+bwd in {r1['wall']:.1f} s in one spawned host process + "
+                                  f"one full Adam pass ({t_adam:.2f} s), FP64, extrapolated to the 4096-ray step")}
+                r = {"t_adam": t_adam}
+            except Exception:
+                r = oracle_throughput(0, budget)
+                cpu = {"value": r["value"], "unit": "samples/s", "cores": 1, "kind": "oracle",
+                       "sample": (f"{r['rays']} of {N_RAYS} rays fwd+bwd ({r['t_rays']:.1f} s) + one full Adam "
+                                  f"pass ({r['t_adam']:.2f} s), FP64, 1 host thread in the bench process, "
+                                  f"extrapolated to the 4096-ray step")}
             ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
             if ncores > 1:  # the same oracle on every host core, one process per core
                 try:
