@@ -456,7 +456,7 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
             a.chunk_start[i - first + 1] = a.chunk_start[i - first] + (o.n + kAdamChunk - 1) / kAdamChunk;
         }
         const int64_t chunks = a.chunk_start[a.n_segs];
-        const int grid = (int)std::min<int64_t>(chunks, (int64_t)c->n_sm * 8);
+        const int grid = (int)std::min<int64_t>(chunks, (int64_t)c->n_sm * 16);
         if (grid == 0)
             continue;
         cudaEvent_t ev;
@@ -621,7 +621,7 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
             if (o.lss && p.scales.n < kMaxScaleObjs)
                 p.scales.s[p.scales.n++] = o.lss;
         }
-        p.adam_grid = (int)std::min<int64_t>(a.chunk_start[a.n_segs], (int64_t)c->n_sm * 8);
+        p.adam_grid = (int)std::min<int64_t>(a.chunk_start[a.n_segs], (int64_t)c->n_sm * 16);
     }
     return PRENOM_OK;
 }

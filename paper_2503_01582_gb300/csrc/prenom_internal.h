@@ -154,7 +154,7 @@ struct AdamArgs {
     int64_t chunk_start[kMaxAdamSegs + 1];  // prefix sums of per-segment chunk counts
     AdamSeg seg[kMaxAdamSegs];
 };
-constexpr int kAdamChunk = 4096;  // floats per chunk
+constexpr int kAdamChunk = 1024;  // floats per chunk (fine enough that the last wave leaves no long tail)
 cudaError_t launch_adam(const AdamArgs &a, int grid, cudaStream_t st);
 
 // Reptile meta step (§III-A): broadcast of the meta-parameters to the task
