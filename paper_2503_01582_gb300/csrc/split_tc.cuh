@@ -70,10 +70,11 @@ __global__ void __launch_bounds__(kThreads, 4)
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 pos_two_float(rf[RF_O + a], tk, rf[RF_D + a], ph[a], pl[a]);
-            uint32_t pk[kMaxLevels];
+            const int s = rr * nr + k;  // row of the tile image
+            uint32_t pk[4];  // one 16-byte chunk (4 levels) of the row, stored as soon as it is complete
 #pragma unroll
             for (int l = 0; l < kMaxLevels; ++l) {
-                pk[l] = 0u;
+                pk[l & 3] = 0u;
                 if (l < NL) {
                     const LevelDesc lv = od.lv[l];
                     Corners cs;
@@ -90,21 +91,18 @@ __global__ void __launch_bounds__(kThreads, 4)
                     }
                     if constexpr (FMT == 2) {  // consecutive lanes write consecutive samples of a feature
                         float *fimg = reinterpret_cast<float *>(img);
-                        fimg[(2 * l) * kSplitTile + rr * nr + k] = e0;
-                        fimg[(2 * l + 1) * kSplitTile + rr * nr + k] = e1;
+                        fimg[(2 * l) * kSplitTile + s] = e0;
+                        fimg[(2 * l + 1) * kSplitTile + s] = e1;
                     } else {
-                        pk[l] = (uint32_t)Hf::bits(e0) | ((uint32_t)Hf::bits(e1) << 16);
+                        pk[l & 3] = (uint32_t)Hf::bits(e0) | ((uint32_t)Hf::bits(e1) << 16);
                     }
                 }
-            }
-            if constexpr (FMT != 2) {
                 // row s of the tile image: INP / 8 chunks of 8 columns (16 bytes each)
-                const int s = rr * nr + k;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < INP / 8)
-                        *reinterpret_cast<uint4 *>(img + il_off(s, 8 * q, INP)) =
-                            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                if constexpr (FMT != 2) {
+                    if ((l & 3) == 3 && l / 4 < INP / 8)
+                        *reinterpret_cast<uint4 *>(img + il_off(s, 8 * (l / 4), INP)) =
+                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
             }
         }
         __syncwarp();  // rf and ts are rewritten for the next ray
