@@ -11,8 +11,9 @@
 //   2. hash-grid encoding, two (or four) threads per sample, levels split
 //      between them, with error-free position arithmetic;
 //   3. MLP forward as register-tiled FFMA GEMMs over the tile;
-//   4. compositing (Eq. 7), loss (Eq. 8-9) and its adjoint, one warp per ray
-//      with shuffle scans (prefix for transmittance, suffix for the adjoint);
+//   4. compositing (Eq. 7), loss (Eq. 8-9) and its adjoint, one warp per 32
+//      samples of a ray, one sample per lane, with shuffle scans (prefix for
+//      transmittance, suffix for the adjoint) joined across a ray's warps;
 //   5. MLP backward: dW accumulated in shared memory across all tiles of the
 //      CTA (flushed once with atomics at the end), dX by GEMM;
 //   6. hash-grid scatter of dX: runs of lanes in one cell summed by a
@@ -439,132 +440,22 @@ __device__ __forceinline__ float ray_loss(const ObjDesc &od, const BatchDesc &bd
     return loss * bd.inv_r;
 }
 
-// One warp per ray; lane holds samples lane*Q .. lane*Q+Q-1 (Q = ceil(nr/32)).
-// Forward: tau_k = sigma_k delta_k, T_k = exp(-sum_{j<k} tau_j), w_k = T_k (1 - exp(-tau_k)).
-// Adjoint with v_k = gC.c_k + gD t_k + gA:
-//   dL/dsigma_k = delta_k (T_{k+1} v_k - sum_{j>k} w_j v_j).
-// Writes dL/do (o = raw MLP outputs) into dOT; returns the ray's loss (train mode).
-// Q = QS samples per lane as a compile-time count, or QS = 0 for any count up to
-// kMaxNr (the tile routine below uses QS = 1 and spreads longer rays over warps).
-template <int QS>
-__device__ __forceinline__ float composite_warp_q(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
-                                                  const float *rf, const float *ts, const float *OT, float *dOT,
-                                                  int SP, int lane)
-{
-    constexpr int QM = QS > 0 ? QS : kMaxNr / 32;
-    const int nr = bd.nr;
-    const int Q = QS > 0 ? QS : (nr + 31) >> 5;
-    const float tf = rf[RF_TF];
-    float sig[QM], col[QM][3], tk[QM], dl[QM], tau[QM], o0[QM], pre[QM];
-    float run = 0.f;
-#pragma unroll
-    for (int q = 0; q < QM; ++q) {
-        sig[q] = 0.f;
-        tau[q] = 0.f;
-        dl[q] = 0.f;
-        tk[q] = 0.f;
-        o0[q] = 0.f;
-        col[q][0] = col[q][1] = col[q][2] = 0.f;
-        const int k = lane * Q + q;
-        if (q < Q && k < nr) {
-            const int s = r * nr + k;
-            o0[q] = OT[s];
-            sig[q] = expf(fminf(o0[q], 15.f));
-            if (bd.out_sigma)
-                bd.out_sigma[(size_t)gr * nr + k] = sig[q];
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                col[q][c] = 1.f / (1.f + expf(-OT[(1 + c) * SP + s]));
-            tk[q] = ts[s];
-            const float tnext = (k + 1 < nr) ? ts[s + 1] : tf;
-            dl[q] = tnext - tk[q];
-            tau[q] = sig[q] * dl[q];
-        }
-        pre[q] = run;  // sum of tau over this lane's earlier samples
-        run += tau[q];
-    }
-    const float incl = warp_incl_scan(run, lane);
-    float base = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0)
-        base = 0.f;
-    float w[QM], T[QM];
-    float cr0 = 0.f, cr1 = 0.f, cr2 = 0.f, dsum = 0.f, asum = 0.f, ssum = 0.f;
-#pragma unroll
-    for (int q = 0; q < QM; ++q) {
-        T[q] = expf(-(base + pre[q]));
-        w[q] = T[q] * (-expm1f(-tau[q]));
-        cr0 = fmaf(w[q], col[q][0], cr0);
-        cr1 = fmaf(w[q], col[q][1], cr1);
-        cr2 = fmaf(w[q], col[q][2], cr2);
-        dsum = fmaf(w[q], tk[q], dsum);
-        asum += w[q];
-        ssum += sig[q];
-    }
-    const float Cr[3] = {warp_sum(cr0), warp_sum(cr1), warp_sum(cr2)};
-    const float D = warp_sum(dsum), A = warp_sum(asum);
-    if (bd.mode == kRender) {
-        if (lane == 0) {
-            if (bd.out_rgb) {
-                bd.out_rgb[(size_t)gr * 3 + 0] = Cr[0];
-                bd.out_rgb[(size_t)gr * 3 + 1] = Cr[1];
-                bd.out_rgb[(size_t)gr * 3 + 2] = Cr[2];
-            }
-            if (bd.out_depth)
-                bd.out_depth[gr] = D;
-            if (bd.out_acc)
-                bd.out_acc[gr] = A;
-        }
-        return 0.f;
-    }
-    float gC[3], gD, gA;
-    bool background;
-    const float loss = ray_loss(od, bd, gr, rf, Cr, D, A, [&]() { return warp_sum(ssum); }, gC, gD, gA, background);
-    // adjoint: suffix sums of w v
-    float wv[QM], v[QM];
-    float lsum = 0.f;
-#pragma unroll
-    for (int q = 0; q < QM; ++q) {
-        v[q] = fmaf(gC[0], col[q][0], fmaf(gC[1], col[q][1], fmaf(gC[2], col[q][2], fmaf(gD, tk[q], gA))));
-        wv[q] = w[q] * v[q];
-        lsum += wv[q];
-    }
-    const float sincl = warp_incl_suffix(lsum, lane);
-    float after = __shfl_down_sync(kFull, sincl, 1);  // sum over later lanes
-    if (lane == 31)
-        after = 0.f;
-    const float sig_reg = background ? od.lambda_sigma * bd.inv_r : 0.f;
-#pragma unroll
-    for (int q = QM - 1; q >= 0; --q) {
-        const int k = lane * Q + q;
-        if (q < Q && k < nr) {
-            const int s = r * nr + k;
-            const float Tn = expf(-(base + pre[q] + tau[q]));
-            const float dsig = fmaf(dl[q], fmaf(Tn, v[q], -after), sig_reg);
-            dOT[s] = (o0[q] < 15.f) ? dsig * sig[q] : 0.f;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float dc = w[q] * gC[c];
-                dOT[(1 + c) * SP + s] = dc * col[q][c] * (1.f - col[q][c]);
-            }
-        }
-        if (q < Q)
-            after += wv[q];
-    }
-    return loss;
-}
-
-
 __device__ __forceinline__ void group_bar(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// The same compositing, loss and adjoint with a ray spread over G = ceil(nr / 32)
+// Compositing (Eq. 7), loss and adjoint of one ray spread over G = ceil(nr / 32)
 // warps, one sample per lane: warp g of the group holds samples 32 g .. 32 g + 31.
-// The warps meet through named barrier `bar` (G x 32 threads) and 8 floats per
-// warp of `xs` (shared memory): the warp's sum of tau (slot 0), its partial sums
-// of w c, w t, w and sigma (slots 1-6) and its sum of w v (slot 7), each combined
-// in warp order.  Every warp of the group returns the ray's loss.
+// Forward: tau_k = sigma_k delta_k, T_k = exp(-sum_{j<k} tau_j), w_k = T_k (1 - exp(-tau_k)).
+// Adjoint with v_k = gC.c_k + gD t_k + gA:
+//   dL/dsigma_k = delta_k (T_{k+1} v_k - sum_{j>k} w_j v_j).
+// Writes dL/do (o = raw MLP outputs) into dOT; returns the ray's loss (train
+// mode) on every warp of the group.  For G > 1 the warps meet through named
+// barrier `bar` (G x 32 threads) and 8 floats per warp of `xs` (shared memory):
+// the warp's sum of tau (slot 0), its partial sums of w c, w t, w and sigma
+// (slots 1-6) and its sum of w v (slot 7), each combined in warp order.  For
+// G = 1 nothing leaves the warp's registers.
 template <int G>
 __device__ __forceinline__ float composite_group(const ObjDesc &od, const BatchDesc &bd, int r, int gr,
                                                  const float *rf, const float *ts, const float *OT, float *dOT,
@@ -593,9 +484,11 @@ __device__ __forceinline__ float composite_group(const ObjDesc &od, const BatchD
     float excl = __shfl_up_sync(kFull, incl, 1);  // this warp's samples before this one
     if (lane == 0)
         excl = 0.f;
-    if (lane == 31)
-        xs[8 * wig] = incl;
-    group_bar(bar, 32 * G);
+    if constexpr (G > 1) {
+        if (lane == 31)
+            xs[8 * wig] = incl;
+        group_bar(bar, 32 * G);
+    }
     float pref = 0.f;  // earlier warps' samples
 #pragma unroll
     for (int g = 0; g < G - 1; ++g)
@@ -607,17 +500,22 @@ __device__ __forceinline__ float composite_group(const ObjDesc &od, const BatchD
 #pragma unroll
     for (int i = 0; i < 6; ++i)
         part[i] = warp_sum(part[i]);
-    if (lane == 0)
+    float tot[6] = {part[0], part[1], part[2], part[3], part[4], part[5]};
+    if constexpr (G > 1) {
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                xs[8 * wig + 1 + i] = part[i];
+        group_bar(bar, 32 * G);
 #pragma unroll
         for (int i = 0; i < 6; ++i)
-            xs[8 * wig + 1 + i] = part[i];
-    group_bar(bar, 32 * G);
-    float tot[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            tot[i] = 0.f;
 #pragma unroll
-    for (int g = 0; g < G; ++g)
+        for (int g = 0; g < G; ++g)
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
-            tot[i] += xs[8 * g + 1 + i];
+            for (int i = 0; i < 6; ++i)
+                tot[i] += xs[8 * g + 1 + i];
+    }
     const float Cr[3] = {tot[0], tot[1], tot[2]};
     const float D = tot[3], A = tot[4];
     if (bd.mode == kRender) {
@@ -641,9 +539,11 @@ __device__ __forceinline__ float composite_group(const ObjDesc &od, const BatchD
     const float v = fmaf(gC[0], col[0], fmaf(gC[1], col[1], fmaf(gC[2], col[2], fmaf(gD, tk, gA))));
     const float wv = w * v;
     const float sincl = warp_incl_suffix(wv, lane);
-    if (lane == 0)
-        xs[8 * wig + 7] = sincl;
-    group_bar(bar, 32 * G);
+    if constexpr (G > 1) {
+        if (lane == 0)
+            xs[8 * wig + 7] = sincl;
+        group_bar(bar, 32 * G);
+    }
     float after = __shfl_down_sync(kFull, sincl, 1);  // later lanes of this warp
     if (lane == 31)
         after = 0.f;
@@ -679,7 +579,8 @@ __device__ __forceinline__ float composite_tile(const ObjDesc &od, const BatchDe
     float lsum = 0.f;
     if (G == 1) {
         for (int r = warp; r < nrt; r += kThreads / 32) {
-            const float lr = composite_warp_q<1>(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane);
+            const float lr = composite_group<1>(od, bd, r, ray0 + r, rayf + r * kRayStride, ts, OT, dOT, SP, lane, 0,
+                                                nullptr, 0);
             if (lane == 0)
                 lsum += lr;
         }
