@@ -94,7 +94,7 @@ typedef struct prenom_ctx prenom_ctx; /* opaque; owns all device state */
 
 /* Architecture alpha of one object NeRF (§III-A "Architecture Optimization"
  * lists hash-grid and MLP hyper-parameters and lambda_d, lambda_sigma).
- * Limits of this build: F = 2; L in {4, 8, 16}; width in {16, 32, 64};
+ * Supported values: F = 2; L in {4, 8, 16}; width in {16, 32, 64};
  * 1 <= hidden <= 3; 8 <= log2T <= 24; 2 <= n_min <= n_max <= 2^20;
  * precision = PRENOM_PRECISION_FP32, _FP16 or _BF16. */
 typedef struct {
