@@ -205,8 +205,16 @@ def cdf_invert(cdf, u, tn: float, tf: float):
     return bins, t
 
 
+def _need(x, size: int, name: str):
+    """The C routines read exactly `size` values of an optional array: a shorter
+    (or longer) one is a caller's mistake, reported here instead of read past."""
+    if x is not None and x.size != size:
+        raise ValueError(f"{name} has {x.size} values, {size} expected")
+
+
 def sample_ray(grid, o, d, nc: int, nr: int, eps: float, u):
     g, o, d, u = _d(grid), _d(o), _d(d), _d(u)
+    _need(u, nr, "u")
     out = dict(probe_sigma=np.zeros(nc), rho_term=np.zeros(nc), cdf=np.zeros(nc + 1),
                bins=np.zeros(nr, dtype=np.int32), t=np.zeros(nr))
     tn, tf = C.c_double(), C.c_double()
@@ -294,6 +302,9 @@ def batch(a: Arch, theta, grid, rays: dict, nc: int, nr: int, eps: float = 1e-4,
     t_in = _d(t_in)
     c_rand = _d(c_rand)
     upstream = _d(upstream)
+    for x, size, name in ((u, n * nr, "u"), (t_in, n * nr, "t_in"), (c_rand, n * 3, "c_rand"),
+                          (upstream, n * 5, "upstream"), (theta, param_count(a), "theta")):
+        _need(x, size, name)
     out = dict(rgb=np.zeros((n, 3)), depth=np.zeros(n), acc=np.zeros(n))
     if want_samples:
         out.update(bins=np.zeros((n, nr), dtype=np.int32), t=np.zeros((n, nr)), sigma=np.zeros((n, nr)))

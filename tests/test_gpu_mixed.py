@@ -199,6 +199,35 @@ def test_mixed_full_size_sampled(pkg):
 
 
 @pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("nr", [96, 128])
+def test_mixed_long_rays_against_oracle(pkg, precision, nr):
+    """Rays of 96 and 128 samples (compositing over 3 and 4 warps, one ray per
+    tile) in the tensor-core kernel, split form first (the autotuner's first
+    call) and the fused form: the mixed-precision bounds against the oracle on
+    identical samples."""
+    import torch
+
+    bnd = BOUNDS[precision]
+    a, theta, grid, rays, u, cr = case(CFG1, 41, nr, 32, seed=73, hash_range=0.5)
+    t_in = oracle_t(grid, rays, u, 32, nr)
+    want = orc.batch(a, theta, grid, rays, 32, nr, t_in=t_in, c_rand=cr, want_grad=True)
+    for flags in (pkg.PRENOM_FLAG_SPLIT, pkg.PRENOM_FLAG_FUSED):
+        ctx = pkg.Context(seed=3)
+        obj = ctx.create_object(_arch(pkg, CFG1, precision), theta)
+        ctx.set_prior_grid(obj, grid)
+        b = _dev(rays, obj, cr=cr, t_in=t_in)
+        out = ctx.render(b, pkg.make_opts(nc=32, nr=nr))
+        assert float(np.abs(out["rgb"].cpu().numpy() - want["rgb"]).max()) <= bnd["rgb"]
+        assert rel(out["depth"].cpu().numpy(), want["depth"]) <= bnd["rel"]
+        loss = torch.zeros(1, device="cuda")
+        ctx.train_step([b], pkg.make_opts(nc=32, nr=nr, flags=flags | pkg.PRENOM_FLAG_NO_ADAM), loss)
+        assert abs(loss.item() - want["loss"]) <= bnd["rel"] * abs(want["loss"]), flags
+        cos, l2 = _grad_metrics(ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy(), want["grad"])
+        assert cos >= bnd["cos"] and l2 <= bnd["l2"], (flags, cos, l2)
+        ctx.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("nr,n_rays", [(64, 301), (48, 257), (32, 200)])
 def test_split_form_matches_fused_kernel(pkg, precision, nr, n_rays):
     """The split form (sampling + encoding, the tensor-core MLP, the hash scatter

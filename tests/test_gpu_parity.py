@@ -172,6 +172,30 @@ def test_loss_and_gradients_on_identical_samples(pkg, arch):
     ctx.close()
 
 
+@pytest.mark.parametrize("nr", [80, 96, 128])
+def test_long_rays_over_several_warps(pkg, nr):
+    """Rays of more than 64 samples: the compositing spreads each over
+    ceil(nr/32) = 3 or 4 warps (the last one partly filled for nr = 80), which
+    meet through named barriers; a tile holds one such ray.  Forward, loss and
+    gradients on identical samples against the oracle, both forms."""
+    import torch
+
+    a, theta, grid, rays, u, cr = case(CFG1, 37, nr, 32, seed=61, hash_range=0.5)
+    t_in = oracle_t(grid, rays, u, 32, nr)
+    want = orc.batch(a, theta, grid, rays, 32, nr, t_in=t_in, c_rand=cr, want_grad=True)
+    for flags in (0, pkg.PRENOM_FLAG_FUSED):
+        ctx, obj = _setup(pkg, CFG1, theta, grid)
+        b = _dev(rays, obj, cr=cr, t_in=t_in)
+        out = ctx.render(b, pkg.make_opts(nc=32, nr=nr))
+        for k in ("rgb", "depth", "acc"):
+            assert rel(out[k].cpu().numpy(), want[k]) <= FWD_TOL, (k, flags)
+        loss = torch.zeros(1, device="cuda")
+        ctx.train_step([b], pkg.make_opts(nc=32, nr=nr, flags=flags | pkg.PRENOM_FLAG_NO_ADAM), loss)
+        assert abs(loss.item() - want["loss"]) <= FWD_TOL * abs(want["loss"]), flags
+        _check_grads(a, ctx.get_state(obj, pkg.PRENOM_STATE_GRAD).cpu().numpy(), want["grad"])
+        ctx.close()
+
+
 @pytest.mark.parametrize("arch", ARCHS[:2])
 def test_end_to_end_from_uniforms(pkg, arch):
     """Sampler included: uniforms kept out of bins lighter than 2 % of the ray's mass."""
