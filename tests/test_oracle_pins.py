@@ -372,6 +372,64 @@ def test_batch_one_ray_two_samples_by_hand(orc):
     assert abs(out["loss"] - want) < 1e-15
 
 
+def _constant_field_theta(orc, a, sigma):
+    """Every hash entry 1 (so every encoding feature is 1 by the partition of
+    unity), W_1 = 1/IN (every hidden unit relu(1) = 1), W_out row 0 =
+    ln(sigma)/W and rows 1..3 zero: density sigma and colour 1/2 everywhere."""
+    nh = orc.n_hash_params(a)
+    theta = np.zeros(orc.param_count(a))
+    theta[:nh] = 1.0
+    w1 = orc.mlp_offset(a, 0)
+    theta[w1:w1 + a.width * a.n_in] = 1.0 / a.n_in
+    wo = orc.mlp_offset(a, a.hidden)
+    theta[wo:wo + a.width] = np.log(sigma) / a.width
+    return theta
+
+
+def _two_sample_weights(sigma, t0, t1, tf):
+    w0 = 1 - np.exp(-sigma * (t1 - t0))
+    w1 = np.exp(-sigma * (t1 - t0)) * (1 - np.exp(-sigma * (tf - t1)))
+    return w0, w1
+
+
+def test_batch_three_rays_with_background_and_density_penalty_by_hand(orc):
+    """Eq. 8-9 over a batch of three rays, written out by hand: two object rays
+    (L_c + lambda_d L_d) and one background ray (the C_rand composite and
+    lambda_sigma times the sum of its samples' densities), all divided by the
+    ray count R = 3.  Fails if L_sigma is charged to object rays, if its 1/R is
+    dropped, or if the rays are summed instead of averaged."""
+    lam_d, lam_s, sig = 0.1, 0.05, 2.0
+    a = orc.Arch(L=2, F=2, log2T=10, n_min=2, n_max=4, width=8, hidden=1, lambda_d=lam_d, lambda_sigma=lam_s)
+    theta = _constant_field_theta(orc, a, sig)
+    # three rays along +x, y and z inside the cube: the box interval is [1, 2]
+    rays = dict(o=[[-1.0, 0.5, 0.5], [-1.0, 0.3, 0.6], [-1.0, 0.7, 0.2]], d=[[1.0, 0.0, 0.0]] * 3,
+                rgb=[[0.1, 0.2, 0.3], [0.6, 0.5, 0.4], [0.0, 0.0, 0.0]], depth=[1.4, 1.25, 0.0], is_obj=[1, 1, 0])
+    t_in = np.array([[1.2, 1.7], [1.1, 1.5], [1.3, 1.8]])
+    c_rand = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.2, 0.4, 0.6]])
+    out = orc.batch(a, theta, np.zeros((2, 2, 2)), rays, 4, 2, t_in=t_in, c_rand=c_rand)
+    total = 0.0
+    for r in range(3):
+        w0, w1 = _two_sample_weights(sig, t_in[r, 0], t_in[r, 1], 2.0)
+        A = w0 + w1
+        D = w0 * t_in[r, 0] + w1 * t_in[r, 1]
+        C = np.full(3, 0.5 * A)
+        assert abs(out["acc"][r] - A) < 1e-14 and abs(out["depth"][r] - D) < 1e-14
+        np.testing.assert_allclose(out["rgb"][r], C, rtol=1e-14)
+        if rays["is_obj"][r]:
+            total += np.sum((C - np.array(rays["rgb"][r])) ** 2) + lam_d * abs(D - rays["depth"][r])
+        else:
+            # C + (1 - A) C_rand - C_rand = C - A C_rand; L_sigma = sum over the two samples of sigma
+            total += np.sum((C - A * c_rand[r]) ** 2) + lam_s * (sig + sig)
+    assert abs(out["loss"] - total / 3.0) < 1e-13
+    # the same batch without its background ray loses exactly that ray's share
+    two = {k: v[:2] for k, v in rays.items()}
+    out2 = orc.batch(a, theta, np.zeros((2, 2, 2)), two, 4, 2, t_in=t_in[:2], c_rand=c_rand[:2])
+    w0, w1 = _two_sample_weights(sig, 1.3, 1.8, 2.0)
+    A = w0 + w1
+    bg = np.sum((0.5 * A - A * c_rand[2]) ** 2) + 2 * lam_s * sig
+    assert abs(3.0 * out["loss"] - 2.0 * out2["loss"] - bg) < 1e-13
+
+
 # ------------------------------------------------------------------ gradients
 def _fd_setup(orc, lambda_sigma=0.0):
     from synth import scene_sphere_box, cameras_on_sphere, make_ray_pool, prior_grid, sample_batch
