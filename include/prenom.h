@@ -381,33 +381,46 @@ PRENOM_API int prenom_kernel_time(prenom_ctx *ctx, int32_t kernel, double *total
  * host framework whose caching allocator owns the device pool, or a real-time
  * thread that cannot afford cudaMalloc's implicit device synchronisation.
  *
- * prenom_train_step_noalloc() runs the same training step as
- * prenom_train_step() for one object whose state the caller owns, and calls
- * no cudaMalloc, cudaFree or other allocating routine.  Its only extra device
- * memory is a gradient accumulator of PRENOM_NOALLOC_MAX_PARAMS floats
- * (16 MiB) compiled into the library as a static device array, which every
- * GPU that loads the library holds until the process exits.
- *   arch       architecture (same rules as prenom_create_object); objects with
- *              more than PRENOM_NOALLOC_MAX_PARAMS parameters are rejected
- *              with PRENOM_ERR_INVALID_ARG
- *   theta      device, param_count floats, updated in place (layout above),
- *              16-byte aligned (else PRENOM_ERR_INVALID_ARG)
+ * prenom_train_step_noalloc() runs the training step of prenom_train_step()
+ * (one batch, sampling through Adam) for one FP32 object whose state the
+ * caller owns, in the fused FP32 kernel, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Its only extra device memory is a gradient
+ * accumulator of PRENOM_NOALLOC_MAX_PARAMS floats (16 MiB) compiled into the
+ * library as a static device array, which every GPU that loads the library
+ * holds until the process exits.
+ *   arch       architecture (same rules as prenom_create_object) with
+ *              precision PRENOM_PRECISION_FP32 only (mixed-precision objects
+ *              are rejected); objects with more than PRENOM_NOALLOC_MAX_PARAMS
+ *              parameters are rejected; both with PRENOM_ERR_INVALID_ARG
+ *   theta      device, param_count floats, updated in place (layout above)
  *   adam_m, adam_v  device, param_count floats each, updated in place (zero
  *              before the first step)
+ *              theta, adam_m and adam_v must each be 16-byte aligned, else
+ *              PRENOM_ERR_INVALID_ARG (checked on the host, nothing launched)
  *   step       Adam steps already taken (this call performs step + 1)
- *   grid, res  prior density grid as in prenom_set_prior_grid (device; may be
- *              NULL when the batch gives t_in)
+ *   grid, res  prior density grid as in prenom_set_prior_grid (device,
+ *              2 <= res <= 1024; may be NULL when the batch gives t_in)
  *   batch      rays as for prenom_train_step (batch->obj only keys the Philox
  *              draws when uniforms or c_rand are NULL)
+ *   opts       as for prenom_train_step; flags may hold only PRENOM_FLAG_FUSED
+ *              and PRENOM_FLAG_NO_GRAPH (the call is always one fused launch
+ *              and one Adam launch, never a graph); PRENOM_FLAG_NO_ADAM,
+ *              PRENOM_FLAG_CHECK_FINITE and PRENOM_FLAG_SPLIT are refused with
+ *              PRENOM_ERR_INVALID_ARG, since the gradient lives in the shared
+ *              array only for the duration of one call
  *   loss_dev   device float receiving the batch's loss, or NULL
  *   cuda_stream, seed  stream of all work; Philox seed
  * Errors are reported by the return code; the message is available from
  * prenom_last_error(NULL).
  * The first call on each device looks up the array's device address (set-up
- * done once per device, with that device current): make that first call
- * before any stream capture.  Every call on a device shares the array and
- * clears the part it uses before use, so calls whose work overlaps on the GPU
- * (for example on two streams at once) race and must be avoided. */
+ * done once per device, with that device current); under CUDA's lazy module
+ * loading that lookup is also what loads the library module holding the
+ * array, so the first call may allocate the array and synchronise the device
+ * inside the driver: make that first call during set-up, before any stream
+ * capture and outside any section that must not allocate.  Every call on a
+ * device shares the array and clears the part it uses before use, so calls
+ * whose work overlaps on the GPU (for example on two streams at once) race
+ * and must be avoided. */
 #define PRENOM_NOALLOC_MAX_PARAMS (1 << 22)
 
 PRENOM_API int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, float *adam_m, float *adam_v,

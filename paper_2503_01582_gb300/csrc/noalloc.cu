@@ -17,6 +17,7 @@
 namespace prenom {
 int describe_caller_field(const prenom_arch *arch, const float *theta, float *grad, const float *grid, int32_t R,
                           ObjDesc *od, int64_t *n_params);
+int check_caller_opts(const prenom_train_opts *op);
 int set_context_free_error(int code, const char *msg);
 }  // namespace prenom
 
@@ -52,22 +53,30 @@ extern "C" int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (!theta || !adam_m || !adam_v || !batch || !opts)
         return err(PRENOM_ERR_INVALID_ARG, "noalloc step: theta, adam_m, adam_v, batch and opts are required");
-    if (reinterpret_cast<uintptr_t>(theta) % 16 != 0)
-        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: theta is not 16-byte aligned");
+    // the Adam kernel reads and writes theta, m and v four floats at a time
+    if (reinterpret_cast<uintptr_t>(theta) % 16 != 0 || reinterpret_cast<uintptr_t>(adam_m) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(adam_v) % 16 != 0)
+        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: theta, adam_m and adam_v must be 16-byte aligned");
     if (step < 0)
         return err(PRENOM_ERR_INVALID_ARG, "noalloc step: step %lld < 0", step);
-    if (opts->nr < kMinNr || opts->nr > kMaxNr || opts->nc < 1 || opts->nc > kMaxNc)
-        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: nr = %lld or nc = %lld out of range", opts->nr, opts->nc);
-    if (!(opts->beta1 >= 0.f && opts->beta1 < 1.f) || !(opts->beta2 >= 0.f && opts->beta2 < 1.f) ||
-        !(opts->eps >= 0.f) || !(opts->escape_eps >= 0.f))
-        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: Adam constants or escape_eps out of range");
+    int rc = check_caller_opts(opts);
+    if (rc)
+        return rc;
+    // the gradient lives in the shared array only for the call, so it cannot be
+    // accumulated over calls (NO_ADAM) and no per-call finiteness check exists
+    if (opts->flags & ~(uint32_t)(PRENOM_FLAG_FUSED | PRENOM_FLAG_NO_GRAPH))
+        return err(PRENOM_ERR_INVALID_ARG,
+                   "noalloc step: flags 0x%llx not supported (only PRENOM_FLAG_FUSED and PRENOM_FLAG_NO_GRAPH)",
+                   (long long)opts->flags);
     const prenom_ray_batch &b = *batch;
     if (b.n_rays < 0)
         return err(PRENOM_ERR_INVALID_ARG, "noalloc step: n_rays = %lld < 0", b.n_rays);
     if (b.n_rays > 0 && (!b.o || !b.d || !b.rgb || !b.depth || !b.is_obj))
         return err(PRENOM_ERR_INVALID_ARG, "noalloc step: o, d, rgb, depth and is_obj are required");
-    if (b.n_rays > 0 && !b.t_in && (!grid || res < 2))
-        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: a prior grid (res >= 2) is required without t_in");
+    if (b.n_rays > 0 && !b.t_in && !grid)
+        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: a prior grid is required without t_in");
+    if (grid && (res < 2 || res > 1024))
+        return err(PRENOM_ERR_INVALID_ARG, "noalloc step: res = %lld, must be 2..1024", res);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -87,7 +96,7 @@ extern "C" int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, 
 
     ObjDesc od;
     int64_t n = 0;
-    int rc = describe_caller_field(arch, theta, grad, grid, res, &od, &n);
+    rc = describe_caller_field(arch, theta, grad, grid, res, &od, &n);
     if (rc)
         return rc;
     if (arch->precision != PRENOM_PRECISION_FP32)

@@ -883,6 +883,13 @@ int describe_caller_field(const prenom_arch *arch, const float *theta, float *gr
     return PRENOM_OK;
 }
 
+// The step options checked as prenom_train_step checks them (Adam constants
+// included); failures set the context-free last error.
+int check_caller_opts(const prenom_train_opts *op)
+{
+    return check_opts(nullptr, op, true);
+}
+
 int set_context_free_error(int code, const char *msg)
 {
     return fail(nullptr, code, "%s", msg);

@@ -65,3 +65,35 @@ def test_arch_param_count_matches_oracle_layout(orc):
     with pytest.raises(pkg.PrenomError) as e:
         pkg.arch_param_count(pkg.make_arch(width=48))
     assert e.value.code == -1
+
+
+def test_noalloc_step_refuses_bad_arguments_on_the_host():
+    """The allocation-free step checks its arguments before any CUDA call, so
+    these refusals run without a GPU (the pointers are never dereferenced):
+    moment buffers off a 16-byte boundary (its Adam pass moves four floats at
+    a time), flags it cannot honour, out-of-range Adam constants and grids."""
+    import pytest
+
+    import paper_2503_01582_gb300 as pkg
+    from paper_2503_01582_gb300 import _abi, build
+
+    build.build()
+    arch = pkg.make_arch()
+    batch = _abi.prenom_ray_batch()
+    ok = pkg.make_opts()
+
+    def refused(theta, m, v, opts=ok, grid=0, res=0, what=""):
+        with pytest.raises(_abi.PrenomError) as e:
+            _abi.prenom_train_step_noalloc(arch, theta, m, v, 0, grid, res, batch, opts)
+        assert e.value.code == _abi.PRENOM_ERR_INVALID_ARG
+        assert what in _abi.prenom_last_error(None)
+
+    base = 1 << 20  # an aligned fake address
+    refused(base + 4, base, base, what="16-byte aligned")
+    refused(base, base + 4, base, what="16-byte aligned")
+    refused(base, base, base + 8, what="16-byte aligned")
+    for flag in (pkg.PRENOM_FLAG_NO_ADAM, pkg.PRENOM_FLAG_CHECK_FINITE, pkg.PRENOM_FLAG_SPLIT):
+        refused(base, base, base, opts=pkg.make_opts(flags=flag), what="not supported")
+    refused(base, base, base, opts=pkg.make_opts(lr=float("nan")), what="Adam constants")
+    refused(base, base, base, opts=pkg.make_opts(escape_eps=float("inf")), what="escape_eps")
+    refused(base, base, base, grid=base, res=2048, what="res")

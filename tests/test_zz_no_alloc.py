@@ -7,7 +7,8 @@ thread that cannot take cudaMalloc's implicit synchronisation).  It keeps its
 gradient accumulator in a fixed array inside the library, so this test calls
 it twice in a row through the C ABI -- the second call must not see the
 first call's gradients -- and compares loss, Adam moments and parameters with
-prenom_train_step() on an identical object after each call.
+prenom_train_step() on an identical object after each call.  Around the
+second call the device's free memory and torch's reserved pool must not move.
 """
 
 import numpy as np
@@ -70,9 +71,15 @@ def test_noalloc_step_matches_train_step_on_two_calls():
         ref.close()
 
         ctx.train_step([b], opts, loss_a)
-        _abi.prenom_train_step_noalloc(arch, th.data_ptr(), m.data_ptr(), v.data_ptr(), call, g_dev.data_ptr(),
-                                       grid.shape[0], ray_batch(b), opts, loss_b.data_ptr(), stream.cuda_stream, 5)
+        rb = ray_batch(b)
         torch.cuda.synchronize()
+        free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+        _abi.prenom_train_step_noalloc(arch, th.data_ptr(), m.data_ptr(), v.data_ptr(), call, g_dev.data_ptr(),
+                                       grid.shape[0], rb, opts, loss_b.data_ptr(), stream.cuda_stream, 5)
+        torch.cuda.synchronize()
+        if call == 1:  # past the first call's one-time set-up: no device memory is taken
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_reserved() == reserved0
 
         assert abs(loss_b.item() - loss_a.item()) <= FWD_TOL * abs(loss_a.item())
         ma = ctx.get_state(obj, pkg.PRENOM_STATE_ADAM_M).cpu().numpy()
