@@ -1,11 +1,17 @@
 """Throughput of the PRENOM object-NeRF training step (fwd + bwd + Adam) on GB300.
 
-Default workload: one object at full size -- hash grid L=16, F=2, T=2^19,
-resolutions 16..2048, MLP 32-64-64-4, 4096 rays x 64 samples per step (Nc=64)
-drawn by the prior sampler over a 64^3 prior grid of a random CSG shape.
-One step = sampling, encoding, MLP, compositing, loss, backward and Adam for
-every parameter.  Under torchrun each rank trains its own object (weak scaling,
-no collective: objects are independent).
+Headline workload: 32 heterogeneous objects trained in ONE batched step -- the
+category table's architectures (hash grid L=16, F=2, T = 2^14..2^19, res
+16..2048; MLP width 16/32/64, 1-3 hidden layers), 256..8192 rays per object
+(a projected-area share) x 48 samples drawn by the prior sampler (N_c = 48)
+over each object's 64^3 prior grid of a random CSG shape, FP16 tensor-core MLP
+with FP32 accumulation and master weights.  One step = sampling, encoding,
+MLP, compositing, loss, backward and Adam for every parameter of every object.
+Beside it: the same 32 objects trained one plain FP32 step at a time (the
+metric's "plain FP32" side), and the equal-error check of the pair: both
+trained for a fixed step budget over 3 seeds, held-out colour MSE and depth L1.
+Under torchrun each rank trains its own copy of the workload (weak scaling, no
+collective: objects are independent).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on the same workload instead (bounded ray sample per step, extrapolated).
@@ -28,20 +34,33 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "NeRF training samples/s (fwd+bwd+Adam), batched FP16 vs plain FP32, at equal error"
-ARCH = dict(L=16, F=2, log2T=19, n_min=16, n_max=2048, width=64, hidden=2, lambda_d=0.1, lambda_sigma=0.0)
-N_RAYS, NR, NC, GRID_RES = 4096, 64, 64, 64
-WORKLOAD = ("single object at full size: hash grid L=16 F=2 T=2^19 res 16..2048, MLP 32-64-64-4 (ReLU, exp "
-            "density, sigmoid colour), 4096 rays x 64 samples/step from the prior sampler (Nc=64) over a 64^3 "
-            "prior grid, random CSG scene, 480x640 views, depth noise 2 mm")
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
 PRECISION = {"fp32": 0, "fp16": 1, "bf16": 2}
 DTYPE = {"fp32": "f32", "fp16": "f16 MLP / f32 accumulate", "bf16": "bf16 MLP / f32 accumulate"}
-FORM = {"fp32": "fp32 per-object", "fp16": "mixed precision (FP16 tensor-core MLP, FP32 master weights)",
+FORM = {"fp32": "fp32", "fp16": "mixed precision (FP16 tensor-core MLP, FP32 master weights)",
         "bf16": "mixed precision (BF16 tensor-core MLP, FP32 master weights)"}
 
+# ---- the 32-object batched workload (the headline)
+# (log2 T, width, hidden layers) per object category, a stand-in for the
+# architecture table the paper's genetic search produces (its values are not
+# printed): display, laptop, chair, mug, ball, keyboard, mouse, book, plant.
+CATEGORY_ARCHS = [(17, 32, 1), (16, 32, 2), (19, 64, 3), (18, 64, 2), (14, 16, 1), (17, 32, 2), (14, 16, 1),
+                  (15, 16, 2), (19, 64, 3)]
+BATCHED_OBJECTS, BATCHED_NR, BATCHED_SEED, GRID_RES = 32, 48, 7, 64
+WORKLOAD = ("32 heterogeneous objects in one batched step: category-table architectures (L=16 F=2, T 2^14..2^19, "
+            "res 16..2048, MLP width 16/32/64 with 1-3 hidden layers), 256..8192 rays per object x 48 samples "
+            "from the prior sampler (Nc=48) over 64^3 prior grids of random CSG shapes, 480x640 views, "
+            "depth noise 2 mm, lambda_d 0.1, lambda_sigma 1e-3")
 
-def mlp_macs(a):
-    return a["width"] * a["L"] * a["F"] + (a["hidden"] - 1) * a["width"] ** 2 + 4 * a["width"]
+# ---- the single full-size object (reported under compare)
+ARCH = dict(L=16, F=2, log2T=19, n_min=16, n_max=2048, width=64, hidden=2, lambda_d=0.1, lambda_sigma=0.0)
+N_RAYS, NR, NC = 4096, 64, 64
+SINGLE_WORKLOAD = ("single object at full size: hash grid L=16 F=2 T=2^19 res 16..2048, MLP 32-64-64-4, 4096 rays "
+                   "x 64 samples/step from the prior sampler (Nc=64) over a 64^3 prior grid, random CSG scene")
+
+
+def mlp_macs(W, H, IN=32):
+    return W * IN + (H - 1) * W * W + 4 * W
 
 
 def load_peaks():
@@ -60,27 +79,54 @@ def dist_env():
     return rank, world, local
 
 
-def _workload(seed: int, n_batches: int, n_params_hash: int):
-    from synth import (cameras_on_sphere, init_params, make_ray_pool, prior_grid, random_colours, sample_batch,
+def batched_specs(seed: int = BATCHED_SEED):
+    """(log2 T, W, H, rays) of the 32 objects: the category table's architectures,
+    rays per object 32 * round(8 * 2^(5 a)), a ~ U[0,1) (256..8192, a projected-area share)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(BATCHED_OBJECTS):
+        log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
+        out.append(dict(log2T=log2T, W=W, H=H, rays=int(32 * round(8 * 2 ** (5 * rng.random())))))
+    return out
+
+
+def batched_arch_dict(sp):
+    return dict(L=16, F=2, log2T=sp["log2T"], n_min=16, n_max=2048, width=sp["W"], hidden=sp["H"], lambda_d=0.1,
+                lambda_sigma=1e-3)
+
+
+def batched_host(seed: int = BATCHED_SEED, only=None, pool_factor: int = 4):
+    """Host data of the 32 objects: a random CSG scene and 64^3 prior grid each,
+    a ray pool from 8 views of 480x640 (pool_factor x its rays, at least 4096),
+    and four ray sets (rays, stratified uniforms, background colours)."""
+    from synth import (cameras_on_sphere, make_ray_pool, prior_grid, random_colours, sample_batch,
                        scene_random_csg, stratified_uniforms)
 
-    sc = scene_random_csg(seed)
-    pool = make_ray_pool(sc, cameras_on_sphere(24, 2.0, 50, 480, 640, seed), 65536, seed, depth_noise=0.004)
-    grid = prior_grid(sc, GRID_RES, seed)
-    shapes = [(ARCH["width"], ARCH["L"] * ARCH["F"])] + [(ARCH["width"], ARCH["width"])] * (ARCH["hidden"] - 1) + \
-        [(4, ARCH["width"])]
-    theta = init_params(n_params_hash, shapes, seed + 1)
-    batches = []
-    for i in range(n_batches):
-        b = sample_batch(pool, N_RAYS, 1000 * seed + i)
-        b["uniforms"] = stratified_uniforms(N_RAYS, NR, 2000 * seed + i)
-        b["c_rand"] = random_colours(N_RAYS, 3000 * seed + i)
-        batches.append(b)
-    return grid, theta, batches
+    out = []
+    for i, sp in enumerate(batched_specs(seed)):
+        if only is not None and i not in only:
+            continue
+        rays = sp["rays"]
+        sc = scene_random_csg(1000 * seed + i)
+        pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 50, 480, 640, i), max(pool_factor * rays, 4096), i,
+                             depth_noise=0.004)
+        sets = []
+        for j in range(4):
+            b = sample_batch(pool, rays, 10 * i + j)
+            b["uniforms"] = stratified_uniforms(rays, BATCHED_NR, 20 * i + j)
+            b["c_rand"] = random_colours(rays, 30 * i + j)
+            sets.append(b)
+        out.append(dict(index=i, spec=sp, scene=sc, grid=prior_grid(sc, GRID_RES, i), pool=pool, sets=sets))
+    return out
+
+
+def batched_totals(specs):
+    samples = sum(sp["rays"] * BATCHED_NR for sp in specs)
+    return samples, sum(sp["rays"] for sp in specs)
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,"
@@ -95,7 +141,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         time.sleep(0.3)
@@ -140,7 +186,7 @@ class ClockSampler:
         if not inside:  # region shorter than the sampling period: nearest sample
             mid = 0.5 * (t0 + t1)
             inside = [min(rows, key=lambda r: abs(r[0] - mid))]
-            note = "nearest sample (timed region shorter than 200 ms)"
+            note = "nearest sample (timed region shorter than the 100 ms sampling period)"
         reasons = sorted({nm for r in inside for nm, v in zip(names, r[3]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
                 "reasons": reasons, "samples": len(inside), "note": note}
@@ -178,55 +224,66 @@ def profiled_traffic(kernel: str):
     return float(rec["dram_bytes_per_launch"])
 
 
+
+
 # ------------------------------------------------------------------- oracle arm
-def oracle_workload(seed: int):
-    """The full-size object's workload for the oracle: (arch, grid, theta, batch)."""
+def _oracle_objects(only=None):
+    """The batched workload for the oracle: per object (index, Arch, grid, theta
+    in FP64, ray set 0 with its uniforms and colours)."""
+    import oracle as orc
+    from synth import init_params
+
+    objs = []
+    for h in batched_host(only=only):
+        a = orc.Arch(**batched_arch_dict(h["spec"]))
+        theta = init_params(orc.n_hash_params(a), a.mlp_shapes(), 5 + h["index"]).astype(np.float64)
+        objs.append((h["index"], a, h["grid"], theta, h["sets"][0]))
+    return objs
+
+
+def _oracle_rays(obj, budget_s: float):
+    """Forward + backward of the oracle on 16-ray chunks of one object's batch
+    until budget_s (at least one chunk): (rays done, seconds)."""
     import oracle as orc
 
-    a = orc.Arch(**ARCH)
-    grid, theta, batches = _workload(seed, 1, orc.n_hash_params(a))
-    return a, grid, theta.astype(np.float64), batches[0]
-
-
-def oracle_throughput(seed: int, budget_s: float, workload=None, t_adam=None):
-    """FP64 oracle (as it stands, one host thread) on a bounded sample of the
-    workload: rays of one step until budget_s of fwd+bwd, plus one full Adam
-    pass over every parameter (timed here unless t_adam is given); the step
-    time is extrapolated to 4096 rays."""
-    import oracle as orc
-
-    a, grid, theta, b = workload if workload is not None else oracle_workload(seed)
-    done = 0
-    t_rays = 0.0
-    chunk = 16
-    while t_rays < budget_s and done < N_RAYS:
+    _, a, grid, theta, b = obj
+    n = b["o"].shape[0]
+    done, spent, chunk = 0, 0.0, 16
+    while (spent < budget_s or done == 0) and done < n:
         sl = slice(done, done + chunk)
         sub = {k: b[k][sl] for k in ("o", "d", "rgb", "depth", "is_obj")}
         t0 = time.perf_counter()
-        orc.batch(a, theta, grid, sub, NC, NR, u=b["uniforms"][sl], c_rand=b["c_rand"][sl], want_grad=True,
-                  want_samples=False)
-        t_rays += time.perf_counter() - t0
-        done += chunk
-    if t_adam is None:
-        m = np.zeros_like(theta)
-        v = np.zeros_like(theta)
-        g = np.zeros_like(theta)
-        t0 = time.perf_counter()
-        orc.adam(theta.copy(), m, v, g, 1, 1e-2)
-        t_adam = time.perf_counter() - t0
-    step_s = t_rays * (N_RAYS / done) + t_adam
-    return dict(value=N_RAYS * NR / step_s, rays=done, t_rays=t_rays, t_adam=t_adam, step_s=step_s)
+        orc.batch(a, theta, grid, sub, BATCHED_NR, BATCHED_NR, u=b["uniforms"][sl], c_rand=b["c_rand"][sl],
+                  want_grad=True, want_samples=False)
+        spent += time.perf_counter() - t0
+        done += min(chunk, n - done)
+    return done, spent
 
 
-def oracle_adam_seconds():
-    """Seconds of one full oracle Adam pass over the full-size object's parameters."""
+def oracle_adam_seconds_per_param():
+    """Seconds per parameter of the oracle's dense Adam pass (timed on 12.2 M parameters)."""
     import oracle as orc
 
-    n = orc.param_count(orc.Arch(**ARCH))
+    n = 12_204_288
     theta, m, v, g = (np.full(n, 1e-3) for _ in range(4))  # written once, so no first-touch page faults are timed
     t0 = time.perf_counter()
     orc.adam(theta, m, v, g, 1, 1e-2)
-    return time.perf_counter() - t0
+    return (time.perf_counter() - t0) / n
+
+
+def oracle_param_total():
+    import oracle as orc
+
+    return sum(orc.param_count(orc.Arch(**batched_arch_dict(sp))) for sp in batched_specs())
+
+
+def oracle_step_seconds(per_obj, cores: int, adam_s: float):
+    """Step time extrapolated from per-object (rays done, seconds): every object's
+    rays at its measured rate, the objects spread evenly over `cores` (they are
+    independent), plus one single-thread Adam pass over every parameter."""
+    specs = batched_specs()
+    rays_s = sum(specs[i]["rays"] * t / max(d, 1) for i, (d, t) in per_obj.items())
+    return rays_s / cores + adam_s
 
 
 _BARRIER = None
@@ -238,70 +295,58 @@ def _oracle_pool_init(barrier):
 
 
 def _oracle_worker(job):
-    """One host process of the all-core oracle timing: rays first, first + stride,
-    ... of the step's batch (16 at a time), started together with the other
-    processes at a barrier, for budget_s of wall time."""
-    seed, budget_s, first, stride = job
-    import oracle as orc
-
-    a = orc.Arch(**ARCH)
-    grid, theta, batches = _workload(seed, 1, orc.n_hash_params(a))
-    b = batches[0]
-    theta = theta.astype(np.float64)
-    chunk = 16
-    starts = list(range(first, N_RAYS, stride))
-    _BARRIER.wait()
-    t0 = time.perf_counter()
-    done = 0
-    i = 0
-    while time.perf_counter() - t0 < budget_s:
-        st = starts[i % len(starts)]
-        sl = slice(st, st + chunk)
-        sub = {k: b[k][sl] for k in ("o", "d", "rgb", "depth", "is_obj")}
-        orc.batch(a, theta, grid, sub, NC, NR, u=b["uniforms"][sl], c_rand=b["c_rand"][sl], want_grad=True,
-                  want_samples=False)
-        done += chunk
-        i += 1
-    return done, time.perf_counter() - t0
+    """One host process of the oracle timing: its objects' workloads are built,
+    then (after a barrier shared with the other processes) each object's rays
+    run for budget_s: {index: (rays, seconds)}."""
+    only, budget_s = job
+    objs = _oracle_objects(only=set(only))
+    if _BARRIER is not None:
+        _BARRIER.wait()
+    return {o[0]: _oracle_rays(o, budget_s) for o in objs}
 
 
-def oracle_throughput_all_cores(seed: int, budget_s: float, cores: int):
-    """The same oracle, unchanged, in `cores` host processes (spawned, so that none
-    inherits a CUDA context), each over its own rays for budget_s, started at a
-    common barrier; the fwd+bwd rate of all of them together, with the single
-    Adam pass of `adam_s` added per step."""
+def oracle_timing(budget_s: float, cores: int):
+    """The oracle, as it stands, in `cores` spawned host processes (none inherits
+    a CUDA context), the 32 objects dealt round-robin, each object run for
+    budget_s * cores / 32 seconds: {index: (rays, seconds)}."""
     import multiprocessing as mp
 
     ctx = mp.get_context("spawn")
-    barrier = ctx.Barrier(cores, timeout=120)
+    barrier = ctx.Barrier(cores, timeout=300)
+    per = budget_s * cores / BATCHED_OBJECTS
+    jobs = [(list(range(k, BATCHED_OBJECTS, cores)), per) for k in range(cores)]
     with ctx.Pool(cores, initializer=_oracle_pool_init, initargs=(barrier,)) as pool:
-        jobs = pool.map_async(_oracle_worker, [(seed, budget_s, 16 * i, 16 * cores) for i in range(cores)],
-                              chunksize=1)
-        res = jobs.get(timeout=budget_s + 300)  # a worker that died never returns: give up, do not hang
-    rays = sum(r[0] for r in res)
-    wall = max(r[1] for r in res)
-    return dict(rays_per_s=rays / wall, rays=rays, wall=wall)
+        res = pool.map_async(_oracle_worker, jobs, chunksize=1).get(timeout=budget_s + 600)
+    out = {}
+    for r in res:
+        out.update(r)
+    return out
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    # per step a ray sample of at most 4 s, shrunk so that all K steps take about
-    # 150 s at most (every step still runs at least one 16-ray chunk)
+    # per step a ray sample of at most 4 s over the 32 objects, shrunk so that
+    # all K steps take about 150 s at most (every object runs at least one chunk)
     budget = min(float(os.environ.get("PRENOM_ORACLE_BUDGET_S", "4")), 150.0 / max(args.steps, 1))
-    workload = oracle_workload(0)  # built once; each step times a ray sample and reuses the Adam pass's time
-    t_adam = oracle_adam_seconds()
-    if args.warmup > 0:
-        oracle_throughput(0, min(0.5, budget), workload, t_adam)
+    objs = _oracle_objects()  # built once
+    adam_s = oracle_adam_seconds_per_param() * oracle_param_total()
+    samples, _ = batched_totals(batched_specs())
+    for _ in range(min(args.warmup, 1)):
+        for o in objs:
+            _oracle_rays(o, 0.0)
     vals, times = [], []
     for _ in range(args.steps):
-        r = oracle_throughput(0, budget, workload, t_adam)
-        vals.append(r["value"])
-        times.append(r["step_s"])
+        per_obj = {o[0]: _oracle_rays(o, budget / len(objs)) for o in objs}
+        step_s = oracle_step_seconds(per_obj, 1, adam_s)
+        vals.append(samples / step_s)
+        times.append(step_s)
     value = statistics.median(vals)
-    sample = (f"per step: {r['rays']} of {N_RAYS} rays fwd+bwd ({r['t_rays']:.2f} s) + one full Adam pass "
-              f"({r['t_adam']:.2f} s, timed once), extrapolated to the 4096-ray step")
+    rays = sum(d for d, _ in per_obj.values())
+    sample = (f"per step: {rays} of the step's rays fwd+bwd (each of the 32 objects for {budget / len(objs):.2f} s, "
+              f"at least 16 rays) + one full Adam pass over every parameter ({adam_s:.2f} s, timed once on 12.2 M "
+              f"parameters and scaled), extrapolated to the whole step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -312,14 +357,6 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------- GPU arm
-# (log2 T, width, hidden layers) per object category, a stand-in for the
-# architecture table the paper's genetic search produces (its values are not
-# printed): display, laptop, chair, mug, ball, keyboard, mouse, book, plant.
-CATEGORY_ARCHS = [(17, 32, 1), (16, 32, 2), (19, 64, 3), (18, 64, 2), (14, 16, 1), (17, 32, 2), (14, 16, 1),
-                  (15, 16, 2), (19, 64, 3)]
-BATCHED_OBJECTS, BATCHED_NR = 32, 48
-
-
 def _device_batches(batches_np, obj, stream):
     import torch
 
@@ -332,48 +369,39 @@ def _device_batches(batches_np, obj, stream):
     return out
 
 
-def _pack_batches(batches_np):
-    """Each host batch as one pinned byte block: its arrays at 256-byte aligned
-    offsets, in a layout shared by all batches (the same keys, shapes and dtypes)."""
+def _pack(batches_np):
+    """All arrays of a list of host batches as one pinned byte block at 256-byte
+    aligned offsets; returns (block, layout), layout[j] = [(key, offset, shape,
+    dtype)] of batch j.  Blocks packed from lists of the same shapes share a layout."""
     import torch
 
     layout, off = [], 0
-    for k, v in batches_np[0].items():
-        a = np.ascontiguousarray(v)
-        layout.append((k, off, a.shape, a.dtype))
-        off += -(-a.nbytes // 256) * 256
-    blocks = []
     for b in batches_np:
-        buf = np.zeros(off, np.uint8)
-        for k, o, shape, dtype in layout:
+        ent = []
+        for k, v in b.items():
+            a = np.ascontiguousarray(v)
+            ent.append((k, off, a.shape, a.dtype))
+            off += -(-a.nbytes // 256) * 256
+        layout.append(ent)
+    buf = np.zeros(off, np.uint8)
+    for b, ent in zip(batches_np, layout):
+        for k, o, shape, dtype in ent:
             a = np.ascontiguousarray(b[k], dtype=dtype)
             assert a.shape == shape
             buf[o:o + a.nbytes] = a.reshape(-1).view(np.uint8)
-        blocks.append(torch.from_numpy(buf).pin_memory())
-    return blocks, layout
+    return torch.from_numpy(buf).pin_memory(), layout
 
 
-def _unpack(buf, layout):
-    """Typed views of a packed block (host or device) by the layout of _pack_batches."""
+def _unpack(buf, ent):
+    """Typed views of one batch of a packed block (host or device) by its layout entry."""
     import torch
 
     tdt = {np.dtype(np.float32): torch.float32, np.dtype(np.uint8): torch.uint8, np.dtype(np.int32): torch.int32}
     out = {}
-    for k, o, shape, dtype in layout:
+    for k, o, shape, dtype in ent:
         n = int(np.prod(shape)) * np.dtype(dtype).itemsize
         out[k] = buf[o:o + n].view(tdt[np.dtype(dtype)]).view(shape)
     return out
-
-
-def _setup_single(pkg, ctx, precision, seed, stream):
-    arch = pkg.make_arch(**ARCH, precision=PRECISION[precision])
-    probe = ctx.create_object(arch)
-    n_params = ctx.param_count(probe)
-    ctx.destroy_object(probe)
-    grid, theta, batches_np = _workload(seed, 8, n_params - mlp_macs(ARCH))
-    obj = ctx.create_object(arch, theta)
-    ctx.set_prior_grid(obj, grid)
-    return obj, _device_batches(batches_np, obj, stream), batches_np, n_params
 
 
 def _time(stream, fn, steps, warmup, barrier=lambda: None, clocks=None):
@@ -398,44 +426,193 @@ def _time(stream, fn, steps, warmup, barrier=lambda: None, clocks=None):
     return ev0.elapsed_time(ev1)
 
 
-def _batched_specs(pkg, precision, seed):
-    """(arch, rays) of the 32 objects: the category table's architectures, rays
-    per object 32 * round(8 * 2^(5 a)), a ~ U[0,1) (256..8192, a projected-area share)."""
-    rng = np.random.default_rng(seed)
-    specs = []
-    for i in range(BATCHED_OBJECTS):
-        log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
-        rays = int(32 * round(8 * 2 ** (5 * rng.random())))
-        specs.append((pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
-                                    lambda_sigma=1e-3, precision=PRECISION[precision]), rays))
-    return specs
+def _batched_objects(pkg, ctx, stream, precision, host, thetas=None):
+    """Objects of the batched workload on the device: ids and the four ray sets
+    as lists of device batches (one per object)."""
+    objs = []
+    for k, h in enumerate(host):
+        arch = pkg.make_arch(**batched_arch_dict(h["spec"]), precision=PRECISION[precision])
+        obj = ctx.create_object(arch, None if thetas is None else thetas[k])
+        ctx.set_prior_grid(obj, h["grid"])
+        objs.append(obj)
+    sets = [[_device_batches([h["sets"][j]], o, stream)[0] for h, o in zip(host, objs)] for j in range(4)]
+    return objs, sets
 
 
-def _batched_workload(pkg, ctx, stream, precision, seed, theta_from=None, only=None):
-    """The 32 objects with random CSG shapes, 48 samples per ray, 64^3 prior
-    grids, four rotating ray sets; `only` restricts it to some object indices."""
-    from synth import (cameras_on_sphere, make_ray_pool, prior_grid, random_colours, sample_batch,
+def _e2e(ctx, stream, objs, host, opts, steps, barrier):
+    """The batched step through the public API with host buffers: every step
+    copies all 32 objects' rays, targets, uniforms and colours from pinned host
+    memory (one block, one copy; on a copy stream, double-buffered, so the copy
+    of step i+1 overlaps step i) and reads the 32 losses back into pinned memory
+    (double-buffered on the device, on a stream of its own)."""
+    import torch
+
+    packed = [_pack([h["sets"][j] for h in host]) for j in range(4)]
+    layout = packed[0][1]
+    blocks = [p[0] for p in packed]
+    h2d = blocks[0].numel()
+    n = len(objs)
+    staging = [torch.empty_like(blocks[0], device="cuda") for _ in range(2)]
+    views = [[dict(_unpack(buf, ent), obj=o) for ent, o in zip(layout, objs)] for buf in staging]
+    losses = [torch.zeros(n, device="cuda") for _ in range(2)]
+    loss_host = torch.zeros((steps, n)).pin_memory()
+    copy_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    stepped = [torch.cuda.Event() for _ in range(2)]
+    read = [torch.cuda.Event() for _ in range(2)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        slot = i % 2
+        if i >= 2:
+            copy_stream.wait_event(stepped[slot])  # the step that read this input buffer is done
+        with torch.cuda.stream(copy_stream):
+            staging[slot].copy_(blocks[i % len(blocks)], non_blocking=True)
+            copied[slot].record(copy_stream)
+        stream.wait_event(copied[slot])
+        if i >= 2:
+            stream.wait_event(read[slot])  # this loss buffer's previous values have been read back
+        ctx.train_step(views[slot], opts, losses[slot])
+        stepped[slot].record(stream)
+        d2h_stream.wait_event(stepped[slot])
+        with torch.cuda.stream(d2h_stream):
+            loss_host[i].copy_(losses[slot], non_blocking=True)
+            read[slot].record(d2h_stream)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    assert np.all(np.isfinite(loss_host.numpy()))
+    return secs, int(h2d), 4 * n
+
+
+def _held_out(host, seed=99):
+    """4 held-out 480x640 views per object, 4096 rays each object (o, d; targets)."""
+    from synth import cameras_on_sphere, make_ray_pool
+
+    out = []
+    for h in host:
+        p = make_ray_pool(h["scene"], cameras_on_sphere(4, 2.0, 50, 480, 640, seed + h["index"]), 4096,
+                          seed + h["index"])
+        out.append(p)
+    return out
+
+
+def _errors(ctx, objs, held, opts):
+    """Mean over the objects of the held-out colour MSE (all rays, black behind
+    the object) and depth L1 (object rays)."""
+    import torch
+
+    mse, l1 = [], []
+    for o, p in zip(objs, held):
+        r = ctx.render({"o": torch.from_numpy(p.o).cuda(), "d": torch.from_numpy(p.d).cuda(), "obj": o}, opts)
+        rgb, depth = r["rgb"].cpu().numpy(), r["depth"].cpu().numpy()
+        tgt = np.where(p.is_obj[:, None] == 1, p.rgb, 0.0)
+        m = p.is_obj == 1
+        mse.append(float(np.mean((rgb - tgt) ** 2)))
+        l1.append(float(np.mean(np.abs(depth - p.depth)[m])) if m.any() else 0.0)
+    return float(np.mean(mse)), float(np.mean(l1))
+
+
+def _equal_error(pkg, ctx, stream, prec, steps=300, seeds=(0, 1, 2)):
+    """The metric's condition on the headline workload: the 32 objects trained
+    for `steps` Adam steps in the batched mixed-precision form and, from the same
+    initial parameters and on the same rays, one plain FP32 step at a time; then
+    held-out colour MSE and depth L1 (mean over the objects) for each seed.  Each
+    step draws every object's rays from a pool of 16x its ray count (on the
+    device, seeded) with the library's own Philox uniforms and background
+    colours.  The mixed-precision form passes when its seed mean is within
+    max(5 %, 2 x the FP32 seed-to-seed std) of the FP32 mean on both errors."""
+    import torch
+    from synth import init_params
+
+    host = batched_host(pool_factor=16)
+    held = _held_out(host)
+    pools = [{k: torch.from_numpy(np.ascontiguousarray(getattr(h["pool"], k))).cuda()
+              for k in ("o", "d", "rgb", "depth", "is_obj")} for h in host]
+    opts = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2)
+    runs = {prec: [], "fp32": []}
+    for seed in seeds:
+        thetas = []
+        for h in host:
+            a = batched_arch_dict(h["spec"])
+            n = pkg.arch_param_count(pkg.make_arch(**a))
+            nmlp = mlp_macs(a["width"], a["hidden"])
+            shapes = [(a["width"], 32)] + [(a["width"], a["width"])] * (a["hidden"] - 1) + [(4, a["width"])]
+            thetas.append(init_params(n - nmlp, shapes, 100 * seed + h["index"]))
+        for form in (prec, "fp32"):
+            objs, _ = _batched_objects(pkg, ctx, stream, form, host, thetas)
+            g = torch.Generator(device="cuda")
+            g.manual_seed(1000 + seed)
+            loss = torch.zeros(len(objs), device="cuda")
+            for i in range(steps):
+                bs = []
+                for h, o, pl in zip(host, objs, pools):
+                    idx = torch.randint(0, pl["o"].shape[0], (h["spec"]["rays"],), device="cuda", generator=g)
+                    bs.append({k: v[idx] for k, v in pl.items()} | {"obj": o})
+                if form == "fp32":  # plain FP32, one object at a time
+                    for j, b in enumerate(bs):
+                        ctx.train_step([b], opts, loss[j:j + 1])
+                else:
+                    ctx.train_step(bs, opts, loss)
+            runs[form].append(_errors(ctx, objs, held, opts) + (float(loss.mean().item()),))
+            for o in objs:
+                ctx.destroy_object(o)
+    out = {}
+    for form, rs in runs.items():
+        a = np.array(rs)
+        out[form] = {"colour_mse": float(a[:, 0].mean()), "colour_mse_std": float(a[:, 0].std(ddof=1)),
+                     "depth_l1": float(a[:, 1].mean()), "depth_l1_std": float(a[:, 1].std(ddof=1)),
+                     "final_loss": float(a[:, 2].mean()), "per_seed": [[round(x, 6) for x in r] for r in rs]}
+    ok = True
+    tol = {}
+    for key in ("colour_mse", "depth_l1"):
+        t = max(0.05 * out["fp32"][key], 2.0 * out["fp32"][key + "_std"])
+        d = out[prec][key] - out["fp32"][key]
+        tol[key] = {"tolerance": t, "difference": d, "within": abs(d) <= t}
+        ok = ok and abs(d) <= t
+    out["tolerance"] = tol
+    out["pass"] = bool(ok)
+    out["workload"] = (f"the headline's 32 objects, {steps} Adam steps each, batched {prec} vs one FP32 step per "
+                       f"object at a time, same initial parameters; held-out: 4 views of 480x640 per object, 4096 "
+                       f"rays; {len(seeds)} seeds")
+    return out
+
+
+def _single_compare(pkg, ctx, stream, prec, rank, steps, warmup):
+    """The single full-size object (4096 rays x 64 samples) in the mixed-precision
+    form and in plain FP32, one object per step."""
+    import torch
+    from synth import (cameras_on_sphere, init_params, make_ray_pool, prior_grid, random_colours, sample_batch,
                        scene_random_csg, stratified_uniforms)
 
-    objs, sets, n_samples = [], [[], [], [], []], 0
-    for i, (arch, rays) in enumerate(_batched_specs(pkg, precision, seed)):
-        if only is not None and i not in only:
-            continue
-        sc = scene_random_csg(1000 * seed + i)
-        init = None if theta_from is None else theta_from[i]
-        obj = ctx.create_object(arch, init)
-        ctx.set_prior_grid(obj, prior_grid(sc, GRID_RES, i))
-        pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 50, 480, 640, i), max(4 * rays, 4096), i,
-                             depth_noise=0.004)
-        for j in range(4):
-            b = sample_batch(pool, rays, 10 * i + j)
-            b["uniforms"] = stratified_uniforms(rays, BATCHED_NR, 20 * i + j)
-            b["c_rand"] = random_colours(rays, 30 * i + j)
-            sets[j].append(b)
-        objs.append(obj)
-        n_samples += rays * BATCHED_NR
-    dev_sets = [[_device_batches([b], o, stream)[0] for b, o in zip(s, objs)] for s in sets]
-    return objs, dev_sets, n_samples
+    sc = scene_random_csg(rank)
+    pool = make_ray_pool(sc, cameras_on_sphere(24, 2.0, 50, 480, 640, rank), 65536, rank, depth_noise=0.004)
+    grid = prior_grid(sc, GRID_RES, rank)
+    batches_np = []
+    for i in range(8):
+        b = sample_batch(pool, N_RAYS, 1000 * rank + i)
+        b["uniforms"] = stratified_uniforms(N_RAYS, NR, 2000 * rank + i)
+        b["c_rand"] = random_colours(N_RAYS, 3000 * rank + i)
+        batches_np.append(b)
+    opts = pkg.make_opts(nc=NC, nr=NR, lr=1e-2)
+    loss = torch.zeros(1, device="cuda")
+    out = {"workload": SINGLE_WORKLOAD}
+    theta = None
+    for form in (prec, "fp32"):
+        arch = pkg.make_arch(**ARCH, precision=PRECISION[form])
+        if theta is None:
+            n = pkg.arch_param_count(arch)
+            theta = init_params(n - mlp_macs(64, 2), [(64, 32), (64, 64), (4, 64)], rank + 1)
+        obj = ctx.create_object(arch, theta)
+        ctx.set_prior_grid(obj, grid)
+        dev = _device_batches(batches_np, obj, stream)
+        ctx.autotune([dev[0]], opts)
+        f = lambda i: ctx.train_step([dev[i % len(dev)]], opts, loss)  # noqa: E731
+        ms = _time(stream, f, steps, warmup)
+        out[form] = {"value": N_RAYS * NR * steps / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms / steps}
+        ctx.destroy_object(obj)
+    out["speedup"] = out[prec]["value"] / out["fp32"]["value"]
+    return out
 
 
 STRESS_OBJECTS, STRESS_RAYS, STRESS_NR = 64, 1 << 20, 64
@@ -539,8 +716,9 @@ def _ablation_compare(pkg, ctx, stream, prec, steps=300, seeds=(0, 1, 2)):
     """Sampling ablation (the analogue of the paper's Table IV row on
     probabilistic sampling): the small scene (sphere + box, 8 views of 64x64)
     trained for `steps` Adam steps of 256 rays x 32 samples with prior sampling
-    over the 32^3 prior grid (as given, and refreshed from the field every 50
-    steps as §III-B does) and with uniform sampling (a zero grid: every ray
+    over the 32^3 prior grid (as given, refreshed from the field every 50
+    steps as §III-B does, and a softer prior of peak density 8 whose dilated
+    shell is not opaque) and with uniform sampling (a zero grid: every ray
     escapes, so the flat CDF of the escape rule applies), on the same rays; then
     colour MSE (all pixels, black background) and depth L1 (object pixels) on 4
     held-out 64x64 views, sampled the way each was trained.  Each seed draws its
@@ -564,8 +742,11 @@ def _ablation_compare(pkg, ctx, stream, prec, steps=300, seeds=(0, 1, 2)):
     opts = pkg.make_opts(nc=32, nr=32, lr=1e-2)
     loss = torch.zeros(1, device="cuda")
     prior = prior_grid(sc, 32, 0)
+    # a second synthetic prior whose dilated shell is not opaque: peak density 8, so a
+    # ray crossing the 2-voxel shell (2/32 of the cube) sees an optical depth of 0.5
+    soft = prior_grid(sc, 32, 0, peak=8.0)
     variants = (("prior_sampling", prior, 0), ("prior_sampling_refresh_every_50", prior, 50),
-                ("uniform_sampling", np.zeros((32, 32, 32), np.float32), 0))
+                ("prior_sampling_soft_prior", soft, 0), ("uniform_sampling", np.zeros((32, 32, 32), np.float32), 0))
     runs = {name: [] for name, _, _ in variants}
     for seed in seeds:
         theta = init_params(n - (32 * 16 + 32 * 32 + 4 * 32), [(32, 16), (32, 32), (4, 32)], 5 + seed)
@@ -601,6 +782,56 @@ def _ablation_compare(pkg, ctx, stream, prec, steps=300, seeds=(0, 1, 2)):
     return out
 
 
+def _roofline(pkg, report, specs, prec, adam_ms, n_params, peaks):
+    """Each kernel of one batched step against its own bound, from the per-group
+    timing report: a group is every object of one MLP width (all objects have
+    L=16, F=2, so 8 L F x 4 B = 1024 B of gathers or FP32 reductions per sample);
+    its MLP work is 6 MAC FLOP per sample (2 forward, 4 backward).  The record
+    with the largest device time per step is the dominant kernel."""
+    names = {pkg.PRENOM_KERNEL_SAMPLE_ENCODE: "sample_encode_kernel", pkg.PRENOM_KERNEL_SCATTER: "hash_scatter_kernel"}
+    recs = []
+    for label, k, ms, n in report:
+        tok = label.split()
+        W, form = int(tok[1][1:]), tok[6]
+        members = [sp for sp in specs if sp["W"] == W]
+        samples = sum(sp["rays"] * BATCHED_NR for sp in members)
+        flops = sum(sp["rays"] * BATCHED_NR * 6 * mlp_macs(sp["W"], sp["H"]) for sp in members)
+        t = (ms / n) / 1e3
+        if k == pkg.PRENOM_KERNEL_TRAIN and form == "split":
+            tc = prec != "fp32"
+            pk = peaks["bf16"] if tc else FP32_PEAK_TFLOPS
+            ach = flops / t / 1e12
+            rec = {"kernel": ("fused_tc_kernel_split" if tc else "fused_fp32_kernel_split"), "group": label,
+                   "bound": "tensor" if tc else "alu", "achieved": round(ach, 2), "peak": round(pk, 1),
+                   "unit": "TFLOP/s", "frac": round(ach / pk, 4),
+                   "algorithmic": f"6 x MAC FLOP/sample over {samples} samples = {flops / 1e9:.2f} GFLOP",
+                   "peak_src": (peaks["src"] + " bf16 (fp16 same rate)") if tc else "FP32 FFMA 152x128x2x2070 MHz"}
+        else:
+            per = 2048 if k == pkg.PRENOM_KERNEL_TRAIN else 1024
+            byts = samples * per
+            ach = byts / t / 1e9
+            kname = names.get(k, "fused_tc_kernel" if prec != "fp32" else "fused_fp32_kernel")
+            rec = {"kernel": kname, "group": label, "bound": "hbm", "achieved": round(ach, 1),
+                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                   "algorithmic": f"{per} B/sample x {samples} samples = {byts / 1e6:.1f} MB",
+                   "peak_src": peaks["src"] + " copy bandwidth"}
+        rec["avg_us"] = round(t * 1e6, 2)
+        rec["traffic"] = profiled_traffic(f"{rec['kernel']}/{prec}/W{W}")
+        recs.append(rec)
+    t = adam_ms / 1e3
+    ach = n_params * 28 / t / 1e9
+    recs.append({"kernel": "adam_kernel", "group": "every object", "bound": "hbm", "achieved": round(ach, 1),
+                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                 "algorithmic": f"28 B/parameter (read g, m, v, theta; write m, v, theta) x {n_params}",
+                 "peak_src": peaks["src"] + " copy bandwidth", "avg_us": round(t * 1e6, 2),
+                 "traffic": profiled_traffic(f"adam_kernel/{prec}/batched")})
+    dom = max(recs, key=lambda r: r["avg_us"])
+    roof = dict(dom)
+    roof["other_kernels"] = [r for r in recs if r is not dom]
+    roof["step_kernels_us"] = round(sum(r["avg_us"] for r in recs), 2)
+    return roof
+
+
 def run_ours(args):
     import torch
 
@@ -627,112 +858,81 @@ def run_ours(args):
     ctx = pkg.Context(seed=rank, stream=stream)
     prec = args.precision
     form_flags = {"auto": 0, "fused": pkg.PRENOM_FLAG_FUSED, "split": pkg.PRENOM_FLAG_SPLIT}[args.form]
-    opts = pkg.make_opts(nc=NC, nr=NR, lr=1e-2, flags=form_flags)
-    loss = torch.zeros(1, device="cuda")
-    samples_per_step = N_RAYS * NR
+    bopts = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2, flags=form_flags)
+    specs = batched_specs()
+    n_smp, n_rays = batched_totals(specs)
 
-    # ---- headline: the full-size object in the chosen form, inputs resident in HBM
-    obj, dev_batches, batches_np, n_params = _setup_single(pkg, ctx, prec, rank, stream)
-    step = lambda i: ctx.train_step([dev_batches[i % len(dev_batches)]], opts, loss)  # noqa: E731
-    _time(stream, step, 0, args.warmup)  # also runs the autotuner's first calls
+    # ---- headline: the 32 objects in one batched step, inputs resident in HBM.
+    # The autotuner's calls and the graph captures run here, in set-up.
+    host = batched_host()
+    objs, sets = _batched_objects(pkg, ctx, stream, prec, host)
+    n_params = sum(ctx.param_count(o) for o in objs)
+    lossb = torch.zeros(len(objs), device="cuda")
+    ctx.autotune(sets[0], bopts)
+    step = lambda i: ctx.train_step(sets[i % 4], bopts, lossb)  # noqa: E731
+    _time(stream, step, 0, args.warmup)
     tuning = ctx.tuning_report().strip()
+    cap0 = ctx.capture_count()
     launches0 = ctx.launch_count()
     clocks = ClockSampler(gpu_identifier(local))
     with clocks:  # the step as a user runs it: CUDA-graph replay, no per-kernel events
         ms = _time(stream, step, args.steps, 0, barrier, clocks)
     launches = ctx.launch_count() - launches0
-    # per-kernel device times: the same steps launched directly, each kernel between CUDA events
-    ctx.enable_timing(True)
-    _time(stream, step, max(args.steps // 4, 20), 0)
-    ktimes = {k: ctx.kernel_time(k) for k in (pkg.PRENOM_KERNEL_TRAIN, pkg.PRENOM_KERNEL_ADAM,
-                                              pkg.PRENOM_KERNEL_SAMPLE_ENCODE, pkg.PRENOM_KERNEL_SCATTER)}
-    ctx.enable_timing(False)
+    assert ctx.capture_count() == cap0, "the timed region ran autotuner calls or graph captures"
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = t.item()
-    value = samples_per_step * args.steps * world / (ms / 1e3)
+    value = n_smp * args.steps * world / (ms / 1e3)
 
-    # ---- end to end through the public API with host buffers: every step copies its
-    # batch from pinned host memory (one block per batch, its arrays at 256-byte
-    # offsets, so one copy per step; on a copy stream, double-buffered, so the copy
-    # of step i+1 overlaps step i) and reads its loss back into pinned memory
-    pinned, layout = _pack_batches(batches_np)
-    h2d = pinned[0].numel()
-    e2e_steps = max(args.steps // 2, 5)
-    loss_host = torch.zeros(e2e_steps).pin_memory()
-    staging = [torch.empty_like(pinned[0], device="cuda") for _ in range(2)]
-    views = [dict(_unpack(buf, layout), obj=obj) for buf in staging]
-    # the losses are double-buffered too, and read back on a stream of their own,
-    # so that neither copy direction waits in the training stream
-    losses = [torch.zeros(1, device="cuda") for _ in range(2)]
-    copy_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
-    copied = [torch.cuda.Event() for _ in range(2)]
-    stepped = [torch.cuda.Event() for _ in range(2)]
-    read = [torch.cuda.Event() for _ in range(2)]
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        slot = i % 2
-        if i >= 2:
-            copy_stream.wait_event(stepped[slot])  # the step that read this input buffer is done
-        with torch.cuda.stream(copy_stream):
-            staging[slot].copy_(pinned[i % len(pinned)], non_blocking=True)
-            copied[slot].record(copy_stream)
-        stream.wait_event(copied[slot])
-        if i >= 2:
-            stream.wait_event(read[slot])  # this loss buffer's previous value has been read back
-        ctx.train_step([views[slot]], opts, losses[slot])
-        stepped[slot].record(stream)
-        d2h_stream.wait_event(stepped[slot])
-        with torch.cuda.stream(d2h_stream):
-            loss_host[i].copy_(losses[slot][0], non_blocking=True)
-            read[slot].record(d2h_stream)
-    torch.cuda.synchronize()
-    e2e_losses = loss_host.numpy().copy()
-    e2e_s = time.perf_counter() - t0
-    assert np.all(np.isfinite(e2e_losses))
+    # per-kernel device times: the same steps launched directly, each kernel between CUDA events
+    ctx.enable_timing(True)
+    nk = max(args.steps // 4, 5)
+    _time(stream, step, nk, 0)
+    report = ctx.timing_report()
+    adam_ms = ctx.kernel_time(pkg.PRENOM_KERNEL_ADAM)
+    ctx.enable_timing(False)
+    groups = [{"group": lab, "kernel": pkg.KERNEL_NAMES[k], "avg_us": round(1e3 * t_ms / n, 2)}
+              for lab, k, t_ms, n in report]
+    roofline = _roofline(pkg, report, specs, prec, adam_ms[0] / max(adam_ms[1], 1), n_params, load_peaks())
+
+    # ---- end to end through the public API with host buffers
+    e2e_s, h2d, d2h = _e2e(ctx, stream, objs, host, bopts, args.steps, barrier)
     if world > 1:
         t = torch.tensor([e2e_s], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = t.item()
-    e2e_value = samples_per_step * e2e_steps * world / e2e_s
-    ctx.destroy_object(obj)
+    e2e_value = n_smp * args.steps * world / e2e_s
+
+    # ---- the plain FP32 side of the pair: the same 32 objects from the same
+    # parameters, one FP32 step per object at a time (each object autotuned first)
+    thetas = [ctx.get_state(o).cpu().numpy() for o in objs]
+    for o in objs:
+        ctx.destroy_object(o)
+    objs32, sets32 = _batched_objects(pkg, ctx, stream, "fp32", host, thetas)
+    opts32 = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2)
+    for b in sets32[0]:
+        ctx.autotune([b], opts32)
+    fl = lambda i: [ctx.train_step([b], opts32, lossb[j:j + 1]) for j, b in enumerate(sets32[i % 4])]  # noqa
+    ms32 = _time(stream, fl, args.steps, args.warmup, barrier)
+    if world > 1:
+        t = torch.tensor([ms32], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms32 = t.item()
+    fp32_loop = {"value": n_smp * args.steps * world / (ms32 / 1e3), "unit": "samples/s",
+                 "ms_per_step": ms32 / args.steps, "form": "32 single-object plain FP32 steps (each its own launch "
+                                                            "set, CUDA-graph replay)"}
+    for o in objs32:
+        ctx.destroy_object(o)
+
+    equal = None
+    if world == 1 and not args.no_equal_error and prec != "fp32":
+        equal = _equal_error(pkg, ctx, stream, prec, steps=args.equal_error_steps)
 
     compare = {}
     if world == 1 and not args.no_compare:
-        # the plain FP32 per-object form on the same object and rays
-        if prec != "fp32":
-            o32, b32, _, _ = _setup_single(pkg, ctx, "fp32", rank, stream)
-            f = lambda i: ctx.train_step([b32[i % len(b32)]], opts, loss)  # noqa: E731
-            ms32 = _time(stream, f, max(args.steps // 4, 20), args.warmup)
-            compare["fp32_per_object"] = {"value": samples_per_step * max(args.steps // 4, 20) / (ms32 / 1e3),
-                                          "unit": "samples/s", "ms_per_step": ms32 / max(args.steps // 4, 20)}
-            ctx.destroy_object(o32)
-        # 32 heterogeneous objects: one batched step (FP16, graph replay) vs FP32 one object at a time
-        objs16, sets16, n_smp = _batched_workload(pkg, ctx, stream, prec, 7)
-        thetas = [ctx.get_state(o).cpu().numpy() for o in objs16]
-        objs32, sets32, _ = _batched_workload(pkg, ctx, stream, "fp32", 7, theta_from=thetas)
-        bopts = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2)
-        lossb = torch.zeros(len(objs16), device="cuda")
-        nb = max(args.steps // 20, 10)
-        fb = lambda i: ctx.train_step(sets16[i % 4], bopts, lossb)  # noqa: E731
-        msb = _time(stream, fb, nb, max(args.warmup, 6))  # >= 4 calls tune the work-chunk size first
-        fl = lambda i: [ctx.train_step([b], bopts, lossb[j:j + 1]) for j, b in enumerate(sets32[i % 4])]  # noqa
-        msl = _time(stream, fl, nb, 2)
-        compare["batched_32_objects"] = {
-            "workload": "32 objects of the category table (T 2^14..2^19, W 16/32/64, 1-3 hidden layers), "
-                        "256..8192 rays x 48 samples, %d samples per step" % n_smp,
-            "batched_" + prec: {"value": n_smp * nb / (msb / 1e3), "unit": "samples/s", "ms_per_step": msb / nb,
-                                "form": "one launch per kernel variant, CUDA graph replay"},
-            "fp32_per_object_loop": {"value": n_smp * nb / (msl / 1e3), "unit": "samples/s",
-                                     "ms_per_step": msl / nb, "form": "32 single-object FP32 steps"},
-            "speedup": msl / msb}
-        for o in objs16 + objs32:
-            ctx.destroy_object(o)
-
-    if world == 1 and not args.no_compare:
+        compare["single_object_full_size"] = _single_compare(pkg, ctx, stream, prec, rank, max(args.steps, 20),
+                                                             args.warmup)
         compare["reptile_meta_step"] = _meta_compare(pkg, ctx, stream, prec)
         compare["sampling_ablation"] = _ablation_compare(pkg, ctx, stream, prec)
         compare["mapping_stress_64_objects"] = _stress_compare(pkg, ctx, stream)
@@ -742,123 +942,75 @@ def run_ours(args):
         # first on the per-object cost), one batched step per rank, no exchange
         from paper_2503_01582_gb300.shard import object_cost, rank_objects
 
-        specs = _batched_specs(pkg, prec, 7)
-        costs = [object_cost(a.L, a.F, a.width, a.hidden, pkg.arch_param_count(a), r * BATCHED_NR,
-                             4 if prec == "fp32" else 2) for a, r in specs]
+        costs = [object_cost(16, 2, sp["W"], sp["H"], pkg.arch_param_count(pkg.make_arch(**batched_arch_dict(sp))),
+                             sp["rays"] * BATCHED_NR, 4 if prec == "fp32" else 2) for sp in specs]
         mine = rank_objects(costs, world, rank)
-        objs, sets, n_mine = _batched_workload(pkg, ctx, stream, prec, 7, only=set(mine))
-        bopts = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2)
-        lossb = torch.zeros(max(len(objs), 1), device="cuda")
-        nb = max(args.steps // 20, 10)
-        fb = lambda i: ctx.train_step(sets[i % 4], bopts, lossb) if objs else None  # noqa: E731
-        msb = _time(stream, fb, nb, max(args.warmup, 6), barrier)
+        hs = [h for h in host if h["index"] in set(mine)]
+        objs_r, sets_r = _batched_objects(pkg, ctx, stream, prec, hs)
+        lossr = torch.zeros(max(len(objs_r), 1), device="cuda")
+        if objs_r:
+            ctx.autotune(sets_r[0], bopts)
+        fb = lambda i: ctx.train_step(sets_r[i % 4], bopts, lossr) if objs_r else None  # noqa: E731
+        msb = _time(stream, fb, args.steps, args.warmup, barrier)
         t = torch.tensor([msb], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        n_all = sum(r * BATCHED_NR for _, r in specs)
         compare["batched_32_objects_sharded"] = {
             "workload": "the 32-object batched workload split over %d GPUs by longest-processing-time "
-                        "first; %d samples per step in total" % (world, n_all),
-            "value": n_all * nb / (t.item() / 1e3), "unit": "samples/s", "ms_per_step": t.item() / nb,
-            "scaling": "strong"}
-        for o in objs:
+                        "first; %d samples per step in total" % (world, n_smp),
+            "value": n_smp * args.steps / (t.item() / 1e3), "unit": "samples/s",
+            "ms_per_step": t.item() / args.steps, "scaling": "strong"}
+        for o in objs_r:
             ctx.destroy_object(o)
-
-    # ---- roofline: each kernel of the step against its own bound; the one with
-    # the largest device time is reported as `roofline`, the others beside it
-    peaks = load_peaks()
-    feat_bytes = 8 * ARCH["L"] * ARCH["F"] * 4  # corners x levels x features x FP32, per sample
-    flops = samples_per_step * mlp_macs(ARCH) * 6  # MLP: 2 MAC forward + 4 MAC backward flops per sample
-    split = ktimes[pkg.PRENOM_KERNEL_SAMPLE_ENCODE][1] > 0
-
-    def avg_s(k):
-        ms, n = ktimes[k]
-        return (ms / n) / 1e3 if n else 0.0
-
-    def hbm(name, kid, bytes_per_launch, what):
-        t = avg_s(kid)
-        ach = bytes_per_launch / t / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm_gbs"], 4), "avg_us": round(t * 1e6, 2), "algorithmic": what,
-                "peak_src": peaks["src"] + " copy bandwidth"}
-
-    def mlp(name, kid):
-        t = avg_s(kid)
-        ach = flops / t / 1e12
-        pk, src = ((FP32_PEAK_TFLOPS, "FP32 FFMA 152x128x2x2070 MHz") if prec == "fp32" else
-                   (peaks["bf16"], peaks["src"] + " bf16 (fp16 same rate)"))
-        return {"kernel": name, "bound": "alu" if prec == "fp32" else "tensor", "achieved": round(ach, 2),
-                "peak": round(pk, 1), "unit": "TFLOP/s", "frac": round(ach / pk, 4), "avg_us": round(t * 1e6, 2),
-                "algorithmic": f"{6 * mlp_macs(ARCH)} FLOP/sample (2 MAC fwd + 4 MAC bwd) x {samples_per_step}",
-                "peak_src": src}
-
-    recs = []
-    if split:
-        recs.append(hbm("sample_encode_kernel", pkg.PRENOM_KERNEL_SAMPLE_ENCODE, samples_per_step * feat_bytes,
-                        f"{feat_bytes} B/sample hash gather x {samples_per_step} samples"))
-        recs.append(mlp("fused_fp32_kernel_split" if prec == "fp32" else "fused_tc_kernel_split", pkg.PRENOM_KERNEL_TRAIN))
-        recs.append(hbm("hash_scatter_kernel", pkg.PRENOM_KERNEL_SCATTER, samples_per_step * feat_bytes,
-                        f"{feat_bytes} B/sample hash scatter (FP32 reductions) x {samples_per_step} samples"))
-    else:
-        fused = hbm("fused_fp32_kernel" if prec == "fp32" else "fused_tc_kernel", pkg.PRENOM_KERNEL_TRAIN,
-                    samples_per_step * 2 * feat_bytes,
-                    f"{2 * feat_bytes} B/sample (hash gather {feat_bytes} + scatter {feat_bytes}) x "
-                    f"{samples_per_step} samples")
-        fused["mlp"] = mlp(fused["kernel"], pkg.PRENOM_KERNEL_TRAIN)
-        recs.append(fused)
-    recs.append(hbm("adam_kernel", pkg.PRENOM_KERNEL_ADAM, n_params * 28,
-                    f"28 B/parameter (read g, m, v, theta; write m, v, theta) x {n_params}"))
-    dom = max(recs, key=lambda r: r["avg_us"])
-    roofline = dict(dom)
-    roofline["traffic"] = profiled_traffic(dom["kernel"] + "/" + prec)
-    roofline["kernel"] = dom["kernel"] + ", " + prec
-    roofline["other_kernels"] = [dict(r, traffic=profiled_traffic(r["kernel"] + "/" + prec)) for r in recs if r is not dom]
-    roofline["step_kernels_us"] = round(sum(r["avg_us"] for r in recs), 2)
 
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             budget = float(os.environ.get("PRENOM_ORACLE_BUDGET_S", "12"))
+            adam_s = oracle_adam_seconds_per_param() * oracle_param_total()
             try:  # in a spawned process of its own: no CUDA context or bench threads beside it
-                r1 = oracle_throughput_all_cores(0, budget, 1)
-                t_adam = oracle_adam_seconds()
-                cpu = {"value": N_RAYS * NR / (N_RAYS / r1["rays_per_s"] + t_adam), "unit": "samples/s",
-                       "cores": 1, "kind": "oracle",
-                       "sample": (f"{r1['rays']} rays fwd+bwd in {r1['wall']:.1f} s in one spawned host process + "
-                                  f"one full Adam pass ({t_adam:.2f} s), FP64, extrapolated to the 4096-ray step")}
-                r = {"t_adam": t_adam}
+                r1 = oracle_timing(budget, 1)
+                where = "one spawned host process"
             except Exception:
-                r = oracle_throughput(0, budget)
-                cpu = {"value": r["value"], "unit": "samples/s", "cores": 1, "kind": "oracle",
-                       "sample": (f"{r['rays']} of {N_RAYS} rays fwd+bwd ({r['t_rays']:.1f} s) + one full Adam "
-                                  f"pass ({r['t_adam']:.2f} s), FP64, 1 host thread in the bench process, "
-                                  f"extrapolated to the 4096-ray step")}
+                r1 = {o[0]: _oracle_rays(o, budget / BATCHED_OBJECTS) for o in _oracle_objects()}
+                where = "the bench process (the spawned process failed)"
+            s1 = oracle_step_seconds(r1, 1, adam_s)
+            cpu = {"value": n_smp / s1, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                   "sample": (f"{sum(d for d, _ in r1.values())} of the step's {n_rays} rays fwd+bwd (each of the "
+                              f"32 objects for {budget / BATCHED_OBJECTS:.2f} s) in {where} + one full Adam pass "
+                              f"over {oracle_param_total()} parameters ({adam_s:.2f} s, timed on 12.2 M), FP64, "
+                              f"extrapolated to the whole step")}
             ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
             if ncores > 1:  # the same oracle on every host core, one process per core
                 try:
-                    ra = oracle_throughput_all_cores(0, float(os.environ.get("PRENOM_ORACLE_ALL_CORES_S", "6")),
-                                                     ncores)
-                    step_s = N_RAYS / ra["rays_per_s"] + r["t_adam"]
-                    cpu["all_cores"] = {"value": N_RAYS * NR / step_s, "unit": "samples/s", "cores": ncores,
-                                        "sample": (f"{ra['rays']} rays fwd+bwd in {ra['wall']:.1f} s over {ncores} "
-                                                   f"processes + the one-thread Adam pass, extrapolated to the "
-                                                   f"4096-ray step")}
+                    ra = oracle_timing(float(os.environ.get("PRENOM_ORACLE_ALL_CORES_S", "6")), ncores)
+                    sa = oracle_step_seconds(ra, ncores, adam_s)
+                    cpu["all_cores"] = {"value": n_smp / sa, "unit": "samples/s", "cores": ncores,
+                                        "sample": (f"{sum(d for d, _ in ra.values())} rays fwd+bwd over {ncores} "
+                                                   f"processes (objects dealt round-robin, spread evenly in the "
+                                                   f"extrapolation) + the one-thread Adam pass")}
                 except Exception as e:  # the headline line is printed whatever happens here
                     cpu["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
                 "config": {"workload": WORKLOAD,
-                           "form": FORM[prec] + {"auto": ", fused or split form as autotuned",
-                                                 "fused": ", one fused kernel",
-                                                 "split": ", split: sampling+encoding / MLP kernel / "
-                                                          "hash scatter"}[args.form],
-                           "rays_per_step": N_RAYS, "samples_per_ray": NR,
-                           "probes": NC, "params": n_params, "autotuner": tuning,
-                           "parallelism": f"{world} independent objects (one per GPU)" if world > 1 else "1 object",
-                           "l2": "working set > L2: theta, grad, Adam m and v (4 x %.0f MB) stream every step"
-                                 % (n_params * 4 / 1e6)},
-                "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
-                        "d2h_bytes_per_step": 4},
+                           "form": "batched " + FORM[prec] + {"auto": ", fused or split form per group as "
+                                                                      "autotuned",
+                                                              "fused": ", one fused kernel per group",
+                                                              "split": ", split form per group"}[args.form],
+                           "objects": BATCHED_OBJECTS, "rays_per_step": n_rays, "samples_per_ray": BATCHED_NR,
+                           "samples_per_step": n_smp, "params": n_params, "autotuner": tuning,
+                           "groups": groups,
+                           "timed_region": "autotuner calls and graph captures ran in set-up (prenom_autotune); "
+                                           "none inside the timed steps (checked by the library's counters)",
+                           "parallelism": (f"{world} ranks, each its own copy of the 32 objects" if world > 1
+                                           else "1 GPU, 32 objects"),
+                           "l2": "working set > L2: theta, grad, Adam m and v of all objects (4 x %.0f MB) stream "
+                                 "every step" % (n_params * 4 / 1e6)},
+                "fp32_per_object_loop": fp32_loop, "speedup_vs_fp32_loop": value / fp32_loop["value"],
+                "equal_error": equal,
+                "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
                 "clocks": clocks.summary(), "compare": compare}
         print(json.dumps(line), flush=True)
@@ -870,15 +1022,20 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 and 32-object comparison runs")
+    ap.add_argument("--no-compare", action="store_true", help="skip the single-object, Reptile, ablation and "
+                                                              "stress comparison runs")
+    ap.add_argument("--no-equal-error", action="store_true", help="skip the equal-error training runs")
+    ap.add_argument("--equal-error-steps", type=int, default=300)
     ap.add_argument("--precision", default="fp16", choices=list(PRECISION))
     ap.add_argument("--form", default="auto", choices=["auto", "fused", "split"],
-                    help="mixed precision: the autotuner's choice, the one fused kernel, or the three-kernel split form")
+                    help="the autotuner's choice per group, the fused kernel, or the three-kernel split form")
     args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -61,7 +61,7 @@ extern "C" {
  * FP32 accumulation; parameters, Adam state, hash features, sampling,
  * transmittance and the loss stay FP32.  FP16 uses a dynamic loss scale
  * (initial 2^15, halved and the step dropped on an overflow, doubled after 1000
- * clean steps); BF16 uses a scale of 1. */
+ * clean steps, see prenom_set_loss_scale); BF16 uses a scale of 1. */
 #define PRENOM_PRECISION_FP16 1
 #define PRENOM_PRECISION_BF16 2
 
@@ -211,8 +211,13 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * A step synchronises with the step before the previous
  * one (two staging buffers are in flight), allocates its work-list and split
  * buffers on first use and when they must grow, and updates at most 128
- * objects.  With PRENOM_FLAG_CHECK_FINITE the batches run one launch each,
- * without tuning or graphs.
+ * objects.  The tuning calls and the first capture of a signature can be
+ * taken out of a training loop by calling prenom_autotune() first.
+ * With PRENOM_FLAG_CHECK_FINITE the batches run one launch each, without
+ * tuning or graphs; the call then waits for the stream and, when a batch's
+ * loss is NaN or infinite, clears the gradients of the step's objects, takes
+ * no Adam step and returns PRENOM_ERR_NONFINITE (with loss_dev NULL at most
+ * 64 batches, whose losses go to the context's own scratch).
  * loss_dev: device [n_batches] floats receiving each batch's loss, or NULL.
  * Each object named must have a prior grid unless every batch naming it
  * gives t_in. */
@@ -353,6 +358,34 @@ PRENOM_API int prenom_refresh_prior(prenom_ctx *ctx, int32_t obj, int32_t res);
 PRENOM_API int prenom_canonical_yaw(prenom_ctx *ctx, int32_t obj, const float *points, int32_t n_points,
                                     int32_t n_gamma, float *scores, int32_t *best);
 
+/* Runs, ahead of training, what the first calls of prenom_train_step() with
+ * these batches and options would otherwise do inside the training loop: the
+ * autotuner's calls for every group signature not yet tuned (one untimed call,
+ * then two rounds over the candidates), run as gradient-only steps -- no Adam
+ * update, no change of theta, Adam moments or step counts; the gradients they
+ * accumulate and any 16-bit overflow flag they raise are cleared afterwards --
+ * and the capture of the step's CUDA graph for both staging buffers (when
+ * graphs apply: a non-default stream, timing off, no PRENOM_FLAG_NO_GRAPH).
+ * The next prenom_train_step() calls with batches of the same signature then
+ * replay without tuning or capturing.  Same arguments and checks as
+ * prenom_train_step(); batches with PRENOM_FLAG_CHECK_FINITE are neither tuned
+ * nor captured, so the call does nothing for them.  Waits for the stream. */
+PRENOM_API int prenom_autotune(prenom_ctx *ctx, const prenom_ray_batch *batches, int32_t n_batches,
+                               const prenom_train_opts *opts);
+
+/* Counters of the context: step graphs captured so far, and training steps run
+ * as autotuner measurements (either may be NULL).  Unchanged counters around a
+ * loop of steps show that the loop neither tuned nor captured. */
+PRENOM_API int prenom_capture_count(prenom_ctx *ctx, int64_t *captures, int64_t *tuning_calls);
+
+/* Per-group kernel times of the batched steps run while timing was enabled
+ * (prenom_enable_timing): one line per (group, kernel) "label<TAB>kK<TAB>total
+ * ms<TAB>launches", where the label names the group's precision, MLP width W,
+ * encoding width IN, deepest hidden depth H, batch and tile counts, form
+ * (split or fused) and grid, and K is a PRENOM_KERNEL_* id.  Synchronises.
+ * buf: host, cap bytes, NUL-terminated, truncated to fit. */
+PRENOM_API int prenom_timing_report(prenom_ctx *ctx, char *buf, size_t cap);
+
 /* The autotuner's record as text (one line per group signature: the step
  * times in ms of each timed call, "cK" = candidate K, and the chosen candidate
  * after "->"; candidates: c0 the split form, c1..c3 the fused kernel in one
@@ -432,6 +465,12 @@ PRENOM_API int prenom_train_step_noalloc(const prenom_arch *arch, float *theta, 
  * scale and the number of steps dropped because a scaled 16-bit gradient
  * overflowed.  FP32 objects report scale 1 and 0 dropped steps. */
 PRENOM_API int prenom_get_loss_scale(prenom_ctx *ctx, int32_t obj, float *scale, int32_t *dropped_steps);
+
+/* Sets the loss scale of a mixed-precision object (1 <= scale <= 2^24) and the
+ * number of clean steps in a row after which it doubles (growth_interval >= 1;
+ * 1000 by default); the count of clean steps restarts at 0.  Blocking.  FP32
+ * objects have no loss scale: PRENOM_ERR_INVALID_ARG. */
+PRENOM_API int prenom_set_loss_scale(prenom_ctx *ctx, int32_t obj, float scale, int32_t growth_interval);
 
 /* Total kernel launches made by the library on this context. */
 PRENOM_API int prenom_launch_count(prenom_ctx *ctx, int64_t *launches);

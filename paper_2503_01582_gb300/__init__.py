@@ -16,6 +16,11 @@ from __future__ import annotations
 from . import _abi
 from ._abi import (  # noqa: F401
     KERNEL_NAMES,
+    PRENOM_ERR_CUDA,
+    PRENOM_ERR_DEVICE_TIMEOUT,
+    PRENOM_ERR_INVALID_ARG,
+    PRENOM_ERR_NONFINITE,
+    PRENOM_ERR_OOM,
     PRENOM_FLAG_CHECK_FINITE,
     PRENOM_FLAG_FUSED,
     PRENOM_FLAG_SPLIT,
@@ -198,6 +203,24 @@ class Context:
     def loss_scale(self, obj: int):
         """(current loss scale, steps dropped after a 16-bit overflow)."""
         return _abi.prenom_get_loss_scale(self._ctx, obj)
+
+    def set_loss_scale(self, obj: int, scale: float, growth_interval: int = 1000):
+        """Sets a mixed-precision object's loss scale and the clean steps after which it doubles."""
+        _abi.prenom_set_loss_scale(self._ctx, obj, scale, growth_interval)
+
+    def autotune(self, batches, opts: prenom_train_opts):
+        """Runs the autotuner's calls for these batches (no Adam, state left as it was) and
+        captures the step graphs, so that the following train_step calls only replay."""
+        _abi.prenom_autotune(self._ctx, [ray_batch(b) for b in batches], opts)
+
+    def capture_count(self):
+        """(step graphs captured, steps run as autotuner measurements) so far."""
+        return _abi.prenom_capture_count(self._ctx)
+
+    def timing_report(self):
+        """Per-group kernel times of the batched steps timed since enable_timing:
+        list of (group label, kernel id, total ms, launches)."""
+        return _abi.prenom_timing_report(self._ctx)
 
     def zero_grads(self, obj: int):
         _abi.prenom_zero_grads(self._ctx, obj)

@@ -117,6 +117,10 @@ _SIGS = {
     "prenom_kernel_time": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "prenom_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
     "prenom_get_loss_scale": (C.c_int, [_CTX, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
+    "prenom_set_loss_scale": (C.c_int, [_CTX, C.c_int32, C.c_float, C.c_int32]),
+    "prenom_autotune": (C.c_int, [_CTX, C.POINTER(prenom_ray_batch), C.c_int32, C.POINTER(prenom_train_opts)]),
+    "prenom_capture_count": (C.c_int, [_CTX, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "prenom_timing_report": (C.c_int, [_CTX, C.c_char_p, C.c_size_t]),
     "prenom_train_step_noalloc": (C.c_int, [C.POINTER(prenom_arch), _P, _P, _P, C.c_int32, _P, C.c_int32,
                                             C.POINTER(prenom_ray_batch), C.POINTER(prenom_train_opts), _P, _P,
                                             C.c_uint64]),
@@ -333,3 +337,33 @@ def prenom_get_loss_scale(ctx, obj: int):
     n = C.c_int32()
     check(lib().prenom_get_loss_scale(ctx, obj, C.byref(s), C.byref(n)), ctx)
     return s.value, n.value
+
+
+def prenom_set_loss_scale(ctx, obj: int, scale: float, growth_interval: int = 1000):
+    """Loss scale and growth interval (clean steps before it doubles) of a mixed-precision object."""
+    check(lib().prenom_set_loss_scale(ctx, obj, scale, growth_interval), ctx)
+
+
+def prenom_autotune(ctx, batches, opts: prenom_train_opts):
+    """The autotuner's calls (gradient-only, cleaned up) and the step graphs, before training."""
+    arr = (prenom_ray_batch * max(len(batches), 1))(*batches)
+    check(lib().prenom_autotune(ctx, arr, len(batches), C.byref(opts)), ctx)
+
+
+def prenom_capture_count(ctx):
+    """(step graphs captured, steps run as autotuner measurements) so far."""
+    a = C.c_int64()
+    b = C.c_int64()
+    check(lib().prenom_capture_count(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def prenom_timing_report(ctx):
+    """Per-group kernel times of timed batched steps: list of (label, kernel id, total ms, launches)."""
+    buf = C.create_string_buffer(1 << 16)
+    check(lib().prenom_timing_report(ctx, buf, len(buf)), ctx)
+    out = []
+    for ln in buf.value.decode().splitlines():
+        label, k, ms, n = ln.split("\t")
+        out.append((label, int(k[1:]), float(ms), int(n)))
+    return out

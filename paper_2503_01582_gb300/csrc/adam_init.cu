@@ -133,21 +133,25 @@ cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_
 
 // ------------------------------------------------------ loss scaling
 // Dynamic loss scale of a mixed-precision object, run after its Adam step:
-// an overflow halves the scale (the step was dropped), 1000 clean steps in a
-// row double it (capped at 2^24).
-__global__ void loss_scale_update_kernel(LossScaleState *s)
+// an overflow halves the scale (the step was dropped), growth_interval clean
+// steps in a row double it (capped at 2^24).
+__device__ __forceinline__ void loss_scale_update(LossScaleState *s)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0)
-        return;
     if (s->overflow) {
         s->scale = fmaxf(s->scale * 0.5f, 1.f);
         s->good_steps = 0;
         s->skipped += 1;
         s->overflow = 0;
-    } else if (++s->good_steps >= 1000) {
+    } else if (++s->good_steps >= s->growth_interval) {
         s->scale = fminf(s->scale * 2.f, 16777216.f);
         s->good_steps = 0;
     }
+}
+
+__global__ void loss_scale_update_kernel(LossScaleState *s)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        loss_scale_update(s);
 }
 
 cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st)
@@ -160,18 +164,8 @@ cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st)
 __global__ void loss_scale_update_list_kernel(const ScaleList l)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= l.n)
-        return;
-    LossScaleState *s = l.s[i];
-    if (s->overflow) {
-        s->scale = fmaxf(s->scale * 0.5f, 1.f);
-        s->good_steps = 0;
-        s->skipped += 1;
-        s->overflow = 0;
-    } else if (++s->good_steps >= 1000) {
-        s->scale = fminf(s->scale * 2.f, 16777216.f);
-        s->good_steps = 0;
-    }
+    if (i < l.n)
+        loss_scale_update(l.s[i]);
 }
 
 cudaError_t launch_loss_scale_update_list(const ScaleList &l, cudaStream_t st)

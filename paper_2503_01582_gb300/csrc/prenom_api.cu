@@ -22,6 +22,7 @@ using namespace prenom;
 namespace {
 
 std::string g_create_error;
+constexpr int kScratchLosses = 64;  // device floats of prenom_ctx::scratch
 
 struct Object {
     bool alive = false;
@@ -40,6 +41,7 @@ struct Object {
 struct TimedEv {
     cudaEvent_t a, b;
     int kernel;
+    int group;  // index into prenom_ctx::group_names, or -1 outside a batched group
 };
 
 }  // namespace
@@ -59,6 +61,12 @@ struct prenom_ctx {
     double total_ms[PRENOM_N_KERNELS] = {};
     int64_t count[PRENOM_N_KERNELS] = {};
     int64_t launches = 0;
+    // timed batched steps: kernel times per (group, kernel id)
+    int cur_group = -1;
+    std::vector<std::string> group_names;
+    std::map<std::pair<int, int>, std::pair<double, int64_t>> group_time;
+    int64_t n_captures = 0;    // step graphs captured
+    int64_t n_tune_calls = 0;  // steps run as autotuner measurements
     // batched steps: device work list (+ per-object Adam factors behind it),
     // two pinned staging buffers, the graphs captured per step signature and
     // the autotuner's choice of tiles per CTA per group signature
@@ -234,7 +242,26 @@ void timed_end(prenom_ctx *c, int kernel, cudaEvent_t a)
     cudaEvent_t b = c->ev_free.back();
     c->ev_free.pop_back();
     cudaEventRecord(b, c->stream);
-    c->pending.push_back({a, b, kernel});
+    c->pending.push_back({a, b, kernel, c->cur_group});
+}
+
+// Adds the durations of all recorded event pairs to the totals (after the stream finished).
+void fold_pending(prenom_ctx *c)
+{
+    for (auto &p : c->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        c->total_ms[p.kernel] += ms;
+        c->count[p.kernel] += 1;
+        if (p.group >= 0) {
+            auto &g = c->group_time[{p.group, p.kernel}];
+            g.first += ms;
+            g.second += 1;
+        }
+        c->ev_free.push_back(p.a);
+        c->ev_free.push_back(p.b);
+    }
+    c->pending.clear();
 }
 
 ObjDesc make_objdesc(const Object &o, float *grad)
@@ -546,6 +573,26 @@ std::string tune_key(const Group &g)
     return buf;
 }
 
+// A group as the timing report names it: precision, widths, deepest MLP, batch
+// and tile counts, form and grid.
+std::string group_label(const Group &g)
+{
+    static const char *prec[] = {"fp32", "fp16", "bf16"};
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%s W%d IN%d H%d batches%d tiles%d %s grid%d", prec[g.precision], g.W, g.IN, g.hmax,
+             g.count, g.total_tiles, g.split ? "split" : "fused", g.grid);
+    return buf;
+}
+
+int group_index(prenom_ctx *c, const std::string &label)
+{
+    for (size_t i = 0; i < c->group_names.size(); ++i)
+        if (c->group_names[i] == label)
+            return (int)i;
+    c->group_names.push_back(label);
+    return (int)c->group_names.size() - 1;
+}
+
 int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const prenom_train_opts &op, float *loss_dev,
                  Plan &p)
 {
@@ -641,6 +688,7 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
             continue;
         const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax, g.split ? 1 : 0};
         cudaEvent_t ev;
+        c->cur_group = timed ? group_index(c, group_label(g)) : -1;
         if (g.split) {
             if (timed)
                 timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
@@ -666,6 +714,7 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
                 timed_end(c, PRENOM_KERNEL_SCATTER, ev);
         }
     }
+    c->cur_group = -1;
     if (e == cudaSuccess && p.adam_grid > 0) {
         AdamArgs a = p.adam;
         for (int s = 0; s < a.n_segs; ++s)
@@ -692,7 +741,10 @@ int launches_of(const Plan &p)
     return n;
 }
 
-int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const prenom_train_opts &op, float *loss_dev)
+// capture_only: build the step's graph for the current staging buffer and keep
+// it, without launching anything (the autotuner's set-up call).
+int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const prenom_train_opts &op, float *loss_dev,
+                  bool capture_only = false)
 {
     Plan p;
     int rc = plan_batched(c, batches, n, op, loss_dev, p);
@@ -771,7 +823,10 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         memcpy(c->h_stage[b] + items_bytes, p.adam_scal.data(), p.adam_scal.size() * sizeof(float2));
 
     const bool use_graph = !tuning && !c->timing && c->stream != nullptr && !(op.flags & PRENOM_FLAG_NO_GRAPH);
+    if (capture_only && !use_graph)
+        return PRENOM_OK;  // nothing to capture (still tuning, timing on, legacy stream or graphs off)
     if (tuning) {
+        c->n_tune_calls++;
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0);
         cudaEventCreate(&t1);
@@ -829,6 +884,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
                 cudaGraphDestroy(graph);
             if (e != cudaSuccess)
                 return cuda_fail(c, e, "batched step graph capture");
+            c->n_captures++;
             if (c->graphs.size() >= kMaxGraphs) {  // evict the least recently used signature
                 auto old = c->graphs.begin();
                 for (auto g = c->graphs.begin(); g != c->graphs.end(); ++g)
@@ -841,6 +897,10 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
             it = c->graphs.emplace(key, prenom_ctx::CachedGraph{exec, 0}).first;
         }
         it->second.last_use = ++c->graph_tick;
+        if (capture_only) {  // kept for the step that will use this staging buffer
+            c->stage_idx ^= 1;
+            return PRENOM_OK;
+        }
         e = cudaGraphLaunch(it->second.exec, c->stream);
     } else {
         const int64_t before = c->launches;  // timed launches count themselves; the total is set below
@@ -857,6 +917,22 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         for (int32_t id : p.touched)
             c->objs[id].step += 1;
     return PRENOM_OK;
+}
+
+// Whether some group signature of this step still has autotuner calls ahead.
+bool tuning_pending(prenom_ctx *c, const prenom_ray_batch *batches, int n, const prenom_train_opts &op, int *rc)
+{
+    Plan p;
+    *rc = plan_batched(c, batches, n, op, nullptr, p);
+    if (*rc)
+        return false;
+    const bool split_allowed = !(op.flags & PRENOM_FLAG_FUSED);
+    if (split_allowed && (op.flags & PRENOM_FLAG_SPLIT))
+        return false;
+    for (const Group &g : p.groups)
+        if (!c->tune_best.count(tune_key(g) + (split_allowed ? "/s" : "/f")))
+            return true;
+    return false;
 }
 
 }  // namespace
@@ -925,7 +1001,7 @@ int prenom_create(prenom_ctx **out, void *cuda_stream, uint64_t seed)
         }
     }
     if (e == cudaSuccess)
-        e = cudaMalloc(&c->scratch, 64 * sizeof(float));
+        e = cudaMalloc(&c->scratch, kScratchLosses * sizeof(float));
     if (e == cudaSuccess)
         e = cudaMalloc(&c->status, 4 * sizeof(int32_t));
     if (e == cudaSuccess)
@@ -1019,7 +1095,7 @@ int prenom_create_object(prenom_ctx *c, const prenom_arch *arch, const float *in
     if (e == cudaSuccess && arch->precision != PRENOM_PRECISION_FP32) {
         e = cudaMalloc(&o.lss, sizeof(LossScaleState));
         if (e == cudaSuccess) {
-            const LossScaleState init{arch->precision == PRENOM_PRECISION_FP16 ? 32768.f : 1.f, 0, 0, 0};
+            const LossScaleState init{arch->precision == PRENOM_PRECISION_FP16 ? 32768.f : 1.f, 0, 0, 0, kLossScaleGrowth};
             e = cudaMemcpyAsync(o.lss, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
         }
     }
@@ -1137,6 +1213,15 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
     }
     if (n_batches > 0 && !(op->flags & PRENOM_FLAG_CHECK_FINITE))
         return train_batched(c, batches, n_batches, *op, loss_dev);
+    // the finiteness check reads every batch's loss: without loss_dev they go to
+    // the context's scratch slots
+    const bool check = (op->flags & PRENOM_FLAG_CHECK_FINITE) && n_batches > 0;
+    if (check && !loss_dev) {
+        if (n_batches > kScratchLosses)
+            return fail(c, PRENOM_ERR_INVALID_ARG, "PRENOM_FLAG_CHECK_FINITE with more than %d batches needs loss_dev",
+                        kScratchLosses);
+        loss_dev = c->scratch;
+    }
     if (loss_dev && n_batches > 0) {
         const cudaError_t e = cudaMemsetAsync(loss_dev, 0, (size_t)n_batches * sizeof(float), c->stream);
         if (e != cudaSuccess)
@@ -1154,7 +1239,7 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
         if (std::find(touched.begin(), touched.end(), b.obj) == touched.end())
             touched.push_back(b.obj);
     }
-    if ((op->flags & PRENOM_FLAG_CHECK_FINITE) && loss_dev && n_batches > 0) {
+    if (check) {
         std::vector<float> h(n_batches);
         const cudaError_t e = cudaMemcpyAsync(h.data(), loss_dev, h.size() * sizeof(float), cudaMemcpyDeviceToHost,
                                               c->stream);
@@ -1170,6 +1255,52 @@ int prenom_train_step(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_
     if (op->flags & PRENOM_FLAG_NO_ADAM)
         return PRENOM_OK;
     return run_adam(c, touched, *op);
+}
+
+int prenom_autotune(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_batches, const prenom_train_opts *op)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_batches < 0 || (n_batches > 0 && !batches))
+        return fail(c, PRENOM_ERR_INVALID_ARG, "bad batch list");
+    int rc = check_opts(c, op, true);
+    if (rc)
+        return rc;
+    for (int i = 0; i < n_batches; ++i)
+        if ((rc = check_batch(c, batches[i], true)))
+            return rc;
+    if (n_batches == 0 || (op->flags & PRENOM_FLAG_CHECK_FINITE))
+        return PRENOM_OK;  // such steps are neither tuned nor captured
+    // the autotuner's calls, as gradient-only steps (no Adam, no step count)
+    prenom_train_opts t = *op;
+    t.flags |= PRENOM_FLAG_NO_ADAM;
+    for (int i = 0; i < 2 + kTuneN * kTuneRounds; ++i) {
+        const bool pending = tuning_pending(c, batches, n_batches, t, &rc);
+        if (rc)
+            return rc;
+        if (!pending)
+            break;
+        if ((rc = train_batched(c, batches, n_batches, t, nullptr)))
+            return rc;
+    }
+    // undo what those calls left behind: accumulated gradients, overflow flags
+    std::set<int32_t> seen;
+    for (int i = 0; i < n_batches; ++i) {
+        Object &o = c->objs[batches[i].obj];
+        if (!seen.insert(batches[i].obj).second)
+            continue;
+        cudaError_t e = cudaMemsetAsync(o.grad, 0, (size_t)o.n * sizeof(float), c->stream);
+        if (e == cudaSuccess && o.lss)
+            e = cudaMemsetAsync(&o.lss->overflow, 0, sizeof(int32_t), c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "autotune clean-up");
+    }
+    // the step's graphs, one per staging buffer, captured now and launched by later steps
+    for (int i = 0; i < 2; ++i)
+        if ((rc = train_batched(c, batches, n_batches, *op, nullptr, true)))
+            return rc;
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "autotune");
 }
 
 int prenom_render(prenom_ctx *c, const prenom_ray_batch *b, const prenom_train_opts *op, float *rgb, float *depth,
@@ -1617,7 +1748,7 @@ int prenom_get_loss_scale(prenom_ctx *c, int32_t obj, float *scale, int32_t *dro
     Object *o = get_obj(c, obj);
     if (!o)
         return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
-    LossScaleState s{1.f, 0, 0, 0};
+    LossScaleState s{1.f, 0, 0, 0, kLossScaleGrowth};
     if (o->lss) {
         cudaError_t e = cudaMemcpyAsync(&s, o->lss, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess)
@@ -1646,6 +1777,7 @@ int prenom_enable_timing(prenom_ctx *c, int32_t enable)
         c->total_ms[k] = 0.0;
         c->count[k] = 0;
     }
+    c->group_time.clear();
     c->timing = enable != 0;
     return PRENOM_OK;
 }
@@ -1657,19 +1789,63 @@ int prenom_kernel_time(prenom_ctx *c, int32_t kernel, double *total_ms, int64_t 
     const cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess)
         return cuda_fail(c, e, "stream");
-    for (auto &p : c->pending) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, p.a, p.b);
-        c->total_ms[p.kernel] += ms;
-        c->count[p.kernel] += 1;
-        c->ev_free.push_back(p.a);
-        c->ev_free.push_back(p.b);
-    }
-    c->pending.clear();
+    fold_pending(c);
     if (total_ms)
         *total_ms = c->total_ms[kernel];
     if (launches)
         *launches = c->count[kernel];
+    return PRENOM_OK;
+}
+
+int prenom_capture_count(prenom_ctx *c, int64_t *captures, int64_t *tuning_calls)
+{
+    if (!c)
+        return fail(nullptr, PRENOM_ERR_INVALID_ARG, "ctx is NULL");
+    if (captures)
+        *captures = c->n_captures;
+    if (tuning_calls)
+        *tuning_calls = c->n_tune_calls;
+    return PRENOM_OK;
+}
+
+int prenom_set_loss_scale(prenom_ctx *c, int32_t obj, float scale, int32_t growth_interval)
+{
+    Object *o = get_obj(c, obj);
+    if (!o)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
+    if (!o->lss)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "object %d is FP32: it has no loss scale", obj);
+    if (!(scale >= 1.f && scale <= 16777216.f) || growth_interval < 1)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "scale must be in [1, 2^24] and growth_interval >= 1");
+    const int32_t v[2] = {0, growth_interval};  // good_steps restarts, then the interval
+    cudaError_t e = cudaMemcpyAsync(&o->lss->scale, &scale, sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&o->lss->good_steps, &v[0], sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&o->lss->growth_interval, &v[1], sizeof(int32_t), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "loss-scale write");
+}
+
+int prenom_timing_report(prenom_ctx *c, char *buf, size_t cap)
+{
+    if (!c || !buf || cap == 0)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "ctx, buf and cap are required");
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(c, e, "stream");
+    fold_pending(c);
+    std::string r;
+    for (const auto &kv : c->group_time) {
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp), "%s\tk%d\t%.6f\t%lld\n", c->group_names[kv.first.first].c_str(), kv.first.second,
+                 kv.second.first, (long long)kv.second.second);
+        r += tmp;
+    }
+    const size_t n = std::min(cap - 1, r.size());
+    memcpy(buf, r.data(), n);
+    buf[n] = 0;
     return PRENOM_OK;
 }
 

@@ -77,7 +77,9 @@ struct LossScaleState {
     int32_t good_steps;
     int32_t overflow;
     int32_t skipped;
+    int32_t growth_interval;  // clean steps in a row after which the scale doubles
 };
+constexpr int32_t kLossScaleGrowth = 1000;  // default growth interval
 
 struct WorkItem;
 struct WorkList;

@@ -1,6 +1,7 @@
 """Host-side logic of bench.py and of the oracle's marshalling, on the CPU: the
-packed host batches of the end-to-end loop, the DRAM-traffic record's source
-check, and the oracle's refusal of arrays of the wrong size."""
+packed host ray sets of the end-to-end loop, the 32-object workload, the
+oracle timing's extrapolation, the DRAM-traffic record's source check, and
+the oracle's refusal of arrays of the wrong size."""
 
 import hashlib
 import json
@@ -21,33 +22,48 @@ def bench():
     return importlib.import_module("bench")
 
 
-def test_packed_batches_round_trip(bench, monkeypatch):
+def test_packed_sets_round_trip(bench, monkeypatch):
     import torch
 
     monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)  # no CUDA here
     rng = np.random.default_rng(0)
-    batches = [dict(o=rng.random((7, 3), np.float32), d=rng.random((7, 3), np.float32),
-                    is_obj=rng.integers(0, 2, 7).astype(np.uint8), uniforms=rng.random((7, 5), np.float32))
-               for _ in range(3)]
-    blocks, layout = bench._pack_batches(batches)
-    assert len(blocks) == 3 and all(b.numel() == blocks[0].numel() for b in blocks)
-    assert all(off % 256 == 0 for _, off, _, _ in layout)  # every array starts on a 256-byte boundary
-    for blk, b in zip(blocks, batches):
-        got = bench._unpack(blk, layout)
-        assert set(got) == set(b)
-        for k in b:
-            assert got[k].dtype == {np.float32: torch.float32, np.uint8: torch.uint8}[b[k].dtype.type]
-            np.testing.assert_array_equal(got[k].numpy(), b[k])
+
+    def batch(n):
+        return dict(o=rng.random((n, 3), np.float32), d=rng.random((n, 3), np.float32),
+                    is_obj=rng.integers(0, 2, n).astype(np.uint8), uniforms=rng.random((n, 5), np.float32))
+
+    sets = [[batch(7), batch(33), batch(1)] for _ in range(3)]  # objects of different ray counts
+    packed = [bench._pack(s) for s in sets]
+    layout = packed[0][1]
+    assert all(p[1] == layout for p in packed)  # sets of the same shapes share one layout
+    assert all(p[0].numel() == packed[0][0].numel() for p in packed)
+    assert all(off % 256 == 0 for ent in layout for _, off, _, _ in ent)  # 256-byte aligned arrays
+    for (blk, _), s in zip(packed, sets):
+        for ent, b in zip(layout, s):
+            got = bench._unpack(blk, ent)
+            assert set(got) == set(b)
+            for k in b:
+                assert got[k].dtype == {np.float32: torch.float32, np.uint8: torch.uint8}[b[k].dtype.type]
+                np.testing.assert_array_equal(got[k].numpy(), b[k])
 
 
-def test_packed_batches_reject_a_different_shape(bench, monkeypatch):
-    import torch
+def test_batched_workload_specs(bench):
+    """The 32 objects: the category table in order, rays 32 round(8 2^(5a)) in 256..8192."""
+    specs = bench.batched_specs()
+    assert len(specs) == 32
+    for i, sp in enumerate(specs):
+        assert (sp["log2T"], sp["W"], sp["H"]) == bench.CATEGORY_ARCHS[i % 9]
+        assert sp["rays"] % 32 == 0 and 256 <= sp["rays"] <= 8192
+    samples, rays = bench.batched_totals(specs)
+    assert samples == 48 * rays
 
-    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
-    a = dict(o=np.zeros((4, 3), np.float32))
-    b = dict(o=np.zeros((5, 3), np.float32))
-    with pytest.raises(AssertionError):
-        bench._pack_batches([a, b])
+
+def test_oracle_step_extrapolation(bench):
+    specs = bench.batched_specs()
+    per = {i: (16, 0.5) for i in range(32)}  # every object: 16 rays in 0.5 s
+    rays = sum(sp["rays"] for sp in specs)
+    assert abs(bench.oracle_step_seconds(per, 1, 2.0) - (rays * 0.5 / 16 + 2.0)) < 1e-9
+    assert abs(bench.oracle_step_seconds(per, 4, 2.0) - (rays * 0.5 / 16 / 4 + 2.0)) < 1e-9
 
 
 def test_traffic_record_follows_its_sources(bench, tmp_path, monkeypatch):

@@ -309,6 +309,62 @@ def test_render_backward_matches_oracle(pkg):
     ctx.close()
 
 
+def test_autograd_render_matches_central_differences(pkg):
+    """The GPU backward through torch.autograd against central differences of
+    the GPU forward itself (FP32), on the L = 4, T = 2^12 architecture: for the
+    hash entries and MLP weights with the largest gradients, (f(theta + h e_i) -
+    f(theta - h e_i)) / 2h with h = 1e-2 max(|theta_i|, 0.1) agrees with the
+    analytic gradient to 1e-2.  Entries are kept only where the oracle's own
+    central difference at the same points (FP64) matches the oracle's analytic
+    gradient to 2e-3, so that the step h does not cross a ReLU or cell kink."""
+    import torch
+
+    from paper_2503_01582_gb300.autograd import render
+
+    arch = dict(L=4, F=2, log2T=12, n_min=4, n_max=32, width=16, hidden=2, lambda_d=0.1, lambda_sigma=0.0)
+    a, theta, grid, rays, u, cr = case(arch, 32, 16, 16, seed=101, hash_range=0.5)
+    t_in = oracle_t(grid, rays, u, 16, 16)
+    up = np.random.default_rng(7).normal(size=(32, 5)).astype(np.float32)
+    ctx, obj = _setup(pkg, arch, theta, grid)
+    batch = _dev(rays, obj, t_in=t_in)
+    opts = pkg.make_opts(nc=16, nr=16)
+    upt = torch.from_numpy(up).cuda()
+
+    def f_gpu(th):
+        rgb, depth, acc = render(ctx, obj, th, batch, opts)
+        return (rgb * upt[:, :3]).sum() + (depth * upt[:, 3]).sum() + (acc * upt[:, 4]).sum()
+
+    th = torch.from_numpy(theta.astype(np.float32)).cuda().requires_grad_(True)
+    f_gpu(th).backward()
+    g = th.grad.cpu().numpy().astype(np.float64)
+
+    def f_orc(tt):
+        return orc.batch(a, tt, grid, rays, 16, 16, t_in=t_in, upstream=up, want_samples=False)["loss"]
+
+    g64 = orc.batch(a, theta.astype(np.float64), grid, rays, 16, 16, t_in=t_in, upstream=up, want_grad=True)["grad"]
+    nh = orc.n_hash_params(a)
+    cand = np.concatenate([np.argsort(-np.abs(g64[:nh]))[:40], nh + np.argsort(-np.abs(g64[nh:]))[:40]])
+    kept, bad = 0, []
+    th0 = theta.astype(np.float32)
+    with torch.no_grad():
+        for i in cand:
+            h = np.float32(1e-2 * max(abs(float(th0[i])), 0.1))
+            hi, lo = th0.copy(), th0.copy()
+            hi[i] = th0[i] + h
+            lo[i] = th0[i] - h
+            den = float(hi[i]) - float(lo[i])  # the FP32 points both sides evaluate
+            fd64 = (f_orc(hi.astype(np.float64)) - f_orc(lo.astype(np.float64))) / den
+            if abs(fd64 - g64[i]) > 2e-3 * abs(g64[i]):
+                continue  # a kink inside [theta_i - h, theta_i + h]
+            kept += 1
+            fd = (float(f_gpu(torch.from_numpy(hi).cuda())) - float(f_gpu(torch.from_numpy(lo).cuda()))) / den
+            if abs(fd - g[i]) > 1e-2 * abs(g[i]) + 1e-6 * np.abs(g).max():
+                bad.append((int(i), fd, g[i]))
+    assert kept >= 40, kept
+    assert not bad, bad
+    ctx.close()
+
+
 def test_philox_draws_match_oracle(pkg):
     import torch
 
