@@ -855,6 +855,9 @@ def run_ours(args):
             torch.distributed.barrier()
 
     stream = torch.cuda.Stream()
+    # every torch op of the bench runs on the library's stream: inputs made here
+    # are ordered before the steps that read them, and freed only after them
+    torch.cuda.set_stream(stream)
     ctx = pkg.Context(seed=rank, stream=stream)
     prec = args.precision
     form_flags = {"auto": 0, "fused": pkg.PRENOM_FLAG_FUSED, "split": pkg.PRENOM_FLAG_SPLIT}[args.form]

@@ -95,8 +95,35 @@ def ray_batch(b: dict) -> prenom_ray_batch:
     )
 
 
+def _stream_ordered(method):
+    """Orders a call's work with torch's current stream: the library's stream
+    first waits for the work already queued on the current stream (the call's
+    input tensors), and the current stream then waits for the call's work (its
+    output tensors), so tensors can be made and read on either stream.  When the
+    current stream is the context's own stream both waits are skipped."""
+    import functools
+
+    @functools.wraps(method)
+    def call(self, *a, **k):
+        import torch
+
+        cur = torch.cuda.current_stream()
+        other = cur != self.stream
+        if other:
+            self.stream.wait_stream(cur)
+        out = method(self, *a, **k)
+        if other:
+            cur.wait_stream(self.stream)
+        return out
+
+    return call
+
+
 class Context:
-    """One library context on the current CUDA device and a torch stream."""
+    """One library context on the current CUDA device and a torch stream.
+    Every call that launches work is ordered with torch's current stream (see
+    _stream_ordered); a loop run under `torch.cuda.stream(context.stream)` skips
+    those waits."""
 
     def __init__(self, seed: int = 0, stream=None):
         import torch
@@ -117,6 +144,7 @@ class Context:
             pass
 
     # ---- objects ----
+    @_stream_ordered
     def create_object(self, arch: prenom_arch, init_params=None) -> int:
         """init_params: None (random), a CUDA float32 tensor or a numpy float32 array."""
         ptr = 0
@@ -143,6 +171,7 @@ class Context:
     def level_info(self, obj: int):
         return _abi.prenom_level_info(self._ctx, obj, self._archs[obj].L)
 
+    @_stream_ordered
     def set_prior_grid(self, obj: int, grid):
         import numpy as np
 
@@ -154,10 +183,12 @@ class Context:
             _abi.prenom_set_prior_grid(self._ctx, obj, _dptr(grid, None, "grid"), int(grid.shape[0]))
 
     # ---- steps ----
+    @_stream_ordered
     def train_step(self, batches, opts: prenom_train_opts, loss=None):
         cb = [ray_batch(b) for b in batches]
         _abi.prenom_train_step(self._ctx, cb, opts, _dptr(loss, None, "loss"))
 
+    @_stream_ordered
     def render(self, batch: dict, opts: prenom_train_opts, want_samples: bool = False):
         import torch
 
@@ -173,11 +204,13 @@ class Context:
                            out["t"].data_ptr() if want_samples else 0)
         return out
 
+    @_stream_ordered
     def render_backward(self, batch: dict, opts: prenom_train_opts, d_out, grad):
         _abi.prenom_render_backward(self._ctx, ray_batch(batch), opts, _dptr(d_out, None, "d_out"),
                                     _dptr(grad, None, "grad"))
 
     # ---- state ----
+    @_stream_ordered
     def get_state(self, obj: int, which: int = PRENOM_STATE_THETA):
         import torch
 
@@ -185,6 +218,7 @@ class Context:
         _abi.prenom_get_state(self._ctx, obj, which, t.data_ptr(), t.numel())
         return t
 
+    @_stream_ordered
     def set_state(self, obj: int, which: int, src):
         import numpy as np
 
@@ -208,6 +242,7 @@ class Context:
         """Sets a mixed-precision object's loss scale and the clean steps after which it doubles."""
         _abi.prenom_set_loss_scale(self._ctx, obj, scale, growth_interval)
 
+    @_stream_ordered
     def autotune(self, batches, opts: prenom_train_opts):
         """Runs the autotuner's calls for these batches (no Adam, state left as it was) and
         captures the step graphs, so that the following train_step calls only replay."""
@@ -222,6 +257,7 @@ class Context:
         list of (group label, kernel id, total ms, launches)."""
         return _abi.prenom_timing_report(self._ctx)
 
+    @_stream_ordered
     def zero_grads(self, obj: int):
         _abi.prenom_zero_grads(self._ctx, obj)
 
@@ -230,6 +266,7 @@ class Context:
         return _abi.prenom_tuning_report(self._ctx)
 
     # ---- training rays from RGB-D keyframes (§III-B "Training Data")
+    @_stream_ordered
     def make_rays(self, keyframes, state, n_rays: int, draws=None, count: bool = False):
         """Ray batch (dict of CUDA tensors: o, d, rgb, depth, is_obj) drawn from the
         keyframes' candidate pixels.  keyframes: dicts with CUDA tensors rgb (uint8
@@ -266,6 +303,7 @@ class Context:
         return (out, n) if count else out
 
     # ---- prior density grid (§III-A mesh generation, §III-B refresh) and Eq. 3
+    @_stream_ordered
     def density_grid(self, obj: int, res: int):
         """[res, res, res] (z, y, x) CUDA tensor: the field's density at the voxel centres."""
         import torch
@@ -274,10 +312,12 @@ class Context:
         _abi.prenom_density_grid(self._ctx, obj, res, out.data_ptr())
         return out
 
+    @_stream_ordered
     def refresh_prior(self, obj: int, res: int):
         """Replaces the object's prior grid by its own density at resolution res."""
         _abi.prenom_refresh_prior(self._ctx, obj, res)
 
+    @_stream_ordered
     def canonical_yaw(self, obj: int, points, n_gamma: int):
         """Eq. 3 with the object's prior grid: (best yaw index, scores [n_gamma])."""
         import torch
@@ -288,18 +328,22 @@ class Context:
         return best, scores
 
     # ---- Reptile meta step (§III-A, Eq. 1-2)
+    @_stream_ordered
     def reptile_begin(self, meta: int, tasks):
         """Every task object <- the meta object's parameters, fresh Adam state."""
         _abi.prenom_reptile_begin(self._ctx, meta, list(tasks))
 
+    @_stream_ordered
     def reptile_update(self, meta: int, tasks, beta: float):
         """theta_meta <- theta_meta + beta (mean of the tasks' parameters - theta_meta)."""
         _abi.prenom_reptile_update(self._ctx, meta, list(tasks), beta)
 
+    @_stream_ordered
     def reptile_task_sum(self, tasks, out):
         """out (CUDA float32, param_count) <- sum of the tasks' parameters."""
         _abi.prenom_reptile_task_sum(self._ctx, list(tasks), _dptr(out, name="out"))
 
+    @_stream_ordered
     def reptile_apply(self, meta: int, task_sum, n_total: int, beta: float):
         """theta_meta <- theta_meta + beta (task_sum / n_total - theta_meta)."""
         _abi.prenom_reptile_apply(self._ctx, meta, _dptr(task_sum, name="task_sum"), n_total, beta)

@@ -21,9 +21,19 @@ __device__ __forceinline__ void adam_one(float &th, float &m, float &v, float g,
     th -= lr_c1 * m / (sqrtf(v * inv_c2) + eps);
 }
 
+// max |x| of a warp into *dst (non-negative floats order like their bit patterns)
+__device__ __forceinline__ void warp_absmax_to(uint32_t *dst, float amax)
+{
+    const uint32_t m = __reduce_max_sync(kFull, __float_as_uint(amax));
+    if ((threadIdx.x & 31) == 0 && m != 0u)
+        atomicMax(dst, m);
+}
+
 __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
 {
     const int64_t total = a.chunk_start[a.n_segs];
+    int cur = -1;       // segment whose updated hash entries amax covers (block-uniform)
+    float amax = 0.f;   // this thread's max |theta| over them
     for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
         int lo = 0, hi = a.n_segs - 1;
         while (lo < hi) {  // last segment whose first chunk is <= c
@@ -34,6 +44,12 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
                 hi = mid - 1;
         }
         const AdamSeg &sg = a.seg[lo];
+        if (lo != cur) {
+            if (cur >= 0 && a.seg[cur].absmax)
+                warp_absmax_to(a.seg[cur].absmax, amax);
+            cur = lo;
+            amax = 0.f;
+        }
         const int64_t base = (c - a.chunk_start[lo]) * kAdamChunk;
         const int64_t end = min(base + (int64_t)kAdamChunk, sg.n);
         if (sg.skip && *sg.skip) {  // a 16-bit gradient overflowed: drop the step, clear the gradients
@@ -47,6 +63,7 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
             lr_c1 = s.x;
             inv_c2 = s.y;
         }
+        const int64_t n_hash = sg.absmax ? sg.n_hash : 0;  // a multiple of 4: quadruples never straddle it
         // one quadruple of each array per thread (a 1024-float chunk is one pass of 256 threads)
         for (int64_t i = base + threadIdx.x * 4; i < end; i += blockDim.x * 4) {
             if (i + 4 <= end) {
@@ -62,14 +79,20 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
                 __stcs(reinterpret_cast<float4 *>(sg.m + i), m);
                 __stcs(reinterpret_cast<float4 *>(sg.v + i), v);
                 *reinterpret_cast<float4 *>(sg.grad + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < n_hash)
+                    amax = fmaxf(amax, fmaxf(fmaxf(fabsf(th.x), fabsf(th.y)), fmaxf(fabsf(th.z), fabsf(th.w))));
             } else {
                 for (int64_t j = i; j < end; ++j) {
                     adam_one(sg.theta[j], sg.m[j], sg.v[j], sg.grad[j], a.beta1, a.beta2, a.eps, lr_c1, inv_c2);
                     sg.grad[j] = 0.f;
+                    if (j < n_hash)
+                        amax = fmaxf(amax, fabsf(sg.theta[j]));
                 }
             }
         }
     }
+    if (cur >= 0 && a.seg[cur].absmax)
+        warp_absmax_to(a.seg[cur].absmax, amax);
 }
 
 cudaError_t launch_adam(const AdamArgs &a, int grid, cudaStream_t st)
@@ -134,10 +157,22 @@ cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_
 // ------------------------------------------------------ loss scaling
 // Dynamic loss scale of a mixed-precision object, run after its Adam step:
 // an overflow halves the scale (the step was dropped), growth_interval clean
-// steps in a row double it (capped at 2^24).
+// steps in a row double it (capped at 2^24).  An FP16 object's encoding scale
+// then follows the largest hash entry that Adam left (unchanged when the step
+// was dropped, since theta was).
+__device__ __forceinline__ float enc_scale_for(uint32_t absmax_bits)
+{
+    const float a = __uint_as_float(absmax_bits);
+    if (!(a > 0.f) || !isfinite(a))
+        return a > 0.f ? 1.f : ldexpf(1.f, kEncMaxLog2);  // infinite entries: no scaling; all zero: any
+    const int k = ilogbf(kEncTarget / a);                  // floor(log2(kEncTarget / a))
+    return ldexpf(1.f, min(max(k, 0), kEncMaxLog2));
+}
+
 __device__ __forceinline__ void loss_scale_update(LossScaleState *s)
 {
-    if (s->overflow) {
+    const bool dropped = s->overflow != 0;
+    if (dropped) {
         s->scale = fmaxf(s->scale * 0.5f, 1.f);
         s->good_steps = 0;
         s->skipped += 1;
@@ -146,6 +181,39 @@ __device__ __forceinline__ void loss_scale_update(LossScaleState *s)
         s->scale = fminf(s->scale * 2.f, 16777216.f);
         s->good_steps = 0;
     }
+    if (s->enc_auto) {
+        if (!dropped)
+            s->enc_scale = enc_scale_for(s->hash_absmax);
+        s->hash_absmax = 0u;
+    }
+}
+
+// max |theta[0..n_hash)| into s->hash_absmax; enc_scale_set_kernel then derives enc_scale from it
+__global__ void __launch_bounds__(256) enc_absmax_kernel(const float *theta, int64_t n_hash, LossScaleState *s)
+{
+    float amax = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_hash; i += (int64_t)gridDim.x * blockDim.x)
+        amax = fmaxf(amax, fabsf(theta[i]));
+    warp_absmax_to(&s->hash_absmax, amax);
+}
+
+__global__ void enc_scale_set_kernel(LossScaleState *s)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && s->enc_auto) {
+        s->enc_scale = enc_scale_for(s->hash_absmax);
+        s->hash_absmax = 0u;
+    }
+}
+
+cudaError_t launch_enc_scale_refresh(const float *theta, int64_t n_hash, LossScaleState *s, int grid,
+                                     cudaStream_t st)
+{
+    enc_absmax_kernel<<<grid, 256, 0, st>>>(theta, n_hash, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    enc_scale_set_kernel<<<1, 32, 0, st>>>(s);
+    return cudaGetLastError();
 }
 
 __global__ void loss_scale_update_kernel(LossScaleState *s)

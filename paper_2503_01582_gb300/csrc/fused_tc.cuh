@@ -17,7 +17,11 @@
 // an M = 64 product, when its columns fit in the CTA's 256 (else it is summed
 // on the CUDA cores while the tensor cores form dH of the last hidden layer).
 // The backward gradients are multiplied by a loss scale before the 16-bit cast
-// (FP16 dynamic range) and divided by it in FP32 on the way out.
+// (FP16 dynamic range) and divided by it in FP32 on the way out.  Likewise an
+// FP16 object's encoding is multiplied by a power of two before its cast (so
+// that the small features of a freshly initialised table stay FP16 normals);
+// the first layer's products are divided by it in FP32 before the ReLU, and its
+// weight gradient on the way out.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -312,7 +316,7 @@ __device__ __forceinline__ void tc_load_object(const ObjDesc &od, unsigned char 
 template <int W, int IN>
 __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDesc &bd, uint32_t lane_base,
                                                 bool have_dw, bool tc_dwo, float (&dwo_acc)[8], float &loss_acc,
-                                                float inv_scale)
+                                                float inv_scale, float inv_enc)
 {
     constexpr int INP = TcLayout<W, IN>::INP;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -346,14 +350,15 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
         const int nin = l == 0 ? IN : W;
         const int nrow = l == H ? 4 : W;
         float *dst = gw + (l == 0 ? 0 : IN * W + (l - 1) * W * W);
+        const float f = l == 0 ? inv_scale * inv_enc : inv_scale;  // dW_0 was formed from the scaled encoding
         for (int c0 = half * 8; c0 < ncol; c0 += 16) {
             float v[8];
             tmem_ld8(lane_base + dw_col<W, IN>(l) + c0, v);
             const int row = 16 * quad + lane;
             if (lane < 16 && row < nrow && c0 < nin) {  // nin and c0 are multiples of 8: two aligned quads
                 float4 *p = reinterpret_cast<float4 *>(dst + row * nin + c0);
-                red_add_f4(p, v[0] * inv_scale, v[1] * inv_scale, v[2] * inv_scale, v[3] * inv_scale);
-                red_add_f4(p + 1, v[4] * inv_scale, v[5] * inv_scale, v[6] * inv_scale, v[7] * inv_scale);
+                red_add_f4(p, v[0] * f, v[1] * f, v[2] * f, v[3] * f);
+                red_add_f4(p + 1, v[4] * f, v[5] * f, v[6] * f, v[7] * f);
             }
         }
     }
@@ -435,6 +440,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     float dwo_acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dW_out entries of this thread's group
     float loss_acc = 0.f;
     float scale = 1.f, inv_scale = 1.f;
+    float enc = 1.f, inv_enc = 1.f;  // FP16: power of two applied to the encoding before its cast
 
     __shared__ __align__(16) WorkItem cur;  // the item being processed
     const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -454,7 +460,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             ++nk;
         if (nk != k) {  // entering another object: flush the previous one, load this one
             if (k >= 0)
-                tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, tc_dwo, dwo_acc, loss_acc, inv_scale);
+                tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, tc_dwo, dwo_acc, loss_acc, inv_scale,
+                                       inv_enc);
             __syncthreads();
             stage_item(list[nk], cur);
             tc_load_object<W, IN, BF16>(cur.od, Wt0, WtH, WtO);
@@ -463,6 +470,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             const BatchDesc &nb = cur.bd;
             scale = (nb.mode != kRender && nb.loss_scale) ? *nb.loss_scale : 1.f;
             inv_scale = 1.f / scale;
+            enc = nb.enc_scale ? *nb.enc_scale : 1.f;
+            inv_enc = 1.f / enc;  // exact: enc is a power of two
             tc_sync();
         }
         const ObjDesc &od = cur.od;
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                         e1 = fmaf(cs.wt[c], f[c].y, e1);
                     }
                     *reinterpret_cast<uint32_t *>(XA + il_off(s, 2 * l, INP)) =
-                        (uint32_t)Hf::bits(e0) | ((uint32_t)Hf::bits(e1) << 16);
+                        (uint32_t)Hf::bits(e0 * enc) | ((uint32_t)Hf::bits(e1 * enc) << 16);
                 }
                 for (int l = NL + part; l < INP / 2; l += 2)  // zero padding of a narrow encoding
                     *reinterpret_cast<uint32_t *>(XA + il_off(s, 2 * l, INP)) = 0u;
@@ -569,9 +578,14 @@ __global__ void __launch_bounds__(kThreads, 2)
             const bool done = mbar_poll(mbar, parity, bd.status);
             parity ^= 1u;
             // epilogue: relu -> 16-bit -> HA[l]; warp half h takes columns [h W/2, (h+1) W/2)
+            // (layer 0's products carry the encoding's scale, divided out here)
             {
                 float v[W / 2];
                 tmem_ld_cols<W / 2>(lane_base + half * (W / 2), v);
+                if (l == 0)
+#pragma unroll
+                    for (int c = 0; c < W / 2; ++c)
+                        v[c] *= inv_enc;
 #pragma unroll
                 for (int c0 = 0; c0 < W / 2; c0 += 8) {
                     const int col = half * (W / 2) + c0;
@@ -779,7 +793,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 
     if (k >= 0 && ok)
-        tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, tc_dwo, dwo_acc, loss_acc, inv_scale);
+        tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, tc_dwo, dwo_acc, loss_acc, inv_scale, inv_enc);
     tc_sync();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));

@@ -314,6 +314,8 @@ BatchDesc make_batchdesc(const prenom_ctx *c, const Object &o, const prenom_ray_
         d.loss_scale = &o.lss->scale;
         d.overflow = &o.lss->overflow;
     }
+    if (o.lss && o.arch.precision == PRENOM_PRECISION_FP16)
+        d.enc_scale = &o.lss->enc_scale;
     d.status = c->status;
     return d;
 }
@@ -456,6 +458,24 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
     return PRENOM_OK;
 }
 
+// Where Adam gathers max |hash entry| of an FP16 object (its encoding scale follows it).
+uint32_t *enc_absmax_ptr(const Object &o)
+{
+    return o.lss && o.arch.precision == PRENOM_PRECISION_FP16 ? &o.lss->hash_absmax : nullptr;
+}
+
+// Recomputes an FP16 object's encoding scale from its current hash tables
+// (after a write of theta that Adam did not make).
+int refresh_enc_scale(prenom_ctx *c, const Object &o)
+{
+    if (!enc_absmax_ptr(o))
+        return PRENOM_OK;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((o.n_hash + 1023) / 1024, (int64_t)c->n_sm * 8));
+    const cudaError_t e = launch_enc_scale_refresh(o.theta, o.n_hash, o.lss, grid, c->stream);
+    c->launches += 2;
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "encoding-scale refresh");
+}
+
 int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train_opts &op)
 {
     for (size_t first = 0; first < objs.size(); first += kMaxAdamSegs) {
@@ -480,6 +500,8 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
             s.lr_c1 = (float)((double)op.lr / c1);
             s.inv_c2 = (float)(1.0 / c2);
             s.skip = o.lss ? &o.lss->overflow : nullptr;
+            s.absmax = enc_absmax_ptr(o);
+            s.n_hash = o.n_hash;
             a.chunk_start[i - first + 1] = a.chunk_start[i - first] + (o.n + kAdamChunk - 1) / kAdamChunk;
         }
         const int64_t chunks = a.chunk_start[a.n_segs];
@@ -664,6 +686,8 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
             sg.v = o.v;
             sg.n = o.n;
             sg.skip = o.lss ? &o.lss->overflow : nullptr;
+            sg.absmax = enc_absmax_ptr(o);
+            sg.n_hash = o.n_hash;
             a.chunk_start[s + 1] = a.chunk_start[s] + (o.n + kAdamChunk - 1) / kAdamChunk;
             if (o.lss && p.scales.n < kMaxScaleObjs)
                 p.scales.s[p.scales.n++] = o.lss;
@@ -1095,10 +1119,13 @@ int prenom_create_object(prenom_ctx *c, const prenom_arch *arch, const float *in
     if (e == cudaSuccess && arch->precision != PRENOM_PRECISION_FP32) {
         e = cudaMalloc(&o.lss, sizeof(LossScaleState));
         if (e == cudaSuccess) {
-            const LossScaleState init{arch->precision == PRENOM_PRECISION_FP16 ? 32768.f : 1.f, 0, 0, 0, kLossScaleGrowth};
+            const bool fp16 = arch->precision == PRENOM_PRECISION_FP16;
+            const LossScaleState init{fp16 ? 32768.f : 1.f, 0, 0, 0, kLossScaleGrowth, fp16 ? 1 : 0, 1.f, 0u};
             e = cudaMemcpyAsync(o.lss, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
         }
     }
+    if (e == cudaSuccess && refresh_enc_scale(c, o) != PRENOM_OK)
+        e = cudaErrorLaunchFailure;
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -1373,6 +1400,8 @@ int prenom_set_state(prenom_ctx *c, int32_t obj, int32_t which, const float *src
     if (!o || !src || (size_t)o->n != n || !state_ptr(o, which))
         return fail(c, PRENOM_ERR_INVALID_ARG, "set_state: bad object, buffer, size or selector");
     cudaError_t e = cudaMemcpyAsync(state_ptr(o, which), src, n * sizeof(float), cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && which == PRENOM_STATE_THETA && refresh_enc_scale(c, *o) != PRENOM_OK)
+        return PRENOM_ERR_CUDA;
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "set_state");
@@ -1458,8 +1487,11 @@ int prenom_reptile_begin(prenom_ctx *c, int32_t meta, const int32_t *tasks, int3
     a.meta = m->theta;
     if ((rc = reptile_launch(c, a, kReptileBroadcast)))
         return rc;
-    for (int i = 0; i < n_tasks; ++i)
+    for (int i = 0; i < n_tasks; ++i) {
         c->objs[tasks[i]].step = 0;
+        if ((rc = refresh_enc_scale(c, c->objs[tasks[i]])))
+            return rc;
+    }
     return PRENOM_OK;
 }
 
@@ -1476,7 +1508,9 @@ int prenom_reptile_update(prenom_ctx *c, int32_t meta, const int32_t *tasks, int
     a.meta = m->theta;
     a.beta = beta;
     a.nf = (float)n_tasks;
-    return reptile_launch(c, a, kReptileSum);
+    if ((rc = reptile_launch(c, a, kReptileSum)))
+        return rc;
+    return refresh_enc_scale(c, *m);
 }
 
 int prenom_reptile_task_sum(prenom_ctx *c, const int32_t *tasks, int32_t n_tasks, float *sum)
@@ -1509,7 +1543,8 @@ int prenom_reptile_apply(prenom_ctx *c, int32_t meta, const float *sum, int32_t 
     a.sum = const_cast<float *>(sum);
     a.beta = beta;
     a.nf = (float)n_total;
-    return reptile_launch(c, a, kReptileApply);
+    const int rc = reptile_launch(c, a, kReptileApply);
+    return rc ? rc : refresh_enc_scale(c, *m);
 }
 
 // ------------------------------------------------- prior grid and Eq. 3
@@ -1748,7 +1783,7 @@ int prenom_get_loss_scale(prenom_ctx *c, int32_t obj, float *scale, int32_t *dro
     Object *o = get_obj(c, obj);
     if (!o)
         return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
-    LossScaleState s{1.f, 0, 0, 0, kLossScaleGrowth};
+    LossScaleState s{1.f, 0, 0, 0, kLossScaleGrowth, 0, 1.f, 0u};
     if (o->lss) {
         cudaError_t e = cudaMemcpyAsync(&s, o->lss, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess)

@@ -55,6 +55,8 @@ struct BatchDesc {
     // mixed-precision form only
     const float *loss_scale;  // device scalar multiplying dL/d(MLP output) before the 16-bit cast
     int32_t *overflow;        // device flag set when a scaled 16-bit gradient is not finite
+    const float *enc_scale;   // FP16: device power of two multiplying the encoding before its 16-bit cast
+                              // (divided out of the first layer's products in FP32); NULL = 1
     int32_t *status;          // device word: nonzero when a bounded wait gave up
     // split execution of a mixed-precision training step (all NULL otherwise):
     // the three kernels hand over these per-batch buffers
@@ -78,8 +80,17 @@ struct LossScaleState {
     int32_t overflow;
     int32_t skipped;
     int32_t growth_interval;  // clean steps in a row after which the scale doubles
+    // FP16 objects: the encoding is cast to FP16 as enc_scale * e, enc_scale = 2^k
+    // with k = floor(log2(kEncTarget / max |hash entry|)) in [0, kEncMaxLog2],
+    // so that it lies in FP16's normal range whatever the tables' magnitude
+    // (the encoding is a convex combination of entries: |e| <= max |entry|)
+    int32_t enc_auto;      // 1 for FP16 objects (else enc_scale stays 1)
+    float enc_scale;
+    uint32_t hash_absmax;  // bits of max |hash entry| gathered by the last pass over theta
 };
 constexpr int32_t kLossScaleGrowth = 1000;  // default growth interval
+constexpr float kEncTarget = 4096.f;        // largest scaled encoding, 16x below FP16's 65504
+constexpr int kEncMaxLog2 = 24;
 
 struct WorkItem;
 struct WorkList;
@@ -109,6 +120,10 @@ struct ScaleList {
     LossScaleState *s[kMaxScaleObjs];
 };
 cudaError_t launch_loss_scale_update_list(const ScaleList &l, cudaStream_t st);
+// enc_scale of an FP16 object from max |theta[0..n_hash)| (after any write of
+// theta other than Adam's, which gathers the maximum as it updates).
+cudaError_t launch_enc_scale_refresh(const float *theta, int64_t n_hash, LossScaleState *s, int grid,
+                                     cudaStream_t st);
 // Zeroes the loss accumulator of every item of a device work list.
 cudaError_t launch_zero_losses(const WorkItem *items, int n, cudaStream_t st);
 
@@ -149,6 +164,8 @@ struct AdamSeg {
     float inv_c2;    // 1 / (1 - beta2^t)
     const int32_t *skip;  // mixed precision: nonzero overflow flag = drop this step (NULL for FP32)
     const float2 *scal;   // device (lr_c1, inv_c2) of this step, or NULL to use the two fields above
+    uint32_t *absmax;     // FP16: max |updated theta| over [0, n_hash) gathered here (NULL = not gathered)
+    int64_t n_hash;
 };
 struct AdamArgs {
     int32_t n_segs;

@@ -118,3 +118,30 @@ def bins_match(gpu_bins, want_bins, cdf_rows, u, margin=1e-5):
                 ok = 0 <= b < cdf.size - 1 and cdf[b] - margin <= u[r, k] < cdf[b + 1] + margin
                 bad += int(not ok)
     return bad, near
+
+
+def grad_blocks(a, g, want):
+    """Cosine and relative L2 error of a gradient against the oracle's, per hash
+    level and per MLP matrix (blocks the oracle leaves at zero are skipped), so
+    that an error in a block of small entries is not hidden by the large ones."""
+    g = np.asarray(g, np.float64)
+    want = np.asarray(want, np.float64)
+    spans = [(f"level {l}", orc.level_offset(a, l), orc.level_offset(a, l + 1)) for l in range(a.L)]
+    spans += [(f"layer {k}", orc.mlp_offset(a, k), orc.mlp_offset(a, k + 1)) for k in range(a.hidden + 1)]
+    out = {}
+    for name, lo, hi in spans:
+        x, y = g[lo:hi], want[lo:hi]
+        ny = np.linalg.norm(y)
+        if ny == 0.0:
+            continue
+        nx = np.linalg.norm(x)
+        out[name] = (float(x @ y / (nx * ny)) if nx > 0 else 0.0, float(np.linalg.norm(x - y) / ny))
+    return out
+
+
+def worst_blocks(a, g, want):
+    """(smallest cosine, largest relative L2, the blocks they come from) over grad_blocks."""
+    b = grad_blocks(a, g, want)
+    kc = min(b, key=lambda k: b[k][0])
+    kl = max(b, key=lambda k: b[k][1])
+    return b[kc][0], b[kl][1], (kc, kl)

@@ -139,7 +139,7 @@ def test_check_finite_reports_a_nan_loss_and_skips_adam(pkg, with_loss):
 def test_autotune_leaves_the_state_and_the_loop_neither_tunes_nor_captures(pkg):
     import torch
 
-    ctx = pkg.Context(seed=9)
+    ctx = pkg.Context(seed=9, stream=torch.cuda.Stream())  # graphs need a stream of its own
     objs, batches = [], []
     for i, prec in enumerate((pkg.PRENOM_PRECISION_FP16, pkg.PRENOM_PRECISION_FP16, pkg.PRENOM_PRECISION_FP32)):
         _, theta, grid, rays, u, cr = case(CFG1, 96 + 64 * i, 32, 32, seed=81 + i, hash_range=0.5)
