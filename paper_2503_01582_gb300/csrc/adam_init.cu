@@ -158,18 +158,64 @@ cudaError_t launch_init_params(float *theta, int64_t n_hash, const int32_t *mlp_
 // Dynamic loss scale of a mixed-precision object, run after its Adam step:
 // an overflow halves the scale (the step was dropped), growth_interval clean
 // steps in a row double it (capped at 2^24).  An FP16 object's encoding scale
-// then follows the largest hash entry that Adam left (unchanged when the step
+// then follows the tables and weights that Adam left (unchanged when the step
 // was dropped, since theta was).
-__device__ __forceinline__ float enc_scale_for(uint32_t absmax_bits)
+__device__ __forceinline__ float enc_scale_for(uint32_t absmax_bits, float gain)
 {
-    const float a = __uint_as_float(absmax_bits);
-    if (!(a > 0.f) || !isfinite(a))
-        return a > 0.f ? 1.f : ldexpf(1.f, kEncMaxLog2);  // infinite entries: no scaling; all zero: any
-    const int k = ilogbf(kEncTarget / a);                  // floor(log2(kEncTarget / a))
-    return ldexpf(1.f, min(max(k, 0), kEncMaxLog2));
+    const float a = __uint_as_float(absmax_bits) * gain;
+    if (!(a > 0.f))
+        return ldexpf(1.f, kEncMaxLog2);  // an all-zero table: every scale is exact
+    if (!isfinite(a))
+        return 1.f;
+    const int k = ilogbf(kEncTarget / a);  // floor(log2(kEncTarget / a)); INT_MAX for an infinite ratio
+    return ldexpf(1.f, min(max(k, kEncMinLog2), kEncMaxLog2));
 }
 
-__device__ __forceinline__ void loss_scale_update(LossScaleState *s)
+// max(1, max_l prod_{j<=l} ||W_j||_inf) over the hidden layers (all threads of
+// the block call it and receive the value; one row per thread, width <= 128)
+__device__ float mlp_gain(const LossScaleState *s)
+{
+    __shared__ uint32_t red[32];
+    const float *w = s->mlp;
+    int in = s->in;
+    float cum = 1.f, gain = 1.f;
+    for (int l = 0; l < s->hidden; ++l) {
+        float rowsum = 0.f;
+        if ((int)threadIdx.x < s->width)
+            for (int c = 0; c < in; ++c)
+                rowsum += fabsf(w[threadIdx.x * in + c]);
+        const uint32_t m = __reduce_max_sync(kFull, __float_as_uint(rowsum));
+        if ((threadIdx.x & 31) == 0)
+            red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        uint32_t bm = 0u;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+            bm = max(bm, red[i]);
+        __syncthreads();
+        cum *= __uint_as_float(bm);
+        gain = fmaxf(gain, cum);
+        w += (size_t)s->width * in;
+        in = s->width;
+    }
+    return gain;
+}
+
+// The encoding scale from the gathered hash maximum and the weights (kept
+// when `keep`); the gathered maximum restarts for the next pass.
+__device__ void enc_update_block(LossScaleState *s, bool keep)
+{
+    if (!s->enc_auto)
+        return;
+    const float gain = mlp_gain(s);
+    if (threadIdx.x == 0) {
+        if (!keep)
+            s->enc_scale = enc_scale_for(s->hash_absmax, gain);
+        s->hash_absmax = 0u;
+    }
+}
+
+// the scalar bookkeeping; returns whether the step was dropped
+__device__ __forceinline__ bool loss_scale_update(LossScaleState *s)
 {
     const bool dropped = s->overflow != 0;
     if (dropped) {
@@ -181,11 +227,36 @@ __device__ __forceinline__ void loss_scale_update(LossScaleState *s)
         s->scale = fminf(s->scale * 2.f, 16777216.f);
         s->good_steps = 0;
     }
-    if (s->enc_auto) {
-        if (!dropped)
-            s->enc_scale = enc_scale_for(s->hash_absmax);
-        s->hash_absmax = 0u;
-    }
+    return dropped;
+}
+
+constexpr int kScaleThreads = 128;  // one block per object: one MLP row per thread
+
+// the bookkeeping of every object of l, one block each (the single-object path passes a list of one)
+__global__ void __launch_bounds__(kScaleThreads) loss_scale_update_list_kernel(const ScaleList l)
+{
+    __shared__ int dropped;
+    LossScaleState *s = l.s[blockIdx.x];
+    if (threadIdx.x == 0)
+        dropped = loss_scale_update(s);
+    __syncthreads();
+    enc_update_block(s, dropped != 0);
+}
+
+cudaError_t launch_loss_scale_update_list(const ScaleList &l, cudaStream_t st)
+{
+    if (l.n <= 0)
+        return cudaSuccess;
+    loss_scale_update_list_kernel<<<l.n, kScaleThreads, 0, st>>>(l);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st)
+{
+    ScaleList l{};
+    l.n = 1;
+    l.s[0] = s;
+    return launch_loss_scale_update_list(l, st);
 }
 
 // max |theta[0..n_hash)| into s->hash_absmax; enc_scale_set_kernel then derives enc_scale from it
@@ -197,12 +268,9 @@ __global__ void __launch_bounds__(256) enc_absmax_kernel(const float *theta, int
     warp_absmax_to(&s->hash_absmax, amax);
 }
 
-__global__ void enc_scale_set_kernel(LossScaleState *s)
+__global__ void __launch_bounds__(kScaleThreads) enc_scale_set_kernel(LossScaleState *s)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0 && s->enc_auto) {
-        s->enc_scale = enc_scale_for(s->hash_absmax);
-        s->hash_absmax = 0u;
-    }
+    enc_update_block(s, false);
 }
 
 cudaError_t launch_enc_scale_refresh(const float *theta, int64_t n_hash, LossScaleState *s, int grid,
@@ -212,35 +280,7 @@ cudaError_t launch_enc_scale_refresh(const float *theta, int64_t n_hash, LossSca
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    enc_scale_set_kernel<<<1, 32, 0, st>>>(s);
-    return cudaGetLastError();
-}
-
-__global__ void loss_scale_update_kernel(LossScaleState *s)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0)
-        loss_scale_update(s);
-}
-
-cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st)
-{
-    loss_scale_update_kernel<<<1, 32, 0, st>>>(s);
-    return cudaGetLastError();
-}
-
-// The same bookkeeping for every mixed-precision object of a batched step.
-__global__ void loss_scale_update_list_kernel(const ScaleList l)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < l.n)
-        loss_scale_update(l.s[i]);
-}
-
-cudaError_t launch_loss_scale_update_list(const ScaleList &l, cudaStream_t st)
-{
-    if (l.n <= 0)
-        return cudaSuccess;
-    loss_scale_update_list_kernel<<<(l.n + 127) / 128, 128, 0, st>>>(l);
+    enc_scale_set_kernel<<<1, kScaleThreads, 0, st>>>(s);
     return cudaGetLastError();
 }
 

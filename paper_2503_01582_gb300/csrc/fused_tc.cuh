@@ -18,10 +18,12 @@
 // on the CUDA cores while the tensor cores form dH of the last hidden layer).
 // The backward gradients are multiplied by a loss scale before the 16-bit cast
 // (FP16 dynamic range) and divided by it in FP32 on the way out.  Likewise an
-// FP16 object's encoding is multiplied by a power of two before its cast (so
-// that the small features of a freshly initialised table stay FP16 normals);
-// the first layer's products are divided by it in FP32 before the ReLU, and its
-// weight gradient on the way out.
+// FP16 object's encoding is multiplied by a power of two 2^k before its cast, so
+// that the small features and activations of a freshly initialised object stay
+// FP16 normals: the layers have no biases and ReLU is positively homogeneous, so
+// every hidden activation carries the same factor, which the output layer's
+// FP32 products and every weight gradient divide out on the way out (dX does
+// not carry it).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -334,10 +336,9 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
         const int o = pair / (W / 8), i0 = (pair % (W / 8)) * 8;
         if (tid % SL == 0) {  // 16-byte reductions: the 304-way contention per address is per request
             float4 *p = reinterpret_cast<float4 *>(gw + IN * W + (H - 1) * W * W + o * W + i0);
-            red_add_f4(p, dwo_acc[0] * inv_scale, dwo_acc[1] * inv_scale, dwo_acc[2] * inv_scale,
-                       dwo_acc[3] * inv_scale);
-            red_add_f4(p + 1, dwo_acc[4] * inv_scale, dwo_acc[5] * inv_scale, dwo_acc[6] * inv_scale,
-                       dwo_acc[7] * inv_scale);
+            const float f = inv_scale * inv_enc;  // dO times the scaled activations
+            red_add_f4(p, dwo_acc[0] * f, dwo_acc[1] * f, dwo_acc[2] * f, dwo_acc[3] * f);
+            red_add_f4(p + 1, dwo_acc[4] * f, dwo_acc[5] * f, dwo_acc[6] * f, dwo_acc[7] * f);
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -350,7 +351,7 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
         const int nin = l == 0 ? IN : W;
         const int nrow = l == H ? 4 : W;
         float *dst = gw + (l == 0 ? 0 : IN * W + (l - 1) * W * W);
-        const float f = l == 0 ? inv_scale * inv_enc : inv_scale;  // dW_0 was formed from the scaled encoding
+        const float f = inv_scale * inv_enc;  // every dW was formed from scaled inputs of its layer
         for (int c0 = half * 8; c0 < ncol; c0 += 16) {
             float v[8];
             tmem_ld8(lane_base + dw_col<W, IN>(l) + c0, v);
@@ -578,14 +579,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             const bool done = mbar_poll(mbar, parity, bd.status);
             parity ^= 1u;
             // epilogue: relu -> 16-bit -> HA[l]; warp half h takes columns [h W/2, (h+1) W/2)
-            // (layer 0's products carry the encoding's scale, divided out here)
+            // (the activations keep the encoding's scale: the layers are linear up to ReLU)
             {
                 float v[W / 2];
                 tmem_ld_cols<W / 2>(lane_base + half * (W / 2), v);
-                if (l == 0)
-#pragma unroll
-                    for (int c = 0; c < W / 2; ++c)
-                        v[c] *= inv_enc;
 #pragma unroll
                 for (int c0 = 0; c0 < W / 2; c0 += 8) {
                     const int col = half * (W / 2) + c0;
@@ -613,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 tmem_ld4(lane_base, v);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    OT[c * SP + srow] = v[c];
+                    OT[c * SP + srow] = v[c] * inv_enc;  // the raw outputs without the encoding's scale
             }
             ok = tc_sync_and(done);
         }

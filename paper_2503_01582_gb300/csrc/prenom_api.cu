@@ -1120,7 +1120,8 @@ int prenom_create_object(prenom_ctx *c, const prenom_arch *arch, const float *in
         e = cudaMalloc(&o.lss, sizeof(LossScaleState));
         if (e == cudaSuccess) {
             const bool fp16 = arch->precision == PRENOM_PRECISION_FP16;
-            const LossScaleState init{fp16 ? 32768.f : 1.f, 0, 0, 0, kLossScaleGrowth, fp16 ? 1 : 0, 1.f, 0u};
+            const LossScaleState init{fp16 ? 32768.f : 1.f, 0, 0, 0, kLossScaleGrowth, fp16 ? 1 : 0, 1.f, 0u,
+                                      o.theta + o.n_hash, o.IN, arch->width, arch->hidden};
             e = cudaMemcpyAsync(o.lss, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
         }
     }
@@ -1783,7 +1784,7 @@ int prenom_get_loss_scale(prenom_ctx *c, int32_t obj, float *scale, int32_t *dro
     Object *o = get_obj(c, obj);
     if (!o)
         return fail(c, PRENOM_ERR_INVALID_ARG, "unknown object %d", obj);
-    LossScaleState s{1.f, 0, 0, 0, kLossScaleGrowth, 0, 1.f, 0u};
+    LossScaleState s{1.f, 0, 0, 0, kLossScaleGrowth, 0, 1.f, 0u, nullptr, 0, 0, 0};
     if (o->lss) {
         cudaError_t e = cudaMemcpyAsync(&s, o->lss, sizeof(s), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess)

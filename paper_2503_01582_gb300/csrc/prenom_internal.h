@@ -80,17 +80,22 @@ struct LossScaleState {
     int32_t overflow;
     int32_t skipped;
     int32_t growth_interval;  // clean steps in a row after which the scale doubles
-    // FP16 objects: the encoding is cast to FP16 as enc_scale * e, enc_scale = 2^k
-    // with k = floor(log2(kEncTarget / max |hash entry|)) in [0, kEncMaxLog2],
-    // so that it lies in FP16's normal range whatever the tables' magnitude
-    // (the encoding is a convex combination of entries: |e| <= max |entry|)
+    // FP16 objects: the encoding and with it every hidden activation (the layers
+    // have no biases, ReLU is positively homogeneous) are cast to FP16 scaled by
+    // enc_scale = 2^k, k = floor(log2(kEncTarget / (A G))) in [kEncMinLog2,
+    // kEncMaxLog2], A = max |hash entry| (the encoding is a convex combination of
+    // entries, so |e| <= A) and G = max(1, max_l prod_{j<=l} ||W_j||_inf) over the
+    // hidden layers (|h_l| <= |h_{l-1}|_max ||W_l||_inf): no scaled value exceeds
+    // kEncTarget, and the small values of a fresh object stay FP16 normals
     int32_t enc_auto;      // 1 for FP16 objects (else enc_scale stays 1)
     float enc_scale;
     uint32_t hash_absmax;  // bits of max |hash entry| gathered by the last pass over theta
+    const float *mlp;      // the object's MLP matrices in theta (W_1 [W][IN], W_2..W_H [W][W])
+    int32_t in, width, hidden;
 };
 constexpr int32_t kLossScaleGrowth = 1000;  // default growth interval
-constexpr float kEncTarget = 4096.f;        // largest scaled encoding, 16x below FP16's 65504
-constexpr int kEncMaxLog2 = 24;
+constexpr float kEncTarget = 32768.f;       // bound on every scaled value, half of FP16's 65504
+constexpr int kEncMinLog2 = -16, kEncMaxLog2 = 24;
 
 struct WorkItem;
 struct WorkList;

@@ -67,9 +67,13 @@ def _grad_metrics(g, want):
 
 def _check_blocks(a, g, want, precision, what=""):
     """The per-block bounds on every hash level and MLP matrix."""
+    from helpers import grad_blocks
+
     cos, l2, names = worst_blocks(a, g, want)
     b = BLOCK_BOUNDS[precision]
     print(f"  per block {what}: worst cos {cos:.6f} ({names[0]}), worst rel-L2 {l2:.2e} ({names[1]})")
+    print("   ", " ".join(f"{k.replace('level ', 'l').replace('layer ', 'W')}:{v[1]:.1e}"
+                          for k, v in grad_blocks(a, g, want).items()))
     assert cos >= b["cos"] and l2 <= b["l2"], (what, cos, l2, names)
 
 
@@ -101,9 +105,9 @@ def test_mixed_forward_and_gradients(pkg, arch, precision):
     e_loss = abs(loss.item() - want["loss"]) / abs(want["loss"])
     print(f"\nprecision={precision} W={arch['width']} H={arch['hidden']} L={arch['L']}: rgb abs {e_rgb:.2e} "
           f"depth {e_d:.2e} acc {e_a:.2e} loss {e_loss:.2e} grad cos {cos:.6f} rel-L2 {l2:.2e}")
+    _check_blocks(a, g, want["grad"], precision, f"W={arch['width']} H={arch['hidden']} L={arch['L']}")
     assert e_rgb <= bnd["rgb"] and e_d <= bnd["rel"] and e_a <= bnd["rel"] and e_loss <= bnd["rel"]
     assert cos >= bnd["cos"] and l2 <= bnd["l2"]
-    _check_blocks(a, g, want["grad"], precision, f"W={arch['width']} H={arch['hidden']} L={arch['L']}")
     ctx.close()
 
 
@@ -309,5 +313,5 @@ def test_split_form_against_oracle_full_size(pkg, hash_range):
     e_loss = abs(loss.item() - want["loss"]) / abs(want["loss"])
     print(f"\nfull size split FP16, hash range {hash_range}: loss {e_loss:.2e} grad cos {cos:.6f} rel-L2 {l2:.2e}")
     bnd = FULL_BOUNDS[hash_range]
-    assert e_loss <= bnd["rel"] and cos >= bnd["cos"] and l2 <= bnd["l2"]
     _check_blocks(a, g, want["grad"], 1, f"full size, hash range {hash_range}")
+    assert e_loss <= bnd["rel"] and cos >= bnd["cos"] and l2 <= bnd["l2"]
