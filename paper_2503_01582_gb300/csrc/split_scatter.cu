@@ -4,49 +4,55 @@
 
 namespace prenom {
 
-// The hash scatter of a work list from its dL/d(encoding) buffers.  Blocks walk
-// contiguous tile ranges; a tile's sample positions are staged in shared
-// memory once and each warp scatters one (level, 32 consecutive samples) at a
-// time, so a warp's lanes hold neighbouring samples of one level.
+// The hash scatter of a work list from its dL/d(encoding) buffers.  Blocks
+// take tiles round-robin (tile t goes to block t mod grid), so the tiles in
+// flight at any moment are a window of about one grid's worth of consecutive
+// tiles: one or two objects of a batched step, whose gradient tables then stay
+// in L2 while their reductions land (with contiguous ranges per block every
+// object of a group is in flight at once, and the tables of a group of larger
+// objects miss L2 on every reduction).  A tile's sample positions are staged in
+// shared memory, double-buffered with the tile's work item, so one block
+// barrier per tile suffices; each warp then scatters one (level, 32 consecutive
+// samples) at a time, so a warp's lanes hold neighbouring samples of one level.
 __global__ void __launch_bounds__(kThreads, 5)
     hash_scatter_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
-    __shared__ __align__(16) WorkItem cur;
-    __shared__ float s_p[6][kSplitTile];  // hi[3], lo[3] of each sample's position
+    __shared__ __align__(16) WorkItem cur[2];
+    __shared__ float s_p[2][6][kSplitTile];  // hi[3], lo[3] of each sample's position
     const WorkItem *list = wl.items ? wl.items : &one;
     const int n_items = wl.items ? wl.n_items : 1;
     const int total = wl.items ? wl.total_tiles : one.bd.n_tiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // contiguous tile ranges whose lengths differ by at most one
-    const int t0 = (int)((long long)blockIdx.x * total / gridDim.x);
-    const int t1 = (int)((long long)(blockIdx.x + 1) * total / gridDim.x);
-    int k = -1;
-    for (int t = t0; t < t1; ++t) {
-        int nk = k < 0 ? item_of_tile(list, n_items, t) : k;
-        while (nk + 1 < n_items && list[nk + 1].tile_begin <= t)
-            ++nk;
-        if (nk != k) {
-            __syncthreads();
-            stage_item(list[nk], cur);
-            k = nk;
+    int held[2] = {-1, -1};  // item held in cur[0], cur[1] (block-uniform)
+    int i = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+        const int b = i & 1;  // readers of cur[b] and s_p[b] from two tiles ago passed the last barrier
+        const int nk = item_of_tile(list, n_items, t);
+        if (nk != held[b]) {
+            const int *src = reinterpret_cast<const int *>(&list[nk]);
+            int *dst = reinterpret_cast<int *>(&cur[b]);
+            for (int q = threadIdx.x; q < (int)(sizeof(WorkItem) / sizeof(int)); q += kThreads)
+                dst[q] = src[q];
+            held[b] = nk;
         }
-        const ObjDesc &od = cur.od;
-        const BatchDesc &bd = cur.bd;
-        const int nr = bd.nr, NR = bd.rays_per_tile;
-        const int tile = t - cur.tile_begin, ray0 = tile * NR;
-        const int ns = min(NR, bd.n_rays - ray0) * nr;
+        const BatchDesc &gb = list[nk].bd;  // read directly until the barrier publishes cur[b]
+        const int nr = gb.nr, NR = gb.rays_per_tile;
+        const int tile = t - list[nk].tile_begin, ray0 = tile * NR;
+        const int ns = min(NR, gb.n_rays - ray0) * nr;
         if ((int)threadIdx.x < ns) {
             const int s = threadIdx.x, gr = ray0 + s / nr;
-            const float tk = bd.sp_t[(size_t)gr * nr + s % nr];
+            const float tk = gb.sp_t[(size_t)gr * nr + s % nr];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 float hi, lo;
-                pos_two_float(bd.o[(size_t)gr * 3 + a], tk, bd.d[(size_t)gr * 3 + a], hi, lo);
-                s_p[a][s] = hi;
-                s_p[3 + a][s] = lo;
+                pos_two_float(gb.o[(size_t)gr * 3 + a], tk, gb.d[(size_t)gr * 3 + a], hi, lo);
+                s_p[b][a][s] = hi;
+                s_p[b][3 + a][s] = lo;
             }
         }
         __syncthreads();
+        const ObjDesc &od = cur[b].od;
+        const BatchDesc &bd = cur[b].bd;
         const int NL = od.IN / 2;
         const float2 *dx = bd.sp_dx + (size_t)tile * kSplitDx;
         float2 *gtab = reinterpret_cast<float2 *>(od.grad);
@@ -59,8 +65,8 @@ __global__ void __launch_bounds__(kThreads, 5)
             float ph[3], pl[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                ph[a] = active ? s_p[a][s] : 0.f;
-                pl[a] = active ? s_p[3 + a][s] : 0.f;
+                ph[a] = active ? s_p[b][a][s] : 0.f;
+                pl[a] = active ? s_p[b][3 + a][s] : 0.f;
             }
             const LevelDesc lv = od.lv[l];
             Corners cs;
@@ -68,7 +74,6 @@ __global__ void __launch_bounds__(kThreads, 5)
             const float2 g = active ? dx[l * kSplitTile + s] : make_float2(0.f, 0.f);
             scatter_level_warp(gtab + lv.offset, active, cs, g.x, g.y, lane);
         }
-        __syncthreads();  // s_p is rewritten for the next tile
     }
 }
 
