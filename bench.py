@@ -426,12 +426,12 @@ def _time(stream, fn, steps, warmup, barrier=lambda: None, clocks=None):
     return ev0.elapsed_time(ev1)
 
 
-def _batched_objects(pkg, ctx, stream, precision, host, thetas=None):
+def _batched_objects(pkg, ctx, stream, precision, host, thetas=None, features=0):
     """Objects of the batched workload on the device: ids and the four ray sets
     as lists of device batches (one per object)."""
     objs = []
     for k, h in enumerate(host):
-        arch = pkg.make_arch(**batched_arch_dict(h["spec"]), precision=PRECISION[precision])
+        arch = pkg.make_arch(**batched_arch_dict(h["spec"]), precision=PRECISION[precision], features=features)
         obj = ctx.create_object(arch, None if thetas is None else thetas[k])
         ctx.set_prior_grid(obj, h["grid"])
         objs.append(obj)
@@ -620,8 +620,8 @@ STRESS_OBJECTS, STRESS_RAYS, STRESS_NR = 64, 1 << 20, 64
 
 def _stress_compare(pkg, ctx, stream, steps=200, warmup=20):
     """Real-time mapping stress: 64 objects of the category table in BF16 (MLP
-    on the tensor cores; the hash features stay FP32, which is their master
-    copy), 2^20 rays per step in total split by a projected-area share
+    on the tensor cores; BF16 hash features, i.e. the gathers read a BF16 copy
+    of the FP32 master tables), 2^20 rays per step in total split by a projected-area share
     2^(5a), a ~ U[0,1), 64 samples per ray from each object's 64^3 prior,
     rays from 480x640 views, the internal Philox uniforms and background
     colours; the whole step (all objects, backward, Adam) is one batched call,
@@ -636,7 +636,7 @@ def _stress_compare(pkg, ctx, stream, steps=200, warmup=20):
     for i in range(STRESS_OBJECTS):
         log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
         arch = pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
-                             lambda_sigma=1e-3, precision=PRECISION["bf16"])
+                             lambda_sigma=1e-3, precision=PRECISION["bf16"], features=pkg.PRENOM_FEATURES_BF16)
         sc = scene_random_csg(5000 + i)
         obj = ctx.create_object(arch)
         ctx.set_prior_grid(obj, prior_grid(sc, GRID_RES, i))
@@ -660,8 +660,8 @@ def _stress_compare(pkg, ctx, stream, steps=200, warmup=20):
     ms = np.array([a.elapsed_time(b) for a, b in ev])
     for o in objs:
         ctx.destroy_object(o)
-    return {"workload": "64 objects of the category table, BF16 MLP, %d rays x 64 samples per step "
-                        "(%d samples), 64^3 priors, one batched step" % (sum(rays), n_smp),
+    return {"workload": "64 objects of the category table, BF16 MLP and BF16 hash features (FP32 master tables), "
+                        "%d rays x 64 samples per step (%d samples), 64^3 priors, one batched step" % (sum(rays), n_smp),
             "value": n_smp / (float(np.mean(ms)) / 1e3), "unit": "samples/s",
             "latency_ms_p50": float(np.percentile(ms, 50)), "latency_ms_p99": float(np.percentile(ms, 99)),
             "steps": steps, "warmup": warmup}
@@ -784,12 +784,15 @@ def _ablation_compare(pkg, ctx, stream, prec, steps=300, seeds=(0, 1, 2)):
 
 def _roofline(pkg, report, specs, prec, adam_ms, n_params, peaks):
     """Each kernel of one batched step against its own bound, from the per-group
-    timing report: a group is every object of one MLP width (all objects have
-    L=16, F=2, so 8 L F x 4 B = 1024 B of gathers or FP32 reductions per sample);
-    its MLP work is 6 MAC FLOP per sample (2 forward, 4 backward).  The record
-    with the largest device time per step is the dominant kernel."""
+    timing report.  A group is every object of one MLP width; all objects have
+    L=16, F=2, so a sample moves 8 L F x 4 B = 1024 B of table gathers (the
+    encoder) or of FP32 reductions (the scatter), and its MLP work is 6 MAC FLOP
+    (2 forward, 4 backward).  Records are per kernel: its launches over the
+    groups (one per group per step) summed, achieved = the summed algorithmic
+    work / the summed device time, with the per-group figures beside it.  The
+    kernel with the largest device time per step is the dominant one."""
     names = {pkg.PRENOM_KERNEL_SAMPLE_ENCODE: "sample_encode_kernel", pkg.PRENOM_KERNEL_SCATTER: "hash_scatter_kernel"}
-    recs = []
+    kernels = {}
     for label, k, ms, n in report:
         tok = label.split()
         W, form = int(tok[1][1:]), tok[6]
@@ -799,36 +802,46 @@ def _roofline(pkg, report, specs, prec, adam_ms, n_params, peaks):
         t = (ms / n) / 1e3
         if k == pkg.PRENOM_KERNEL_TRAIN and form == "split":
             tc = prec != "fp32"
-            pk = peaks["bf16"] if tc else FP32_PEAK_TFLOPS
-            ach = flops / t / 1e12
-            rec = {"kernel": ("fused_tc_kernel_split" if tc else "fused_fp32_kernel_split"), "group": label,
-                   "bound": "tensor" if tc else "alu", "achieved": round(ach, 2), "peak": round(pk, 1),
-                   "unit": "TFLOP/s", "frac": round(ach / pk, 4),
-                   "algorithmic": f"6 x MAC FLOP/sample over {samples} samples = {flops / 1e9:.2f} GFLOP",
-                   "peak_src": (peaks["src"] + " bf16 (fp16 same rate)") if tc else "FP32 FFMA 152x128x2x2070 MHz"}
+            name = "fused_tc_kernel_split" if tc else "fused_fp32_kernel_split"
+            unit, work, what = "TFLOP/s", flops, "6 x MAC FLOP/sample"
+            base = {"bound": "tensor" if tc else "alu", "peak": round(peaks["bf16"] if tc else FP32_PEAK_TFLOPS, 1),
+                    "peak_src": (peaks["src"] + " bf16 (fp16 same rate)") if tc else "FP32 FFMA 152x128x2x2070 MHz"}
         else:
             per = 2048 if k == pkg.PRENOM_KERNEL_TRAIN else 1024
-            byts = samples * per
-            ach = byts / t / 1e9
-            kname = names.get(k, "fused_tc_kernel" if prec != "fp32" else "fused_fp32_kernel")
-            rec = {"kernel": kname, "group": label, "bound": "hbm", "achieved": round(ach, 1),
-                   "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
-                   "algorithmic": f"{per} B/sample x {samples} samples = {byts / 1e6:.1f} MB",
-                   "peak_src": peaks["src"] + " copy bandwidth"}
-        rec["avg_us"] = round(t * 1e6, 2)
-        rec["traffic"] = profiled_traffic(f"{rec['kernel']}/{prec}/W{W}")
-        recs.append(rec)
-    t = adam_ms / 1e3
-    ach = n_params * 28 / t / 1e9
-    recs.append({"kernel": "adam_kernel", "group": "every object", "bound": "hbm", "achieved": round(ach, 1),
-                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
-                 "algorithmic": f"28 B/parameter (read g, m, v, theta; write m, v, theta) x {n_params}",
-                 "peak_src": peaks["src"] + " copy bandwidth", "avg_us": round(t * 1e6, 2),
-                 "traffic": profiled_traffic(f"adam_kernel/{prec}/batched")})
-    dom = max(recs, key=lambda r: r["avg_us"])
+            name = names.get(k, "fused_tc_kernel" if prec != "fp32" else "fused_fp32_kernel")
+            unit, work, what = "GB/s", samples * per, f"{per} B/sample"
+            base = {"bound": "hbm", "peak": peaks["hbm_gbs"], "peak_src": peaks["src"] + " copy bandwidth"}
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        rec = kernels.setdefault(name, dict(kernel=name, unit=unit, work=0.0, t=0.0, groups=[], what=what, **base))
+        rec["work"] += work
+        rec["t"] += t
+        rec["groups"].append({"group": label, "avg_us": round(t * 1e6, 2), "achieved": round(work / t / scale, 2),
+                              "frac": round(work / t / scale / rec["peak"], 4),
+                              "traffic": profiled_traffic(f"{name}/{prec}/W{W}")})
+    kernels["adam_kernel"] = dict(kernel="adam_kernel", unit="GB/s", work=n_params * 28.0, t=adam_ms / 1e3, groups=[],
+                                  what="28 B/parameter (read g, m, v, theta; write m, v, theta)", bound="hbm",
+                                  peak=peaks["hbm_gbs"], peak_src=peaks["src"] + " copy bandwidth")
+    recs = []
+    for rec in kernels.values():
+        scale = 1e12 if rec["unit"] == "TFLOP/s" else 1e9
+        ach = rec["work"] / rec["t"] / scale
+        out = {"kernel": rec["kernel"], "bound": rec["bound"], "achieved": round(ach, 2), "peak": rec["peak"],
+               "unit": rec["unit"], "frac": round(ach / rec["peak"], 4),
+               "algorithmic": f"{rec['what']}: {rec['work'] / (1e9 if rec['unit'] == 'TFLOP/s' else 1e6):.1f} "
+                              f"{'GFLOP' if rec['unit'] == 'TFLOP/s' else 'MB'} per step over "
+                              f"{max(len(rec['groups']), 1)} launch(es)",
+               "avg_us_per_step": round(rec["t"] * 1e6, 2), "launches_per_step": max(len(rec["groups"]), 1),
+               "peak_src": rec["peak_src"],
+               "traffic": (profiled_traffic(f"adam_kernel/{prec}/batched") if rec["kernel"] == "adam_kernel"
+                           else (sum(g["traffic"] for g in rec["groups"])
+                                 if all(g["traffic"] is not None for g in rec["groups"]) else None))}
+        if rec["groups"]:
+            out["groups"] = rec["groups"]
+        recs.append(out)
+    dom = max(recs, key=lambda r: r["avg_us_per_step"])
     roof = dict(dom)
     roof["other_kernels"] = [r for r in recs if r is not dom]
-    roof["step_kernels_us"] = round(sum(r["avg_us"] for r in recs), 2)
+    roof["step_kernels_us"] = round(sum(r["avg_us_per_step"] for r in recs), 2)
     return roof
 
 
@@ -933,6 +946,18 @@ def run_ours(args):
         equal = _equal_error(pkg, ctx, stream, prec, steps=args.equal_error_steps)
 
     compare = {}
+    if world == 1 and not args.no_compare and prec != "fp32":
+        # the same batched step with the gathers on BF16 copies of the tables
+        objs_b, sets_b = _batched_objects(pkg, ctx, stream, prec, host, thetas, features=pkg.PRENOM_FEATURES_BF16)
+        ctx.autotune(sets_b[0], bopts)
+        fb = lambda i: ctx.train_step(sets_b[i % 4], bopts, lossb)  # noqa: E731
+        msb = _time(stream, fb, args.steps, args.warmup)
+        compare["batched_bf16_features"] = {"value": n_smp * args.steps / (msb / 1e3), "unit": "samples/s",
+                                            "ms_per_step": msb / args.steps,
+                                            "form": "the headline step with BF16 copies of the hash tables "
+                                                    "serving the gathers (FP32 master tables)"}
+        for o in objs_b:
+            ctx.destroy_object(o)
     if world == 1 and not args.no_compare:
         compare["single_object_full_size"] = _single_compare(pkg, ctx, stream, prec, rank, max(args.steps, 20),
                                                              args.warmup)

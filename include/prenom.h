@@ -65,6 +65,16 @@ extern "C" {
 #define PRENOM_PRECISION_FP16 1
 #define PRENOM_PRECISION_BF16 2
 
+/* prenom_arch.features: what the hash-grid gathers of the encoding read.
+ * FP32: the FP32 parameter tables themselves.  BF16 (mixed-precision objects
+ * only): a BF16 copy of the tables that each Adam step writes beside the FP32
+ * master values (and that every other write of theta refreshes); the gathers
+ * read it, four entries to one 16-byte load where the x-adjacent corners share
+ * it, and the encoding is summed in FP32.  Gradients, Adam and the master
+ * values stay FP32 in both. */
+#define PRENOM_FEATURES_FP32 0
+#define PRENOM_FEATURES_BF16 2
+
 /* prenom_train_opts.flags */
 #define PRENOM_FLAG_NO_ADAM 1u      /* accumulate gradients, skip Adam (step count unchanged) */
 #define PRENOM_FLAG_CHECK_FINITE 2u /* synchronise and fail with NONFINITE on a NaN/inf loss (per-object path) */
@@ -96,12 +106,14 @@ typedef struct prenom_ctx prenom_ctx; /* opaque; owns all device state */
  * lists hash-grid and MLP hyper-parameters and lambda_d, lambda_sigma).
  * Supported values: F = 2; L in {4, 8, 16}; width in {16, 32, 64};
  * 1 <= hidden <= 3; 8 <= log2T <= 24; 2 <= n_min <= n_max <= 2^20;
- * precision = PRENOM_PRECISION_FP32, _FP16 or _BF16. */
+ * precision = PRENOM_PRECISION_FP32, _FP16 or _BF16; features =
+ * PRENOM_FEATURES_FP32, or _BF16 with a mixed precision. */
 typedef struct {
     int32_t L, F, log2T, n_min, n_max; /* levels, features/level, log2 table size, resolutions */
     int32_t width, hidden;             /* MLP hidden width W and hidden layer count H */
     int32_t precision;                 /* PRENOM_PRECISION_* */
     float lambda_d, lambda_sigma;      /* Eq. 9 loss weights */
+    int32_t features;                  /* PRENOM_FEATURES_* (0 = FP32) */
 } prenom_arch;
 
 /* Step options.  lr, beta1, beta2, eps: Adam (§III-B).  nc, nr: probes and

@@ -21,6 +21,8 @@ from ._abi import (  # noqa: F401
     PRENOM_ERR_INVALID_ARG,
     PRENOM_ERR_NONFINITE,
     PRENOM_ERR_OOM,
+    PRENOM_FEATURES_BF16,
+    PRENOM_FEATURES_FP32,
     PRENOM_FLAG_CHECK_FINITE,
     PRENOM_FLAG_FUSED,
     PRENOM_FLAG_SPLIT,
@@ -50,8 +52,8 @@ __all__ = ["Context", "make_arch", "make_opts", "arch_param_count", "PrenomError
 
 
 def make_arch(L=8, F=2, log2T=14, n_min=16, n_max=256, width=32, hidden=2, precision=PRENOM_PRECISION_FP32,
-              lambda_d=0.1, lambda_sigma=0.0) -> prenom_arch:
-    return prenom_arch(L, F, log2T, n_min, n_max, width, hidden, precision, lambda_d, lambda_sigma)
+              lambda_d=0.1, lambda_sigma=0.0, features=0) -> prenom_arch:
+    return prenom_arch(L, F, log2T, n_min, n_max, width, hidden, precision, lambda_d, lambda_sigma, features)
 
 
 def arch_param_count(arch: prenom_arch) -> int:

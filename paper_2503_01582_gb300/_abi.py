@@ -22,6 +22,8 @@ PRENOM_ERR_NONFINITE = -5
 PRENOM_PRECISION_FP32 = 0
 PRENOM_PRECISION_FP16 = 1
 PRENOM_PRECISION_BF16 = 2
+PRENOM_FEATURES_FP32 = 0
+PRENOM_FEATURES_BF16 = 2
 PRENOM_FLAG_NO_ADAM = 1
 PRENOM_FLAG_CHECK_FINITE = 2
 PRENOM_FLAG_NO_GRAPH = 4
@@ -48,7 +50,7 @@ class prenom_arch(C.Structure):
     _fields_ = [
         ("L", C.c_int32), ("F", C.c_int32), ("log2T", C.c_int32), ("n_min", C.c_int32), ("n_max", C.c_int32),
         ("width", C.c_int32), ("hidden", C.c_int32), ("precision", C.c_int32),
-        ("lambda_d", C.c_float), ("lambda_sigma", C.c_float),
+        ("lambda_d", C.c_float), ("lambda_sigma", C.c_float), ("features", C.c_int32),
     ]
 
 

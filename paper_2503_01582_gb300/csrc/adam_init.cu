@@ -21,6 +21,13 @@ __device__ __forceinline__ void adam_one(float &th, float &m, float &v, float g,
     th -= lr_c1 * m / (sqrtf(v * inv_c2) + eps);
 }
 
+// Two FP32 values as one bf16x2 word, the first in the low half (rounded to nearest even).
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b)
+{
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+
 // max |x| of a warp into *dst (non-negative floats order like their bit patterns)
 __device__ __forceinline__ void warp_absmax_to(uint32_t *dst, float amax)
 {
@@ -81,12 +88,16 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
                 *reinterpret_cast<float4 *>(sg.grad + i) = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (i < n_hash)
                     amax = fmaxf(amax, fmaxf(fmaxf(fabsf(th.x), fabsf(th.y)), fmaxf(fabsf(th.z), fabsf(th.w))));
+                if (sg.mirror && i < sg.n_hash)  // two entries of the tables' BF16 copy
+                    *reinterpret_cast<uint2 *>(sg.mirror + i) = make_uint2(bf16_pair(th.x, th.y), bf16_pair(th.z, th.w));
             } else {
                 for (int64_t j = i; j < end; ++j) {
                     adam_one(sg.theta[j], sg.m[j], sg.v[j], sg.grad[j], a.beta1, a.beta2, a.eps, lr_c1, inv_c2);
                     sg.grad[j] = 0.f;
                     if (j < n_hash)
                         amax = fmaxf(amax, fabsf(sg.theta[j]));
+                    if (sg.mirror && j < sg.n_hash)
+                        sg.mirror[j] = __bfloat16_as_ushort(__float2bfloat16_rn(sg.theta[j]));
                 }
             }
         }
@@ -257,6 +268,21 @@ cudaError_t launch_loss_scale_update(LossScaleState *s, cudaStream_t st)
     l.n = 1;
     l.s[0] = s;
     return launch_loss_scale_update_list(l, st);
+}
+
+// mirror[i] = bf16(theta[i]), i < n (n a multiple of 4; mirror 8-byte aligned)
+__global__ void __launch_bounds__(256) mirror_kernel(const float *theta, int64_t n, uint16_t *mirror)
+{
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; i < n; i += (int64_t)gridDim.x * blockDim.x * 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(theta + i);
+        *reinterpret_cast<uint2 *>(mirror + i) = make_uint2(bf16_pair(t.x, t.y), bf16_pair(t.z, t.w));
+    }
+}
+
+cudaError_t launch_mirror_refresh(const float *theta, int64_t n, uint16_t *mirror, int grid, cudaStream_t st)
+{
+    mirror_kernel<<<grid, 256, 0, st>>>(theta, n, mirror);
+    return cudaGetLastError();
 }
 
 // max |theta[0..n_hash)| into s->hash_absmax; enc_scale_set_kernel then derives enc_scale from it

@@ -205,6 +205,34 @@ __device__ __forceinline__ void gather_pair(const float2 *tab, uint32_t i0, uint
     }
 }
 
+// One entry of a BF16 table: a 32-bit word, feature 0 in the low half (a bf16
+// is the top half of the FP32 it rounds, so widening is a shift).
+__device__ __forceinline__ float2 bf16x2_entry(uint32_t w)
+{
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xFFFF0000u));
+}
+
+// Two entries of a BF16 table.  x-adjacent corners whose indices differ only in
+// their two low bits lie in one aligned group of four entries (16 bytes; every
+// level starts on a multiple of 8 entries), so one load serves both: at hashed
+// levels for x = 0, 1, 2 mod 4 (the x prime is 1), at dense levels for flat
+// indices 0, 1, 2 mod 4 -- three pairs in four, against one in two for the
+// 8-byte FP32 entries.
+__device__ __forceinline__ void gather_pair16(const uint32_t *tab, uint32_t i0, uint32_t i1, float2 &f0, float2 &f1)
+{
+    if ((i0 ^ i1) < 4u) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(tab + (i0 & ~3u)));
+        const uint32_t k0 = i0 & 3u, k1 = i1 & 3u;
+        const uint32_t w0 = k0 == 0u ? q.x : k0 == 1u ? q.y : k0 == 2u ? q.z : q.w;
+        const uint32_t w1 = k1 == 0u ? q.x : k1 == 1u ? q.y : k1 == 2u ? q.z : q.w;
+        f0 = bf16x2_entry(w0);
+        f1 = bf16x2_entry(w1);
+    } else {
+        f0 = bf16x2_entry(__ldg(tab + i0));
+        f1 = bf16x2_entry(__ldg(tab + i1));
+    }
+}
+
 // Adds (a0, a1) to entry i0 and (b0, b1) to entry i1, skipping an entry whose
 // two addends are zero (an exact zero where the pair is one access).
 __device__ __forceinline__ void scatter_pair(float2 *gtab, uint32_t i0, uint32_t i1, float a0, float a1, float b0,

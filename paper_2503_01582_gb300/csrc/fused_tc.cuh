@@ -548,9 +548,15 @@ __global__ void __launch_bounds__(kThreads, 2)
                     Corners cs;
                     level_corners(lv, od.tmask, ph, pl, cs);
                     float2 f[8];
+                    if (od.feat16) {  // the tables' BF16 copy
 #pragma unroll
-                    for (int c = 0; c < 8; c += 2)
-                        gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                        for (int c = 0; c < 8; c += 2)
+                            gather_pair16(od.feat16 + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 8; c += 2)
+                            gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                    }
                     float e0 = 0.f, e1 = 0.f;
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {

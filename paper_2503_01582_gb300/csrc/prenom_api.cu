@@ -32,6 +32,7 @@ struct Object {
     std::vector<int32_t> res, dense;
     std::vector<int64_t> off;  // float offsets, L + 1 entries
     float *arena = nullptr, *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    uint16_t *feat16 = nullptr;  // BF16 copy of the hash tables (PRENOM_FEATURES_BF16)
     float *grid = nullptr;
     int32_t R = 0;
     int32_t step = 0;
@@ -165,6 +166,10 @@ int check_arch(prenom_ctx *c, const prenom_arch *a)
         return fail(c, PRENOM_ERR_INVALID_ARG, "precision %d: must be FP32 (0), FP16 (1) or BF16 (2)", a->precision);
     if (!(a->lambda_d >= 0.f) || !(a->lambda_sigma >= 0.f) || !isfinite(a->lambda_d) || !isfinite(a->lambda_sigma))
         return fail(c, PRENOM_ERR_INVALID_ARG, "lambda_d and lambda_sigma must be finite and >= 0");
+    if (a->features != PRENOM_FEATURES_FP32 && a->features != PRENOM_FEATURES_BF16)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "features %d: must be FP32 (0) or BF16 (2)", a->features);
+    if (a->features == PRENOM_FEATURES_BF16 && a->precision == PRENOM_PRECISION_FP32)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "BF16 features need a mixed-precision object");
     return PRENOM_OK;
 }
 
@@ -268,6 +273,7 @@ ObjDesc make_objdesc(const Object &o, float *grad)
 {
     ObjDesc d{};
     d.theta = o.theta;
+    d.feat16 = reinterpret_cast<const uint32_t *>(o.feat16);
     d.grad = grad;
     d.L = o.arch.L;
     d.IN = o.IN;
@@ -384,7 +390,7 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
             WorkItem one{};
             one.od = od;
             one.bd = bd;
-            const WorkList wl{nullptr, 1, bd.n_tiles, od.H, 1};
+            const WorkList wl{nullptr, 1, bd.n_tiles, od.H, 1, od.feat16 != nullptr};
             cudaEvent_t ev;
             timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
             cudaError_t e = launch_sample_encode(one, wl, o.arch.precision,
@@ -464,16 +470,22 @@ uint32_t *enc_absmax_ptr(const Object &o)
     return o.lss && o.arch.precision == PRENOM_PRECISION_FP16 ? &o.lss->hash_absmax : nullptr;
 }
 
-// Recomputes an FP16 object's encoding scale from its current hash tables
-// (after a write of theta that Adam did not make).
+// Recomputes what an object derives from its hash tables -- the BF16 copy the
+// gathers read and an FP16 object's encoding scale -- after a write of theta
+// that Adam did not make.
 int refresh_enc_scale(prenom_ctx *c, const Object &o)
 {
-    if (!enc_absmax_ptr(o))
-        return PRENOM_OK;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((o.n_hash + 1023) / 1024, (int64_t)c->n_sm * 8));
-    const cudaError_t e = launch_enc_scale_refresh(o.theta, o.n_hash, o.lss, grid, c->stream);
-    c->launches += 2;
-    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "encoding-scale refresh");
+    cudaError_t e = cudaSuccess;
+    if (o.feat16) {
+        e = launch_mirror_refresh(o.theta, o.n_hash, o.feat16, grid, c->stream);
+        c->launches += 1;
+    }
+    if (e == cudaSuccess && enc_absmax_ptr(o)) {
+        e = launch_enc_scale_refresh(o.theta, o.n_hash, o.lss, grid, c->stream);
+        c->launches += 2;
+    }
+    return e == cudaSuccess ? PRENOM_OK : cuda_fail(c, e, "refresh of the tables' copy and scale");
 }
 
 int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train_opts &op)
@@ -502,6 +514,7 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
             s.skip = o.lss ? &o.lss->overflow : nullptr;
             s.absmax = enc_absmax_ptr(o);
             s.n_hash = o.n_hash;
+            s.mirror = o.feat16;
             a.chunk_start[i - first + 1] = a.chunk_start[i - first] + (o.n + kAdamChunk - 1) / kAdamChunk;
         }
         const int64_t chunks = a.chunk_start[a.n_segs];
@@ -537,6 +550,7 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
 struct Group {
     int precision, W, IN, S, hmax, first, count, total_tiles, grid;
     bool split = false;  // mixed precision: the three-kernel split form
+    int feat16 = 0;      // the group's gathers read BF16 copies of the tables
 };
 
 struct Plan {
@@ -580,7 +594,8 @@ int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed
 std::string group_key(const Group &g)
 {
     char buf[128];
-    snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d", g.precision, g.W, g.IN, g.S, g.hmax, g.count, g.total_tiles);
+    snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d/%d", g.precision, g.W, g.IN, g.S, g.hmax, g.count, g.total_tiles,
+             g.feat16);
     return buf;
 }
 
@@ -590,8 +605,8 @@ std::string tune_key(const Group &g)
 {
     auto lg = [](int x) { int b = 0; while (x > 1) { x >>= 1; ++b; } return b; };
     char buf[128];
-    snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/n%d/t%d", g.precision, g.W, g.IN, g.S, g.hmax, lg(g.count),
-             lg(g.total_tiles));
+    snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/n%d/t%d%s", g.precision, g.W, g.IN, g.S, g.hmax, lg(g.count),
+             lg(g.total_tiles), g.feat16 ? "/b" : "");
     return buf;
 }
 
@@ -601,8 +616,8 @@ std::string group_label(const Group &g)
 {
     static const char *prec[] = {"fp32", "fp16", "bf16"};
     char buf[160];
-    snprintf(buf, sizeof(buf), "%s W%d IN%d H%d batches%d tiles%d %s grid%d", prec[g.precision], g.W, g.IN, g.hmax,
-             g.count, g.total_tiles, g.split ? "split" : "fused", g.grid);
+    snprintf(buf, sizeof(buf), "%s W%d IN%d H%d batches%d tiles%d %s grid%d%s", prec[g.precision], g.W, g.IN, g.hmax,
+             g.count, g.total_tiles, g.split ? "split" : "fused", g.grid, g.feat16 ? " bf16-features" : "");
     return buf;
 }
 
@@ -618,7 +633,7 @@ int group_index(prenom_ctx *c, const std::string &label)
 int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const prenom_train_opts &op, float *loss_dev,
                  Plan &p)
 {
-    std::vector<std::array<int, 4>> keys(n);
+    std::vector<std::array<int, 5>> keys(n);
     for (int i = 0; i < n; ++i) {
         const Object &o = c->objs[batches[i].obj];
         int S = 128;
@@ -630,7 +645,7 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
                 return fail(c, PRENOM_ERR_INVALID_ARG, "nr = %d exceeds the %d-sample tile of this architecture",
                             op.nr, S);
         }
-        keys[i] = {o.arch.precision, o.arch.width, o.IN, S};
+        keys[i] = {o.arch.precision, o.arch.width, o.IN, S, o.arch.features == PRENOM_FEATURES_BF16 ? 1 : 0};
     }
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i)
@@ -639,6 +654,7 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
     p.items.resize(n);
     for (int j = 0; j < n;) {
         Group g{keys[order[j]][0], keys[order[j]][1], keys[order[j]][2], keys[order[j]][3], 1, j, 0, 0, 0};
+        g.feat16 = keys[order[j]][4];
         int tiles = 0;
         while (j < n && keys[order[j]] == keys[order[g.first]]) {
             const int i = order[j];
@@ -688,6 +704,7 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
             sg.skip = o.lss ? &o.lss->overflow : nullptr;
             sg.absmax = enc_absmax_ptr(o);
             sg.n_hash = o.n_hash;
+            sg.mirror = o.feat16;
             a.chunk_start[s + 1] = a.chunk_start[s] + (o.n + kAdamChunk - 1) / kAdamChunk;
             if (o.lss && p.scales.n < kMaxScaleObjs)
                 p.scales.s[p.scales.n++] = o.lss;
@@ -710,7 +727,7 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     for (const Group &g : p.groups) {
         if (e != cudaSuccess || g.total_tiles == 0)
             continue;
-        const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax, g.split ? 1 : 0};
+        const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax, g.split ? 1 : 0, g.feat16};
         cudaEvent_t ev;
         c->cur_group = timed ? group_index(c, group_label(g)) : -1;
         if (g.split) {
@@ -1090,14 +1107,18 @@ int prenom_create_object(prenom_ctx *c, const prenom_arch *arch, const float *in
     Object o;
     o.arch = *arch;
     level_geometry(*arch, o);
-    cudaError_t e = cudaMalloc(&o.arena, (size_t)o.n_pad * 4 * sizeof(float));
+    // theta | grad | m | v, each n_pad floats, then (BF16 features) the tables' copy
+    const int64_t mirror_floats = arch->features == PRENOM_FEATURES_BF16 ? (o.n_hash / 2 + 63) / 64 * 64 : 0;
+    const int64_t arena_floats = o.n_pad * 4 + mirror_floats;
+    cudaError_t e = cudaMalloc(&o.arena, (size_t)arena_floats * sizeof(float));
     if (e != cudaSuccess)
-        return fail(c, PRENOM_ERR_OOM, "object arena of %lld floats: %s", (long long)(o.n_pad * 4),
+        return fail(c, PRENOM_ERR_OOM, "object arena of %lld floats: %s", (long long)arena_floats,
                     cudaGetErrorString(e));
     o.theta = o.arena;
     o.grad = o.arena + o.n_pad;
     o.m = o.arena + 2 * o.n_pad;
     o.v = o.arena + 3 * o.n_pad;
+    o.feat16 = mirror_floats ? reinterpret_cast<uint16_t *>(o.arena + 4 * o.n_pad) : nullptr;
     e = cudaMemsetAsync(o.grad, 0, (size_t)o.n_pad * 3 * sizeof(float), c->stream);
     if (e == cudaSuccess) {
         if (init_params) {

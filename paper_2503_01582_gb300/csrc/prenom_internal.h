@@ -25,6 +25,7 @@ struct LevelDesc {
 // One object's field as the fused kernel sees it.
 struct ObjDesc {
     const float *theta;  // parameters (hash tables then MLP matrices)
+    const uint32_t *feat16;  // BF16 copy of the hash tables (one bf16x2 word per entry), or NULL: gathers read theta
     float *grad;         // gradient accumulator (atomically added)
     int32_t L, IN, W, H;
     uint32_t tmask;      // T - 1 for hashed levels
@@ -125,6 +126,8 @@ struct ScaleList {
     LossScaleState *s[kMaxScaleObjs];
 };
 cudaError_t launch_loss_scale_update_list(const ScaleList &l, cudaStream_t st);
+// mirror[i] = bf16(theta[i]) for i < n (after any write of theta other than Adam's).
+cudaError_t launch_mirror_refresh(const float *theta, int64_t n, uint16_t *mirror, int grid, cudaStream_t st);
 // enc_scale of an FP16 object from max |theta[0..n_hash)| (after any write of
 // theta other than Adam's, which gathers the maximum as it updates).
 cudaError_t launch_enc_scale_refresh(const float *theta, int64_t n_hash, LossScaleState *s, int grid,
@@ -147,6 +150,7 @@ struct WorkList {
     const WorkItem *items;  // device memory
     int32_t n_items, total_tiles, hmax;
     int32_t split;  // 1: sampling, encoding and the hash scatter run in kernels of their own
+    int32_t feat16; // 1: every item's gathers read the BF16 copy of its tables (ObjDesc::feat16)
 };
 
 // Dynamic shared memory (bytes) of the fused FP32 kernel for (W, IN, H, S).
@@ -171,6 +175,7 @@ struct AdamSeg {
     const float2 *scal;   // device (lr_c1, inv_c2) of this step, or NULL to use the two fields above
     uint32_t *absmax;     // FP16: max |updated theta| over [0, n_hash) gathered here (NULL = not gathered)
     int64_t n_hash;
+    uint16_t *mirror;     // BF16 copy of theta[0, n_hash) written with the update (NULL = none)
 };
 struct AdamArgs {
     int32_t n_segs;

@@ -38,7 +38,8 @@ __host__ __device__ __forceinline__ int enc_rays_per_warp(int nr)
 
 // FMT: 0 FP16 or 1 BF16 image in the tensor-core kernel's operand layout, 2 FP32
 // feature-major image [IN][kSplitTile] for the FP32 kernel.
-template <int FMT>
+// F16: the items' gathers read the BF16 copies of their tables (FMT 0 or 1 only).
+template <int FMT, bool F16>
 __global__ void __launch_bounds__(kThreads, 4)
     sample_encode_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
@@ -119,9 +120,15 @@ __global__ void __launch_bounds__(kThreads, 4)
                     Corners cs;
                     level_corners(lv, od.tmask, ph, pl, cs);
                     float2 f[8];
+                    if constexpr (F16) {  // the tables' BF16 copy
 #pragma unroll
-                    for (int c = 0; c < 8; c += 2)
-                        gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                        for (int c = 0; c < 8; c += 2)
+                            gather_pair16(od.feat16 + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 8; c += 2)
+                            gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                    }
                     float e0 = 0.f, e1 = 0.f;
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -151,7 +158,13 @@ __global__ void __launch_bounds__(kThreads, 4)
 template <int FMT>
 cudaError_t launch_sample_encode_t(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
-    sample_encode_kernel<FMT><<<grid, kThreads, 0, st>>>(one, wl);
+    if constexpr (FMT != 2) {
+        if (wl.feat16) {
+            sample_encode_kernel<FMT, true><<<grid, kThreads, 0, st>>>(one, wl);
+            return cudaGetLastError();
+        }
+    }
+    sample_encode_kernel<FMT, false><<<grid, kThreads, 0, st>>>(one, wl);
     return cudaGetLastError();
 }
 

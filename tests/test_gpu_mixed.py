@@ -56,9 +56,10 @@ def _dev(rays, obj, cr=None, t_in=None, u=None):
     return b
 
 
-def _arch(p, d, precision):
+def _arch(p, d, precision, features=0):
     return p.make_arch(L=d["L"], F=d["F"], log2T=d["log2T"], n_min=d["n_min"], n_max=d["n_max"], width=d["width"],
-                       hidden=d["hidden"], lambda_d=d["lambda_d"], lambda_sigma=d["lambda_sigma"], precision=precision)
+                       hidden=d["hidden"], lambda_d=d["lambda_d"], lambda_sigma=d["lambda_sigma"], precision=precision,
+                       features=features)
 
 
 def _grad_metrics(g, want):
@@ -321,3 +322,66 @@ def test_split_form_against_oracle_full_size(pkg, hash_range):
     bnd = FULL_BOUNDS[hash_range]
     _check_blocks(a, g, want["grad"], 1, f"full size, hash range {hash_range}")
     assert e_loss <= bnd["rel"] and cos >= bnd["cos"] and l2 <= bnd["l2"]
+
+
+def _bf16_tables(th, nh):
+    """theta with its hash tables rounded to BF16 (nearest even), MLP untouched."""
+    import torch
+
+    t = np.array(th, np.float32, copy=True)
+    t[:nh] = torch.from_numpy(t[:nh]).to(torch.bfloat16).to(torch.float32).numpy()
+    return t
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_bf16_feature_copy_equals_rounded_tables(pkg, precision):
+    """An object whose gathers read the BF16 copy of its tables renders exactly as
+    an object whose FP32 tables hold those rounded values, before and after an
+    Adam step (which writes the copy beside the FP32 master values) and after a
+    state write; and it meets the mixed-precision bounds against the oracle at
+    the rounded tables.  A batched step with both objects runs them as two groups."""
+    import torch
+
+    a, theta, grid, rays, u, cr = case(CFG1, 128, 32, 32, seed=77, hash_range=0.5)
+    nh = orc.n_hash_params(a)
+    t_in = oracle_t(grid, rays, u, 32, 32)
+    opts = pkg.make_opts(nc=32, nr=32)
+    ctx = pkg.Context(seed=3)
+    A = ctx.create_object(_arch(pkg, CFG1, precision, features=pkg.PRENOM_FEATURES_BF16), theta)
+    B = ctx.create_object(_arch(pkg, CFG1, precision), _bf16_tables(theta, nh))
+    for o in (A, B):
+        ctx.set_prior_grid(o, grid)
+
+    def same_renders():
+        ra = ctx.render(_dev(rays, A, t_in=t_in), opts)
+        rb = ctx.render(_dev(rays, B, t_in=t_in), opts)
+        for k in ("rgb", "depth", "acc"):
+            np.testing.assert_array_equal(ra[k].cpu().numpy(), rb[k].cpu().numpy())
+        return ra
+
+    ra = same_renders()
+    want = orc.batch(a, _bf16_tables(theta, nh).astype(np.float64), grid, rays, 32, 32, t_in=t_in, c_rand=cr,
+                     want_grad=True)
+    bnd = BOUNDS[precision]
+    assert float(np.abs(ra["rgb"].cpu().numpy() - want["rgb"]).max()) <= bnd["rgb"]
+    assert rel(ra["depth"].cpu().numpy(), want["depth"]) <= bnd["rel"]
+    loss = torch.zeros(2, device="cuda")
+    ctx.train_step([_dev(rays, A, cr=cr, t_in=t_in), _dev(rays, B, cr=cr, t_in=t_in)],
+                   pkg.make_opts(nc=32, nr=32, flags=pkg.PRENOM_FLAG_NO_ADAM), loss)
+    g = ctx.get_state(A, pkg.PRENOM_STATE_GRAD).cpu().numpy()
+    assert abs(loss[0].item() - want["loss"]) <= bnd["rel"] * abs(want["loss"])
+    _check_blocks(a, g, want["grad"], precision, "BF16 tables")
+    np.testing.assert_allclose(g, ctx.get_state(B, pkg.PRENOM_STATE_GRAD).cpu().numpy(), rtol=0, atol=1e-6 * np.abs(g).max())
+    # an Adam step writes the copy; B then takes A's master values rounded
+    ctx.train_step([_dev(rays, A, cr=cr, t_in=t_in)], pkg.make_opts(nc=32, nr=32, lr=1e-2))
+    th_a = ctx.get_state(A).cpu().numpy()
+    assert np.max(np.abs(th_a - theta)) > 0
+    ctx.set_state(B, pkg.PRENOM_STATE_THETA, _bf16_tables(th_a, nh))
+    same_renders()
+    # a state write refreshes the copy too
+    ctx.set_state(A, pkg.PRENOM_STATE_THETA, theta)
+    ctx.set_state(B, pkg.PRENOM_STATE_THETA, _bf16_tables(theta, nh))
+    same_renders()
+    with pytest.raises(pkg.PrenomError):  # BF16 features need a mixed-precision object
+        ctx.create_object(_arch(pkg, CFG1, 0, features=pkg.PRENOM_FEATURES_BF16))
+    ctx.close()
