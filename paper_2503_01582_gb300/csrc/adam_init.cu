@@ -341,6 +341,14 @@ size_t fused_tc_smem(int W, int IN, int H, bool split)
     }
 }
 
+int fused_tc_occupancy_fp16(int W, int IN, int H, bool split);
+int fused_tc_occupancy_bf16(int W, int IN, int H, bool split);
+
+int fused_tc_occupancy(int precision, int W, int IN, int H, bool split)
+{
+    return precision == 2 ? fused_tc_occupancy_bf16(W, IN, H, split) : fused_tc_occupancy_fp16(W, IN, H, split);
+}
+
 static cudaError_t tc_dispatch(const WorkItem &one, const WorkList &wl, int W, int IN, int precision, int grid,
                                cudaStream_t st)
 {

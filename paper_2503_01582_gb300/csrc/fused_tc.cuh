@@ -266,11 +266,14 @@ struct TcLayout {
     // dO: 4 of 16 columns (the K of the dH product), or of 64 when the dW_out
     // product (M = 64) reads it too
     static __host__ __device__ int doa_cols(int H, bool split) { return split && tc_dw_out<W, IN>(H) ? kDaCols : 16; }
+    // floats of the per-warp scratch: the sampler's CDFs, or in split mode (no
+    // sampler in this kernel) only the compositing's exchange, 8 per warp
+    static __host__ __device__ int scratch_floats(bool split) { return split ? 64 : 8 * (kMaxNc + 1); }
     static __host__ __device__ size_t bytes(int H, bool split)
     {
         size_t b = (size_t)w0 + (size_t)(H - 1) * wh + wo + xa + (size_t)H * ha + da;
         b += (size_t)kTcTile * doa_cols(H, split) * 2;
-        b += sizeof(float) * (8 * SP + SP + (size_t)(kTcTile / kMinNr) * kRayStride + 8 * (size_t)(kMaxNc + 1));
+        b += sizeof(float) * (8 * SP + SP + (size_t)(kTcTile / kMinNr) * kRayStride + scratch_floats(split));
         return b + 64;  // TMEM slot and mbarrier
     }
 };
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     float *ts = dOT + 4 * SP;
     float *rayf = ts + SP;
     float *cdfs = rayf + MAXR * kRayStride;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cdfs + 8 * (kMaxNc + 1));
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cdfs + L::scratch_floats(wl.split != 0));
     uint64_t *mbar = reinterpret_cast<uint64_t *>(tmem_slot + 2);
 
     // buffers with padding that is never written again: W_0 (columns IN..INP),
@@ -812,6 +815,41 @@ cudaError_t launch_tc_t(const WorkItem &one, const WorkList &wl, int grid, cudaS
         return e;
     fused_tc_kernel<W, IN, BF16><<<grid, kThreads, smem, st>>>(one, wl);
     return cudaGetLastError();
+}
+
+// Resident CTAs per SM of a kernel variant with its dynamic shared memory
+// (static shared memory included by the occupancy query), at most two: each
+// CTA holds kTcCols of the SM's 512 TMEM columns.  0 when it does not fit.
+template <int W, int IN, bool BF16>
+int tc_occupancy_t(int H, bool split)
+{
+    const size_t smem = TcLayout<W, IN>::bytes(H, split);
+    if (cudaFuncSetAttribute(fused_tc_kernel<W, IN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_tc_kernel<W, IN, BF16>, kThreads, smem) != cudaSuccess)
+        return 0;
+    return n < 512 / kTcCols ? n : 512 / kTcCols;
+}
+
+template <bool BF16>
+int tc_occupancy_prec(int W, int IN, int H, bool split)
+{
+#define PRENOM_TC_OCC(Wv, INv)                                                                                        \
+    if (W == Wv && IN == INv)                                                                                         \
+        return tc_occupancy_t<Wv, INv, BF16>(H, split);
+    PRENOM_TC_OCC(16, 8)
+    PRENOM_TC_OCC(16, 16)
+    PRENOM_TC_OCC(16, 32)
+    PRENOM_TC_OCC(32, 8)
+    PRENOM_TC_OCC(32, 16)
+    PRENOM_TC_OCC(32, 32)
+    PRENOM_TC_OCC(64, 8)
+    PRENOM_TC_OCC(64, 16)
+    PRENOM_TC_OCC(64, 32)
+#undef PRENOM_TC_OCC
+    return 0;
 }
 
 template <bool BF16>

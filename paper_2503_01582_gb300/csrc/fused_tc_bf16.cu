@@ -8,6 +8,11 @@ cudaError_t launch_fused_tc_bf16(const WorkItem &one, const WorkList &wl, int W,
     return launch_tc_prec<true>(one, wl, W, IN, grid, st);
 }
 
+int fused_tc_occupancy_bf16(int W, int IN, int H, bool split)
+{
+    return tc_occupancy_prec<true>(W, IN, H, split);
+}
+
 cudaError_t launch_sample_encode_bf16(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
     return launch_sample_encode_t<1>(one, wl, grid, st);

@@ -8,6 +8,11 @@ cudaError_t launch_fused_tc_fp16(const WorkItem &one, const WorkList &wl, int W,
     return launch_tc_prec<false>(one, wl, W, IN, grid, st);
 }
 
+int fused_tc_occupancy_fp16(int W, int IN, int H, bool split)
+{
+    return tc_occupancy_prec<false>(W, IN, H, split);
+}
+
 cudaError_t launch_sample_encode_fp16(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
     return launch_sample_encode_t<0>(one, wl, grid, st);

@@ -66,6 +66,7 @@ struct prenom_ctx {
     int cur_group = -1;
     std::vector<std::string> group_names;
     std::map<std::pair<int, int>, std::pair<double, int64_t>> group_time;
+    mutable std::map<int, int> tc_occ;  // resident tensor-core CTAs per SM by variant
     int64_t n_captures = 0;    // step graphs captured
     int64_t n_tune_calls = 0;  // steps run as autotuner measurements
     // batched steps: device work list (+ per-object Adam factors behind it),
@@ -370,6 +371,18 @@ int grid_scatter(const prenom_ctx *c, int total_tiles)
     return std::max(1, std::min(total_tiles, c->n_sm * 5));  // five 256-thread CTAs per SM (48 registers)
 }
 
+// Resident CTAs per SM of a tensor-core kernel variant (queried once per variant).
+int tc_per_sm(const prenom_ctx *c, int precision, int W, int IN, int H, bool split)
+{
+    const int key = (((precision * 128 + W) * 64 + IN) * 8 + H) * 2 + (split ? 1 : 0);
+    auto it = c->tc_occ.find(key);
+    if (it != c->tc_occ.end())
+        return it->second;
+    const int n = fused_tc_occupancy(precision, W, IN, H, split);
+    c->tc_occ[key] = n;
+    return n;
+}
+
 int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &bd, int kernel_id, bool split = false)
 {
     if (bd.n_rays == 0)
@@ -380,7 +393,7 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
             return fail(c, PRENOM_ERR_INVALID_ARG, "architecture needs more shared memory than the device offers");
         bd.rays_per_tile = 128 / bd.nr;
         bd.n_tiles = (bd.n_rays + bd.rays_per_tile - 1) / bd.rays_per_tile;
-        const int per_sm = (2 * (smem + 1024) <= 228 * 1024) ? 2 : 1;  // two CTAs share an SM when they fit
+        const int per_sm = std::max(1, tc_per_sm(c, o.arch.precision, od.W, od.IN, od.H, split && bd.mode == kTrain));
         const int grid = std::min(bd.n_tiles, c->n_sm * per_sm);
         if (split && bd.mode == kTrain) {
             int rc = ensure_split(c, split_bytes(bd.n_rays, bd.nr, bd.n_tiles));
@@ -581,9 +594,8 @@ bool cand_split(const Group &, int cand, bool split_allowed)
 int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed)
 {
     int per_sm = 1;
-    if (g.precision != PRENOM_PRECISION_FP32 &&
-        2 * (fused_tc_smem(g.W, g.IN, g.hmax, cand_split(g, cand, split_allowed)) + 1024) <= 228 * 1024)
-        per_sm = 2;
+    if (g.precision != PRENOM_PRECISION_FP32)
+        per_sm = std::max(1, tc_per_sm(c, g.precision, g.W, g.IN, g.hmax, cand_split(g, cand, split_allowed)));
     const int wave = c->n_sm * per_sm;
     const int tpc = split_allowed ? kTuneTpcTc[cand] : kTuneTpc[cand];
     if (tpc == 0)

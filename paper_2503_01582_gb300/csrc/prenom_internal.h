@@ -103,6 +103,8 @@ struct WorkList;
 
 // Mixed-precision fused kernel (tcgen05 MLP); precision 1 = FP16, 2 = BF16.
 size_t fused_tc_smem(int W, int IN, int H, bool split);
+// Resident CTAs per SM (1 or 2; 0 if the variant does not fit) of the tensor-core kernel.
+int fused_tc_occupancy(int precision, int W, int IN, int H, bool split);
 cudaError_t launch_fused_tc(const ObjDesc &od, const BatchDesc &bd, int precision, int grid, cudaStream_t st);
 cudaError_t launch_fused_tc_list(const WorkList &wl, int W, int IN, int precision, int grid, cudaStream_t st);
 cudaError_t launch_fused_tc_bf16(const WorkItem &one, const WorkList &wl, int W, int IN, int grid, cudaStream_t st);
