@@ -817,20 +817,23 @@ cudaError_t launch_tc_t(const WorkItem &one, const WorkList &wl, int grid, cudaS
     return cudaGetLastError();
 }
 
-// Resident CTAs per SM of a kernel variant with its dynamic shared memory
-// (static shared memory included by the occupancy query), at most two: each
-// CTA holds kTcCols of the SM's 512 TMEM columns.  0 when it does not fit.
+// Resident CTAs per SM of a kernel variant: two when two CTAs' dynamic and
+// static shared memory (each with the per-block reservation) and registers fit
+// the SM, else one; never more, since each CTA holds kTcCols of the SM's 512
+// TMEM columns.  0 when a device query fails.
 template <int W, int IN, bool BF16>
 int tc_occupancy_t(int H, bool split)
 {
-    const size_t smem = TcLayout<W, IN>::bytes(H, split);
-    if (cudaFuncSetAttribute(fused_tc_kernel<W, IN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
+    if (cudaFuncGetAttributes(&fa, fused_tc_kernel<W, IN, BF16>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
         return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_tc_kernel<W, IN, BF16>, kThreads, smem) != cudaSuccess)
-        return 0;
-    return n < 512 / kTcCols ? n : 512 / kTcCols;
+    const size_t per_cta = TcLayout<W, IN>::bytes(H, split) + fa.sharedSizeBytes + (size_t)reserved;
+    const long long regs_cta = (long long)((fa.numRegs + 7) / 8 * 8) * kThreads;
+    return (2 * per_cta <= (size_t)smem_sm && 2 * regs_cta <= regs_sm) ? 2 : 1;
 }
 
 template <bool BF16>
