@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const uint4 *src = bd.sp_x + (size_t)tile * (kSplitXBytes / 16);
             for (int i = tid; i < kTcTile * INP * 2 / 16; i += kThreads) {
                 const int row = ((i >> 3) / (INP >> 3)) * 8 + (i & 7);
-                reinterpret_cast<uint4 *>(XA)[i] = row < ns ? src[i] : make_uint4(0u, 0u, 0u, 0u);
+                reinterpret_cast<uint4 *>(XA)[i] = row < ns ? __ldcs(src + i) : make_uint4(0u, 0u, 0u, 0u);
             }
             if (tid < kTcTile && tid >= ns)
 #pragma unroll
@@ -638,8 +638,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             const uint4 *src = bd.sp_x + (size_t)tile2 * (kSplitXBytes / 16);
             const uint4 z = make_uint4(0u, 0u, 0u, 0u);
             const int i1 = tid + kThreads;
-            px0 = tid < kChunks && ((tid >> 3) / (INP >> 3)) * 8 + (tid & 7) < ns2 ? src[tid] : z;
-            px1 = i1 < kChunks && ((i1 >> 3) / (INP >> 3)) * 8 + (i1 & 7) < ns2 ? src[i1] : z;
+            px0 = tid < kChunks && ((tid >> 3) / (INP >> 3)) * 8 + (tid & 7) < ns2 ? __ldcs(src + tid) : z;
+            px1 = i1 < kChunks && ((i1 >> 3) / (INP >> 3)) * 8 + (i1 & 7) < ns2 ? __ldcs(src + i1) : z;
             const float *rsrc = bd.sp_rays + (size_t)tile2 * kSplitRayFloats;
             pr0 = tid < nr2 ? rsrc[tid] : 0.f;
             pr1 = i1 < nr2 ? rsrc[i1] : 0.f;
@@ -768,7 +768,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                     for (int j = 0; j < INP / 4; ++j)
                         if (l0 + j < NL)
-                            dst[(l0 + j) * kTcTile + s] = make_float2(g[2 * j] * inv_scale, g[2 * j + 1] * inv_scale);
+                            __stcs(dst + (l0 + j) * kTcTile + s,
+                                   make_float2(g[2 * j] * inv_scale, g[2 * j + 1] * inv_scale));
                 }
                 ok = tc_sync_and(done_dx);
                 continue;

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads, 5)
             const LevelDesc lv = od.lv[l];
             Corners cs;
             level_corners(lv, od.tmask, ph, pl, cs);
-            const float2 g = active ? dx[l * kSplitTile + s] : make_float2(0.f, 0.f);
+            const float2 g = active ? __ldcs(dx + l * kSplitTile + s) : make_float2(0.f, 0.f);  // read once
             scatter_level_warp(gtab + lv.offset, active, cs, g.x, g.y, lane);
         }
     }

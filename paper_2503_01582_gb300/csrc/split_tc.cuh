@@ -14,7 +14,10 @@
 //      run the MLP, compositing, loss and MLP backward (a7-a10) and write
 //      dL/d(encoding) per tile, FP32, level-major, instead of scattering it;
 //   3. hash_scatter_kernel: the hash-grid scatter (a10) of those gradients.
-// The arithmetic of every step is the fused kernels' own code.
+// The arithmetic of every step is the fused kernels' own code.  The hand-over
+// buffers are written and read once with evict-first hints (st.cs / ld.cs), so
+// that where they exceed L2 (a batched step of many objects) they do not evict
+// the hash tables and gradient tables that the gathers and reductions reuse.
 #pragma once
 
 #include "fused_tc.cuh"
@@ -146,8 +149,8 @@ __global__ void __launch_bounds__(kThreads, 4)
                 // row of the tile image: INP / 8 chunks of 8 columns (16 bytes each)
                 if constexpr (FMT != 2) {
                     if ((l & 3) == 3 && l / 4 < INP / 8)
-                        *reinterpret_cast<uint4 *>(img + il_off(row, 8 * (l / 4), INP)) =
-                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        __stcs(reinterpret_cast<uint4 *>(img + il_off(row, 8 * (l / 4), INP)),
+                               make_uint4(pk[0], pk[1], pk[2], pk[3]));
                 }
             }
         }
