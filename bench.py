@@ -621,50 +621,58 @@ STRESS_OBJECTS, STRESS_RAYS, STRESS_NR = 64, 1 << 20, 64
 def _stress_compare(pkg, ctx, stream, steps=200, warmup=20):
     """Real-time mapping stress: 64 objects of the category table in BF16 (MLP
     on the tensor cores; BF16 hash features, i.e. the gathers read a BF16 copy
-    of the FP32 master tables), 2^20 rays per step in total split by a projected-area share
-    2^(5a), a ~ U[0,1), 64 samples per ray from each object's 64^3 prior,
-    rays from 480x640 views, the internal Philox uniforms and background
-    colours; the whole step (all objects, backward, Adam) is one batched call,
-    and each step's latency is timed with its own CUDA events."""
+    of the FP32 master tables), 2^20 rays per step in total split by a
+    projected-area share 2^(5a), a ~ U[0,1), 64 samples per ray from each
+    object's 64^3 prior, rays from 480x640 views, the internal Philox uniforms
+    and background colours; the whole step (all objects, backward, Adam) is one
+    batched call, autotuned and graph-captured before the warm-up, and each
+    step's latency is timed with its own CUDA events.  The same workload with
+    the gathers on the FP32 tables is reported beside it."""
     import torch
     from synth import cameras_on_sphere, make_ray_pool, prior_grid, sample_batch, scene_random_csg
 
     rng = np.random.default_rng(17)
     w = 2.0 ** (5 * rng.random(STRESS_OBJECTS))
     rays = [max(32, 32 * int(round(STRESS_RAYS * x / w.sum() / 32))) for x in w]
-    objs, sets = [], [[], []]
-    for i in range(STRESS_OBJECTS):
-        log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
-        arch = pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
-                             lambda_sigma=1e-3, precision=PRECISION["bf16"], features=pkg.PRENOM_FEATURES_BF16)
-        sc = scene_random_csg(5000 + i)
-        obj = ctx.create_object(arch)
-        ctx.set_prior_grid(obj, prior_grid(sc, GRID_RES, i))
-        pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 50, 480, 640, 100 + i), 2 * rays[i], 100 + i,
-                             depth_noise=0.004)
-        for j in range(2):
-            sets[j].append(_device_batches([sample_batch(pool, rays[i], 50 * i + j)], obj, stream)[0])
-        objs.append(obj)
     n_smp = sum(rays) * STRESS_NR
     opts = pkg.make_opts(nc=STRESS_NR, nr=STRESS_NR, lr=1e-2)
     loss = torch.zeros(STRESS_OBJECTS, device="cuda")
-    for i in range(warmup):
-        ctx.train_step(sets[i % 2], opts, loss)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    torch.cuda.synchronize()
-    for i in range(steps):
-        ev[i][0].record(stream)
-        ctx.train_step(sets[i % 2], opts, loss)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    ms = np.array([a.elapsed_time(b) for a, b in ev])
-    for o in objs:
-        ctx.destroy_object(o)
-    return {"workload": "64 objects of the category table, BF16 MLP and BF16 hash features (FP32 master tables), "
-                        "%d rays x 64 samples per step (%d samples), 64^3 priors, one batched step" % (sum(rays), n_smp),
-            "value": n_smp / (float(np.mean(ms)) / 1e3), "unit": "samples/s",
-            "latency_ms_p50": float(np.percentile(ms, 50)), "latency_ms_p99": float(np.percentile(ms, 99)),
-            "steps": steps, "warmup": warmup}
+    out = {}
+    for features in (pkg.PRENOM_FEATURES_BF16, pkg.PRENOM_FEATURES_FP32):
+        objs, sets = [], [[], []]
+        for i in range(STRESS_OBJECTS):
+            log2T, W, H = CATEGORY_ARCHS[i % len(CATEGORY_ARCHS)]
+            arch = pkg.make_arch(L=16, log2T=log2T, n_min=16, n_max=2048, width=W, hidden=H, lambda_d=0.1,
+                                 lambda_sigma=1e-3, precision=PRECISION["bf16"], features=features)
+            sc = scene_random_csg(5000 + i)
+            obj = ctx.create_object(arch)
+            ctx.set_prior_grid(obj, prior_grid(sc, GRID_RES, i))
+            pool = make_ray_pool(sc, cameras_on_sphere(8, 2.0, 50, 480, 640, 100 + i), 2 * rays[i], 100 + i,
+                                 depth_noise=0.004)
+            for j in range(2):
+                sets[j].append(_device_batches([sample_batch(pool, rays[i], 50 * i + j)], obj, stream)[0])
+            objs.append(obj)
+        ctx.autotune(sets[0], opts)
+        for i in range(warmup):
+            ctx.train_step(sets[i % 2], opts, loss)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for i in range(steps):
+            ev[i][0].record(stream)
+            ctx.train_step(sets[i % 2], opts, loss)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        for o in objs:
+            ctx.destroy_object(o)
+        out[features] = {"value": n_smp / (float(np.mean(ms)) / 1e3), "unit": "samples/s",
+                         "latency_ms_p50": float(np.percentile(ms, 50)),
+                         "latency_ms_p99": float(np.percentile(ms, 99))}
+    res = {"workload": "64 objects of the category table, BF16 MLP and BF16 hash features (FP32 master tables), "
+                       "%d rays x 64 samples per step (%d samples), 64^3 priors, one batched step" % (sum(rays), n_smp)}
+    res.update(out[pkg.PRENOM_FEATURES_BF16])
+    res.update(steps=steps, warmup=warmup, fp32_features=out[pkg.PRENOM_FEATURES_FP32])
+    return res
 
 
 META_TASKS, META_INNER, META_RAYS, META_NR = 16, 16, 2048, 48
