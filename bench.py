@@ -808,7 +808,7 @@ def _roofline(pkg, report, specs, prec, adam_ms, n_params, peaks):
         samples = sum(sp["rays"] * BATCHED_NR for sp in members)
         flops = sum(sp["rays"] * BATCHED_NR * 6 * mlp_macs(sp["W"], sp["H"]) for sp in members)
         t = (ms / n) / 1e3
-        if k == pkg.PRENOM_KERNEL_TRAIN and form == "split":
+        if k == pkg.PRENOM_KERNEL_TRAIN and form.startswith("split"):
             tc = prec != "fp32"
             name = "fused_tc_kernel_split" if tc else "fused_fp32_kernel_split"
             unit, work, what = "TFLOP/s", flops, "6 x MAC FLOP/sample"

@@ -259,13 +259,17 @@ __device__ __forceinline__ void scatter_pair(float2 *gtab, uint32_t i0, uint32_t
 // consecutive lanes, so at coarse levels runs of lanes share one cell: a
 // segmented warp scan sums each run (in chunks, below) first and only the
 // chunk's last lane issues the reductions.  A corner of zero weight adds nothing.
-// Lanes of one cell are summed in chunks of at most 2^kScatterChunkLog2 lanes (5
-// would be a whole run) before the reductions: fewer shuffle rounds against
-// more reductions.  Measured on the full-size step, the scatter kernel takes
-// 96.5 / 74.8 / 75.5 / 78.9 / 82.6 us for chunks of 1 / 2 / 4 / 8 / 32 lanes,
-// and the whole step is fastest with 4.
+// Lanes of one cell are summed in chunks of at most 2^CHUNK_LOG2 lanes (5 is a
+// whole run) before the reductions: fewer shuffle rounds against more
+// reductions.  Measured on the full-size single object, the scatter kernel
+// takes 96.5 / 74.8 / 75.5 / 78.9 / 82.6 us for chunks of 1 / 2 / 4 / 8 / 32
+// lanes and the whole step is fastest with 4; on the 32-object batched step
+// (smaller tables, more reductions per entry) 1642 / 1447 / 1355 / 1314 us for
+// 2 / 4 / 8 / 32, so the split form's scatter comes in both, chosen by the
+// autotuner.
 constexpr int kScatterChunkLog2 = 2;
 
+template <int CHUNK_LOG2 = kScatterChunkLog2>
 __device__ __forceinline__ void scatter_level_warp(float2 *gtab, bool active, const Corners &cs, float g0, float g1,
                                                    int lane)
 {
@@ -276,8 +280,8 @@ __device__ __forceinline__ void scatter_level_warp(float2 *gtab, bool active, co
     uint32_t heads = __ballot_sync(kFull, head);
     const uint32_t upto = 0xffffffffu >> (31 - lane);  // lanes 0..lane
     int pos = lane - (31 - __clz(heads & upto));  // position in the run
-    if constexpr (kScatterChunkLog2 < 5) {  // runs cut into chunks of 2^kScatterChunkLog2 lanes
-        heads |= __ballot_sync(kFull, (pos & ((1 << kScatterChunkLog2) - 1)) == 0);
+    if constexpr (CHUNK_LOG2 < 5) {  // runs cut into chunks of 2^CHUNK_LOG2 lanes
+        heads |= __ballot_sync(kFull, (pos & ((1 << CHUNK_LOG2) - 1)) == 0);
         pos = lane - (31 - __clz(heads & upto));
     }
     const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) != 0u;

@@ -563,6 +563,7 @@ int run_adam(prenom_ctx *c, const std::vector<int32_t> &objs, const prenom_train
 struct Group {
     int precision, W, IN, S, hmax, first, count, total_tiles, grid;
     bool split = false;  // mixed precision: the three-kernel split form
+    bool whole_runs = false;  // split form: the scatter sums whole runs of lanes
     int feat16 = 0;      // the group's gathers read BF16 copies of the tables
 };
 
@@ -578,17 +579,24 @@ struct Plan {
 
 // Candidates of the autotuner: tiles per CTA of the training kernel (0 = one
 // persistent wave of resident CTAs).  A group tries the split form first (its
-// MLP kernel in one wave), then the fused kernel with three work-chunk sizes;
-// with the split form excluded, the fused kernel with four.
+// MLP kernel in one wave), with the scatter summing lanes of one cell in chunks
+// of four (c0) or over whole runs (c1), then the fused kernel in one wave and
+// with 16 tiles per CTA; with the split form excluded, the fused kernel with
+// four work-chunk sizes.
 constexpr int kTuneTpc[] = {0, 16, 8, 4};
-constexpr int kTuneTpcTc[] = {0, 0, 16, 8};
+constexpr int kTuneTpcTc[] = {0, 0, 0, 16};
 constexpr int kTuneN = 4;
 constexpr int kTuneRounds = 2;  // each candidate is timed this many times (one whole step each)
 constexpr size_t kMaxGraphs = 64;  // captured step graphs kept per context
 
 bool cand_split(const Group &, int cand, bool split_allowed)
 {
-    return split_allowed && cand == 0;
+    return split_allowed && cand <= 1;
+}
+
+bool cand_whole_runs(int cand, bool split_allowed)
+{
+    return split_allowed && cand == 1;
 }
 
 int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed)
@@ -629,7 +637,8 @@ std::string group_label(const Group &g)
     static const char *prec[] = {"fp32", "fp16", "bf16"};
     char buf[160];
     snprintf(buf, sizeof(buf), "%s W%d IN%d H%d batches%d tiles%d %s grid%d%s", prec[g.precision], g.W, g.IN, g.hmax,
-             g.count, g.total_tiles, g.split ? "split" : "fused", g.grid, g.feat16 ? " bf16-features" : "");
+             g.count, g.total_tiles, g.split ? (g.whole_runs ? "split-runs" : "split") : "fused", g.grid,
+             g.feat16 ? " bf16-features" : "");
     return buf;
 }
 
@@ -762,7 +771,7 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
         if (g.split && e == cudaSuccess) {
             if (timed)
                 timed_begin(c, PRENOM_KERNEL_SCATTER, &ev);
-            e = launch_hash_scatter(unused, wl, grid_scatter(c, g.total_tiles), c->stream);
+            e = launch_hash_scatter(unused, wl, grid_scatter(c, g.total_tiles), c->stream, g.whole_runs);
             if (timed)
                 timed_end(c, PRENOM_KERNEL_SCATTER, ev);
         }
@@ -822,6 +831,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         }
         g.grid = group_grid(c, g, cand, split_allowed);
         g.split = cand_split(g, cand, split_allowed);
+        g.whole_runs = cand_whole_runs(cand, split_allowed);
     }
     // buffers of the split groups (planned before any staging or capture)
     size_t split_need = 0;
@@ -914,7 +924,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
     } else if (use_graph) {
         std::string key = std::to_string(b) + ":" + std::to_string(bytes) + ":" + std::to_string(p.adam_grid);
         for (const Group &g : p.groups)
-            key += "|" + group_key(g) + "/" + std::to_string(g.grid) + (g.split ? "s" : "f");
+            key += "|" + group_key(g) + "/" + std::to_string(g.grid) + (g.split ? (g.whole_runs ? "w" : "s") : "f");
         for (int32_t id : p.touched)
             key += "," + std::to_string(id);
         char tail[96];

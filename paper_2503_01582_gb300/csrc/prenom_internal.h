@@ -113,7 +113,9 @@ cudaError_t launch_fused_tc_fp16(const WorkItem &one, const WorkList &wl, int W,
 // then the tensor-core kernel without its scatter, then the hash scatter.
 // wl.items == nullptr means the single item `one`.
 cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int precision, int grid, cudaStream_t st);
-cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st);
+// whole_runs: lanes of one cell summed over whole runs instead of chunks of four.
+cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st,
+                                bool whole_runs = false);
 // Bytes of split buffers for a batch of n_rays rays of nr samples in n_tiles tiles.
 inline size_t split_bytes(int n_rays, int nr, int n_tiles)
 {

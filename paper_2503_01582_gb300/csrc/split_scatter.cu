@@ -14,6 +14,8 @@ namespace prenom {
 // shared memory, double-buffered with the tile's work item, so one block
 // barrier per tile suffices; each warp then scatters one (level, 32 consecutive
 // samples) at a time, so a warp's lanes hold neighbouring samples of one level.
+// CHUNK_LOG2: lanes of one cell summed in chunks of 2^CHUNK_LOG2 (5: whole runs).
+template <int CHUNK_LOG2>
 __global__ void __launch_bounds__(kThreads, 5)
     hash_scatter_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kThreads, 5)
             Corners cs;
             level_corners(lv, od.tmask, ph, pl, cs);
             const float2 g = active ? __ldcs(dx + l * kSplitTile + s) : make_float2(0.f, 0.f);  // read once
-            scatter_level_warp(gtab + lv.offset, active, cs, g.x, g.y, lane);
+            scatter_level_warp<CHUNK_LOG2>(gtab + lv.offset, active, cs, g.x, g.y, lane);
         }
     }
 }
@@ -87,9 +89,12 @@ cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int pr
     return precision == 2 ? launch_sample_encode_bf16(one, wl, grid, st) : launch_sample_encode_fp16(one, wl, grid, st);
 }
 
-cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
+cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st, bool whole_runs)
 {
-    hash_scatter_kernel<<<grid, kThreads, 0, st>>>(one, wl);
+    if (whole_runs)
+        hash_scatter_kernel<5><<<grid, kThreads, 0, st>>>(one, wl);
+    else
+        hash_scatter_kernel<kScatterChunkLog2><<<grid, kThreads, 0, st>>>(one, wl);
     return cudaGetLastError();
 }
 

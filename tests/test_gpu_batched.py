@@ -93,7 +93,8 @@ def test_batched_gradients_match_per_object_and_oracle(pkg):
 
 def test_batched_adam_graph_replay_and_autotuner(pkg):
     """Twelve batched steps on a side stream: the first nine tune (one untimed
-    call, then two rounds over the split form and three work-chunk sizes), the
+    call, then two rounds over the four candidates: the split form with two
+    scatter variants, the fused kernel with two work-chunk sizes), the
     rest replay a captured graph while the ray buffers change; the losses and
     parameters follow the same objects stepped one at a time (with
     PRENOM_FLAG_CHECK_FINITE, i.e. one launch per object, untuned)."""
