@@ -101,9 +101,12 @@ __device__ __forceinline__ uint32_t mma_idesc(uint32_t fmt, int M, int N, uint32
 // shared-memory address below 256 KB never carries out of it), so the single
 // issuing thread spends a few cycles per MMA instead of a dependent chain of
 // 64-bit shifts and masks.
+// kslices (<= K / 16) issues only the first slices: a weight-gradient product
+// over a tile's samples stops after its last filled sample (rows past it are
+// zero in both operands, so the result is the same).
 template <int K>
 __device__ __forceinline__ void mma_gemm(uint32_t d_tmem, const Operand &a, const Operand &b, uint32_t idesc,
-                                         bool accumulate)
+                                         bool accumulate, int kslices = K / 16)
 {
     static_assert(K % 16 == 0 && K > 0, "K is a multiple of 16");
     const uint64_t ad0 = smem_desc(a.addr, a.kstr, a.mnstr);
@@ -111,6 +114,8 @@ __device__ __forceinline__ void mma_gemm(uint32_t d_tmem, const Operand &a, cons
     const uint64_t astep = (uint64_t)((2u * a.kstr) >> 4), bstep = (uint64_t)((2u * b.kstr) >> 4);
 #pragma unroll
     for (int ks = 0; ks < K / 16; ++ks) {
+        if (ks >= kslices)
+            break;
         const uint64_t ad = ad0 + (uint64_t)ks * astep;
         const uint64_t bd = bd0 + (uint64_t)ks * bstep;
         const uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
@@ -487,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int ray0 = tile * NR;
         const int nrt = min(NR, bd.n_rays - ray0);
         const int ns = nrt * nr;
+        const int kdw = (ns + 15) >> 4;  // 16-sample slices of the weight-gradient products
         // ---- ray data and sampling (FP32, shared with the FP32 kernel)
         const bool split = bd.sp_x != nullptr;  // sampling, encoding and scatter run in kernels of their own
         if (split && pre_t == t) {  // prefetched during the previous tile
@@ -668,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 mma_commit(mbar);
                 if (l == H - 1 && tc_dwo)  // dW_out += dO^T H_{H-1}, rows 0..3 of M = 64 (a later commit covers it)
                     mma_gemm<kTcTile>(tmem + dw_col<W, IN>(H), mnmajor(DOA, kDaCols),
-                                      mnmajor(HA + (H - 1) * L::ha, W), id_dw, !first_dw);
+                                      mnmajor(HA + (H - 1) * L::ha, W), id_dw, !first_dw, kdw);
             }
             if (l == H - 1 && !tc_dwo) {
                 // dW_out[o][i0..i0+7] on the CUDA cores while the tensor cores form dH_{H-1}:
@@ -681,6 +687,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
                 for (int k = 0; k < kTcTile / SL; ++k) {
+                    if (k * SL >= ns)  // the tile's empty rows add nothing
+                        break;
                     const int s = k * SL + slice;
                     // the same 16-bit dO (scaled) the tensor-core form multiplies
                     const float d = Hf::value(Hf::bits(dOT[o * SP + s] * scale));
@@ -732,10 +740,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (tid == 0 && ok) {
                 if (l > 0)
                     mma_gemm<kTcTile>(tmem + dw_col<W, IN>(l), mnmajor(DA, kDaCols), mnmajor(HA + (l - 1) * L::ha, W),
-                                      id_dw, !first_dw);
+                                      id_dw, !first_dw, kdw);
                 else
                     mma_gemm<kTcTile>(tmem + dw_col<W, IN>(0), mnmajor(DA, kDaCols), mnmajor(XA, INP), id_dw0,
-                                      !first_dw);
+                                      !first_dw, kdw);
             }
         }
         if (!ok)
