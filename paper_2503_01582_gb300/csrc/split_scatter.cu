@@ -58,10 +58,12 @@ __global__ void __launch_bounds__(kThreads, 5)
         const int NL = od.IN / 2;
         const float2 *dx = bd.sp_dx + (size_t)tile * kSplitDx;
         float2 *gtab = reinterpret_cast<float2 *>(od.grad);
-        for (int task = warp; task < NL * (kSplitTile / 32); task += kEncWarps) {
-            const int l = task / (kSplitTile / 32), c = task % (kSplitTile / 32);
-            if (c * 32 >= ns)
-                continue;  // warp-uniform
+        // the tile's (level, 32-sample chunk) tasks, over the filled chunks only, dealt
+        // round-robin to the warps (skipping empty chunks instead left whole warps idle
+        // at the barrier: a tile of two 48-sample rays fills 3 of 4 chunks)
+        const int nch = (ns + 31) >> 5;
+        for (int task = warp; task < NL * nch; task += kEncWarps) {
+            const int l = task / nch, c = task - l * nch;
             const int s = c * 32 + lane;
             const bool active = s < ns;
             float ph[3], pl[3];
