@@ -42,6 +42,13 @@ struct Half<true> {
     static __device__ __forceinline__ uint16_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
     static __device__ __forceinline__ float value(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
     static __device__ __forceinline__ bool finite(uint16_t b) { return (b & 0x7F80u) != 0x7F80u; }
+    // two values in one conversion, a in the low half
+    static __device__ __forceinline__ uint32_t pack2(float a, float b)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    static constexpr float kRoundsToInf = 3.3961e38f;  // |x| from here on rounds to infinity
 };
 
 template <>
@@ -50,6 +57,12 @@ struct Half<false> {
     static __device__ __forceinline__ uint16_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
     static __device__ __forceinline__ float value(uint16_t b) { return __half2float(__ushort_as_half(b)); }
     static __device__ __forceinline__ bool finite(uint16_t b) { return (b & 0x7C00u) != 0x7C00u; }
+    static __device__ __forceinline__ uint32_t pack2(float a, float b)
+    {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    static constexpr float kRoundsToInf = 65520.f;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -573,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                         e1 = fmaf(cs.wt[c], f[c].y, e1);
                     }
                     *reinterpret_cast<uint32_t *>(XA + il_off(s, 2 * l, INP)) =
-                        (uint32_t)Hf::bits(e0 * enc) | ((uint32_t)Hf::bits(e1 * enc) << 16);
+                        Hf::pack2(e0 * enc, e1 * enc);
                 }
                 for (int l = NL + part; l < INP / 2; l += 2)  // zero padding of a narrow encoding
                     *reinterpret_cast<uint32_t *>(XA + il_off(s, 2 * l, INP)) = 0u;
@@ -602,10 +615,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int c0 = 0; c0 < W / 2; c0 += 8) {
                     const int col = half * (W / 2) + c0;
                     uint4 pk;
-                    pk.x = (uint32_t)Hf::bits(fmaxf(v[c0], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 1], 0.f)) << 16);
-                    pk.y = (uint32_t)Hf::bits(fmaxf(v[c0 + 2], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 3], 0.f)) << 16);
-                    pk.z = (uint32_t)Hf::bits(fmaxf(v[c0 + 4], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 5], 0.f)) << 16);
-                    pk.w = (uint32_t)Hf::bits(fmaxf(v[c0 + 6], 0.f)) | ((uint32_t)Hf::bits(fmaxf(v[c0 + 7], 0.f)) << 16);
+                    pk.x = Hf::pack2(fmaxf(v[c0], 0.f), fmaxf(v[c0 + 1], 0.f));
+                    pk.y = Hf::pack2(fmaxf(v[c0 + 2], 0.f), fmaxf(v[c0 + 3], 0.f));
+                    pk.z = Hf::pack2(fmaxf(v[c0 + 4], 0.f), fmaxf(v[c0 + 5], 0.f));
+                    pk.w = Hf::pack2(fmaxf(v[c0 + 6], 0.f), fmaxf(v[c0 + 7], 0.f));
                     *reinterpret_cast<uint4 *>(HA + l * L::ha + il_off(srow, col, W)) = pk;
                 }
             }
@@ -715,6 +728,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             const unsigned char *hl = HA + l * L::ha;
             float vb[W / 2];
             tmem_ld_cols<W / 2>(lane_base + half * (W / 2), vb);
+            // an H entry is > 0 iff its 16-bit pattern is neither +0 nor -0 (the ReLU output
+            // is never negative or NaN); a masked value overflows the 16-bit format iff its
+            // magnitude reaches the rounding threshold to infinity, and a NaN shows in the
+            // sum of magnitudes (fmaxf would drop it)
+            float amax = 0.f, asum = 0.f;
 #pragma unroll
             for (int c0 = 0; c0 < W / 2; c0 += 8) {
                 const int col = half * (W / 2) + c0;
@@ -722,19 +740,18 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const uint4 hv = *reinterpret_cast<const uint4 *>(hl + il_off(srow, col, W));
                 const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
                 uint32_t pk[4];
-                bool fin = true;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const uint16_t h0 = (uint16_t)(hw[j] & 0xFFFFu), h1 = (uint16_t)(hw[j] >> 16);
-                    const uint16_t b0 = Hf::bits(Hf::value(h0) > 0.f ? v[2 * j] : 0.f);
-                    const uint16_t b1 = Hf::bits(Hf::value(h1) > 0.f ? v[2 * j + 1] : 0.f);
-                    fin = fin && Hf::finite(b0) && Hf::finite(b1);
-                    pk[j] = (uint32_t)b0 | ((uint32_t)b1 << 16);
+                    const float a = (hw[j] & 0x7FFFu) ? v[2 * j] : 0.f;
+                    const float b = (hw[j] & 0x7FFF0000u) ? v[2 * j + 1] : 0.f;
+                    amax = fmaxf(amax, fmaxf(fabsf(a), fabsf(b)));
+                    asum += fabsf(a) + fabsf(b);
+                    pk[j] = Hf::pack2(a, b);
                 }
-                if (!fin && bd.overflow)
-                    atomicExch(bd.overflow, 1);
                 *reinterpret_cast<uint4 *>(DA + il_off(srow, col, kDaCols)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
+            if ((!(amax < Hf::kRoundsToInf) || asum != asum) && bd.overflow)
+                atomicExch(bd.overflow, 1);
             ok = tc_sync_and(done);
             // dW_l += dH_l^T A_l (M = 64 rows of DA, N = width of A_l, K = 128 samples)
             if (tid == 0 && ok) {

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 4)
                         fimg[(2 * l) * kSplitTile + row] = e0;
                         fimg[(2 * l + 1) * kSplitTile + row] = e1;
                     } else {
-                        pk[l & 3] = (uint32_t)Hf::bits(e0 * enc) | ((uint32_t)Hf::bits(e1 * enc) << 16);
+                        pk[l & 3] = Hf::pack2(e0 * enc, e1 * enc);
                     }
                 }
                 // row of the tile image: INP / 8 chunks of 8 columns (16 bytes each)
