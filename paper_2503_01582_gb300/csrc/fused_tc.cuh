@@ -265,13 +265,22 @@ constexpr int kTcTile = 128;       // samples per tile = MMA M
 constexpr int kTcCols = 256;       // TMEM columns allocated per CTA
 constexpr int kDaCols = 64;        // columns of the dH buffer (dW MMAs use M = 64)
 
-// dW_out (4 x W, rows 0..3 of an M = 64 accumulator at dw_col(H)) is formed on
-// the tensor cores when its W columns fit after the hidden layers' dW (for the
-// launch's deepest MLP), else summed on the CUDA cores.
+// dW_out (4 x W) on the tensor cores, at dw_col(H): for W = 64 as its transpose
+// dW_out^T = H_{H-1}^T dO (M = 64 = W, N = 16: dO's 16 zero-padded columns, so 16
+// TMEM columns and the plain 16-column dO buffer), for W < 64 as rows 0..3 of an
+// M = 64 accumulator of W columns (dO widened to 64 columns); when its columns do
+// not fit after the hidden layers' dW (for the launch's deepest MLP) it is summed
+// on the CUDA cores.
+template <int W>
+__host__ __device__ __forceinline__ constexpr bool tc_dwo_transposed()
+{
+    return W == kDaCols;
+}
+
 template <int W, int IN>
 __host__ __device__ __forceinline__ bool tc_dw_out(int H)
 {
-    return 64 + (IN < 16 ? 16 : IN) + H * W <= kTcCols;
+    return 64 + (IN < 16 ? 16 : IN) + (H - 1) * W + (tc_dwo_transposed<W>() ? 16 : W) <= kTcCols;
 }
 
 template <int W, int IN>
@@ -281,9 +290,12 @@ struct TcLayout {
     // byte sizes of the 16-bit matrices
     static constexpr int w0 = W * INP * 2, wh = W * W * 2, wo = 16 * W * 2;
     static constexpr int xa = kTcTile * INP * 2, ha = kTcTile * W * 2, da = kTcTile * kDaCols * 2;
-    // dO: 4 of 16 columns (the K of the dH product), or of 64 when the dW_out
-    // product (M = 64) reads it too
-    static __host__ __device__ int doa_cols(int H, bool split) { return split && tc_dw_out<W, IN>(H) ? kDaCols : 16; }
+    // dO: 4 of 16 columns (the K of the dH product and the N of the transposed
+    // dW_out product), or of 64 when the M = 64 dW_out product reads it
+    static __host__ __device__ int doa_cols(int H, bool split)
+    {
+        return split && tc_dw_out<W, IN>(H) && !tc_dwo_transposed<W>() ? kDaCols : 16;
+    }
     // floats of the per-warp scratch: the sampler's CDFs, or in split mode (no
     // sampler in this kernel) only the compositing's exchange, 8 per warp
     static __host__ __device__ int scratch_floats(bool split) { return split ? 64 : 8 * (kMaxNc + 1); }
@@ -367,7 +379,21 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
     }
     if (!have_dw)
         return;
-    for (int l = 0; l < H + (tc_dwo ? 1 : 0); ++l) {  // layer H: dW_out, 4 rows
+    if (tc_dwo && tc_dwo_transposed<W>()) {  // dW_out^T: row i of TMEM holds dW_out[0..3][i]
+        if (half == 0) {
+            float v[8];
+            tmem_ld8(lane_base + dw_col<W, IN>(H), v);
+            const int i = 16 * quad + lane;
+            if (lane < 16) {
+                float *dst = gw + IN * W + (H - 1) * W * W + i;
+                const float f = inv_scale * inv_enc;
+#pragma unroll
+                for (int o = 0; o < 4; ++o)
+                    red_add_f(dst + o * W, v[o] * f);
+            }
+        }
+    }
+    for (int l = 0; l < H + (tc_dwo && !tc_dwo_transposed<W>() ? 1 : 0); ++l) {  // layer H: dW_out, 4 rows
         const int ncol = l == 0 ? INP : W;
         const int nin = l == 0 ? IN : W;
         const int nrow = l == H ? 4 : W;
@@ -454,6 +480,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint32_t id_dh = mma_idesc(Hf::fmt, 128, W, 0, 1);
     const uint32_t id_dx = mma_idesc(Hf::fmt, 128, INP, 0, 1);
     const uint32_t id_dw = mma_idesc(Hf::fmt, 64, W, 1, 1);
+    const uint32_t id_dwo_t = mma_idesc(Hf::fmt, 64, 16, 1, 1);  // dW_out^T (W = 64)
     const uint32_t id_dw0 = mma_idesc(Hf::fmt, 64, INP, 1, 1);
 
     uint32_t parity = 0;
@@ -685,9 +712,14 @@ __global__ void __launch_bounds__(kThreads, 2)
                 else
                     mma_gemm<W>(tmem, kmajor(DA, kDaCols), mnmajor(WtH + l * L::wh, W), id_dh, false);
                 mma_commit(mbar);
-                if (l == H - 1 && tc_dwo)  // dW_out += dO^T H_{H-1}, rows 0..3 of M = 64 (a later commit covers it)
-                    mma_gemm<kTcTile>(tmem + dw_col<W, IN>(H), mnmajor(DOA, kDaCols),
-                                      mnmajor(HA + (H - 1) * L::ha, W), id_dw, !first_dw, kdw);
+                if (l == H - 1 && tc_dwo) {  // dW_out (a later commit covers it)
+                    if constexpr (tc_dwo_transposed<W>())  // dW_out^T += H_{H-1}^T dO
+                        mma_gemm<kTcTile>(tmem + dw_col<W, IN>(H), mnmajor(HA + (H - 1) * L::ha, W),
+                                          mnmajor(DOA, 16), id_dwo_t, !first_dw, kdw);
+                    else  // dW_out += dO^T H_{H-1}, rows 0..3 of M = 64
+                        mma_gemm<kTcTile>(tmem + dw_col<W, IN>(H), mnmajor(DOA, kDaCols),
+                                          mnmajor(HA + (H - 1) * L::ha, W), id_dw, !first_dw, kdw);
+                }
             }
             if (l == H - 1 && !tc_dwo) {
                 // dW_out[o][i0..i0+7] on the CUDA cores while the tensor cores form dH_{H-1}:
