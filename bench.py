@@ -610,6 +610,13 @@ def _single_compare(pkg, ctx, stream, prec, rank, steps, warmup):
         f = lambda i: ctx.train_step([dev[i % len(dev)]], opts, loss)  # noqa: E731
         ms = _time(stream, f, steps, warmup)
         out[form] = {"value": N_RAYS * NR * steps / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms / steps}
+        ctx.enable_timing(True)  # per-kernel device times of the same steps, launched directly
+        _time(stream, f, max(steps // 4, 5), 0)
+        out[form]["kernels_us"] = {lab.split()[6] + " " + pkg.KERNEL_NAMES[k]: round(1e3 * t_ms / n, 2)
+                                   for lab, k, t_ms, n in ctx.timing_report()}
+        ad = ctx.kernel_time(pkg.PRENOM_KERNEL_ADAM)
+        out[form]["kernels_us"]["adam"] = round(1e3 * ad[0] / max(ad[1], 1), 2)
+        ctx.enable_timing(False)
         ctx.destroy_object(obj)
     out["speedup"] = out[prec]["value"] / out["fp32"]["value"]
     return out

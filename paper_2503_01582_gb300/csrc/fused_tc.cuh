@@ -671,14 +671,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         if (!ok)
             break;
-        // ---- compositing, loss and its adjoint (FP32)
-        // (the sampler's CDF scratch serves as the compositing's exchange buffer)
-        loss_acc += composite_tile(od, bd, ray0, nrt, rayf, ts, OT, dOT, SP, cdfs);
-        __syncthreads();
-        if (!train)
-            continue;
         pre_t = -1;
-        if (split && t + 1 < t1 && tile + 1 < bd.n_tiles) {  // the next tile of this item: issue its loads now
+        if (split && t + 1 < t1 && tile + 1 < bd.n_tiles) {  // the next tile of this item: issue its loads now,
+            // so that they are in flight through the compositing and the backward pass
             const int tile2 = tile + 1, ray02 = tile2 * NR;
             const int ns2 = min(NR, bd.n_rays - ray02) * nr, nr2 = min(NR, bd.n_rays - ray02) * kRayStride;
             const uint4 *src = bd.sp_x + (size_t)tile2 * (kSplitXBytes / 16);
@@ -692,6 +687,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             pt0 = tid < ns2 ? bd.sp_t[(size_t)ray02 * nr + tid] : 0.f;
             pre_t = t + 1;
         }
+        // ---- compositing, loss and its adjoint (FP32)
+        // (the sampler's CDF scratch serves as the compositing's exchange buffer)
+        loss_acc += composite_tile(od, bd, ray0, nrt, rayf, ts, OT, dOT, SP, cdfs);
+        __syncthreads();
+        if (!train)
+            continue;
         // ---- scaled 16-bit dL/dO (dW_out is summed during the first backward product)
         if (tid < kTcTile) {
             uint32_t lo = (uint32_t)Hf::bits(dOT[tid] * scale) | ((uint32_t)Hf::bits(dOT[SP + tid] * scale) << 16);
