@@ -213,9 +213,10 @@ def gpu_identifier(dev: int) -> str:
         return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+def profiled(kernel: str):
+    """A kernel's record in the committed ncu summary (DRAM bytes per launch and,
+    where captured, L2 throughput and L2 reduction requests), if it was taken
+    on the current kernel sources (else None)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -232,7 +233,27 @@ def profiled_traffic(kernel: str):
             h.update(f.read())
     if h.hexdigest() != rec.get("sources_sha256"):
         return None
-    return float(rec["dram_bytes_per_launch"])
+    return rec
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary (None if it was
+    taken on other kernel sources)."""
+    rec = profiled(kernel)
+    return float(rec["dram_bytes_per_launch"]) if rec else None
+
+
+def profiled_l2(kernel: str, samples: int):
+    """The launch's L2 figures from the committed ncu summary: lts__throughput
+    (% of peak) and, for the scatter, L2 reduction requests per sample."""
+    rec = profiled(kernel)
+    if not rec or "lts_pct" not in rec:
+        return None
+    out = {"lts_pct_of_peak": rec["lts_pct"]}
+    if rec.get("l2_red_requests"):
+        out["l2_red_requests"] = rec["l2_red_requests"]
+        out["red_per_sample"] = round(rec["l2_red_requests"] / max(samples, 1), 3)
+    return out
 
 
 
@@ -844,9 +865,11 @@ def _roofline(pkg, report, specs, prec, adam_ms, n_params, peaks):
         rec = kernels.setdefault(name, dict(kernel=name, unit=unit, work=0.0, t=0.0, groups=[], what=what, **base))
         rec["work"] += work
         rec["t"] += t
-        rec["groups"].append({"group": label, "avg_us": round(t * 1e6, 2), "achieved": round(work / t / scale, 2),
-                              "frac": round(work / t / scale / rec["peak"], 4),
-                              "traffic": profiled_traffic(f"{name}/{prec}/W{W}")})
+        grp = {"group": label, "avg_us": round(t * 1e6, 2), "achieved": round(work / t / scale, 2),
+               "frac": round(work / t / scale / rec["peak"], 4), "traffic": profiled_traffic(f"{name}/{prec}/W{W}")}
+        if name in ("sample_encode_kernel", "hash_scatter_kernel"):  # bound by L1/L2 requests, not DRAM bytes
+            grp["l2"] = profiled_l2(f"{name}/{prec}/W{W}", samples)
+        rec["groups"].append(grp)
     kernels["adam_kernel"] = dict(kernel="adam_kernel", unit="GB/s", work=n_params * 28.0, t=adam_ms / 1e3, groups=[],
                                   what="28 B/parameter (read g, m, v, theta; write m, v, theta)", bound="hbm",
                                   peak=peaks["hbm_gbs"], peak_src=peaks["src"] + " copy bandwidth")
