@@ -398,11 +398,13 @@ PRENOM_API int prenom_capture_count(prenom_ctx *ctx, int64_t *captures, int64_t 
  * buf: host, cap bytes, NUL-terminated, truncated to fit. */
 PRENOM_API int prenom_timing_report(prenom_ctx *ctx, char *buf, size_t cap);
 
-/* The autotuner's record as text (one line per group signature: the step
- * times in ms of each timed call, "cK" = candidate K, and the chosen candidate
+/* The autotuner's record as text (one line per group signature: the group's
+ * own device time in ms (its launches, between events) in each timed call,
+ * "cK" = candidate K, and the chosen candidate
  * after "->"; candidates: c0 the split form whose scatter sums the lanes of one
  * grid cell in chunks of four, c1 the split form summing whole runs of such
- * lanes, c2 c3 the fused kernel in one wave / with 16 tiles per CTA; with
+ * lanes, c2 c3 the fused kernel in one wave / with 16 tiles per CTA, c4 c5 as
+ * c0 c1 with the sampling-encoding kernel at 3 instead of 4 CTAs per SM; with
  * PRENOM_FLAG_FUSED: the fused kernel in one wave / 16 / 8 / 4 tiles per CTA;
  * PRENOM_FLAG_SPLIT: c0 untuned).  buf: host, cap bytes, NUL-terminated,
  * truncated to fit. */

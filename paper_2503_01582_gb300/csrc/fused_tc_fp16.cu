@@ -13,9 +13,9 @@ int fused_tc_occupancy_fp16(int W, int IN, int H, bool split)
     return tc_occupancy_prec<false>(W, IN, H, split);
 }
 
-cudaError_t launch_sample_encode_fp16(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
+cudaError_t launch_sample_encode_fp16(const WorkItem &one, const WorkList &wl, int per_sm, int grid, cudaStream_t st)
 {
-    return launch_sample_encode_t<0>(one, wl, grid, st);
+    return launch_sample_encode_t<0>(one, wl, per_sm, grid, st);
 }
 
 }  // namespace prenom

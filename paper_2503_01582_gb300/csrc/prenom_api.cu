@@ -359,11 +359,12 @@ size_t assign_split(BatchDesc &bd, unsigned char *base)
 }
 
 // Grids of the split form's two extra kernels: the sampling-encoding kernel
-// runs one warp per ray slot, the scatter kernel one block per tile range.
-int grid_sample_encode(const prenom_ctx *c, int total_tiles, int rays_per_tile)
+// runs one warp per ray slot with per_sm (4 or 3) CTAs per SM, the scatter
+// kernel one block per tile range.
+int grid_sample_encode(const prenom_ctx *c, int total_tiles, int rays_per_tile, int per_sm = 4)
 {
     const int64_t slots = (int64_t)total_tiles * rays_per_tile;  // one block per slot at most
-    return (int)std::max<int64_t>(1, std::min<int64_t>(slots, (int64_t)c->n_sm * 4));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(slots, (int64_t)c->n_sm * per_sm));
 }
 
 int grid_scatter(const prenom_ctx *c, int total_tiles)
@@ -406,7 +407,7 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
             const WorkList wl{nullptr, 1, bd.n_tiles, od.H, 1, od.feat16 != nullptr};
             cudaEvent_t ev;
             timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
-            cudaError_t e = launch_sample_encode(one, wl, o.arch.precision,
+            cudaError_t e = launch_sample_encode(one, wl, o.arch.precision, 4,
                                                  grid_sample_encode(c, bd.n_tiles, bd.rays_per_tile), c->stream);
             timed_end(c, PRENOM_KERNEL_SAMPLE_ENCODE, ev);
             if (e != cudaSuccess)
@@ -450,7 +451,7 @@ int launch_fused(prenom_ctx *c, const Object &o, const ObjDesc &od, BatchDesc &b
         const WorkList wl{nullptr, 1, bd.n_tiles, od.H, 1};
         cudaEvent_t ev;
         timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
-        cudaError_t e = launch_sample_encode(one, wl, PRENOM_PRECISION_FP32,
+        cudaError_t e = launch_sample_encode(one, wl, PRENOM_PRECISION_FP32, 4,
                                              grid_sample_encode(c, bd.n_tiles, bd.rays_per_tile), c->stream);
         timed_end(c, PRENOM_KERNEL_SAMPLE_ENCODE, ev);
         if (e != cudaSuccess)
@@ -564,6 +565,7 @@ struct Group {
     int precision, W, IN, S, hmax, first, count, total_tiles, grid;
     bool split = false;  // mixed precision: the three-kernel split form
     bool whole_runs = false;  // split form: the scatter sums whole runs of lanes
+    int enc_per_sm = 4;       // split form: resident CTAs per SM of the sampling-encoding kernel
     int feat16 = 0;      // the group's gathers read BF16 copies of the tables
 };
 
@@ -580,23 +582,32 @@ struct Plan {
 // Candidates of the autotuner: tiles per CTA of the training kernel (0 = one
 // persistent wave of resident CTAs).  A group tries the split form first (its
 // MLP kernel in one wave), with the scatter summing lanes of one cell in chunks
-// of four (c0) or over whole runs (c1), then the fused kernel in one wave and
-// with 16 tiles per CTA; with the split form excluded, the fused kernel with
-// four work-chunk sizes.
+// of four (c0) or over whole runs (c1), then the fused kernel in one wave (c2)
+// and with 16 tiles per CTA (c3), then the split form again with the
+// sampling-encoding kernel at 3 CTAs per SM instead of 4 (c4: chunks of four,
+// c5: whole runs); with the split form excluded, the fused kernel with four
+// work-chunk sizes.
 constexpr int kTuneTpc[] = {0, 16, 8, 4};
-constexpr int kTuneTpcTc[] = {0, 0, 0, 16};
-constexpr int kTuneN = 4;
+constexpr int kTuneTpcTc[] = {0, 0, 0, 16, 0, 0};
+constexpr int kTuneNSplit = 6, kTuneNFused = 4;
 constexpr int kTuneRounds = 2;  // each candidate is timed this many times (one whole step each)
 constexpr size_t kMaxGraphs = 64;  // captured step graphs kept per context
 
+int tune_n(bool split_allowed) { return split_allowed ? kTuneNSplit : kTuneNFused; }
+
 bool cand_split(const Group &, int cand, bool split_allowed)
 {
-    return split_allowed && cand <= 1;
+    return split_allowed && (cand <= 1 || cand >= 4);
 }
 
 bool cand_whole_runs(int cand, bool split_allowed)
 {
-    return split_allowed && cand == 1;
+    return split_allowed && (cand == 1 || cand == 5);
+}
+
+int cand_enc_per_sm(int cand, bool split_allowed)
+{
+    return split_allowed && cand >= 4 ? 3 : 4;
 }
 
 int group_grid(const prenom_ctx *c, const Group &g, int cand, bool split_allowed)
@@ -636,9 +647,11 @@ std::string group_label(const Group &g)
 {
     static const char *prec[] = {"fp32", "fp16", "bf16"};
     char buf[160];
+    const char *form = !g.split ? "fused"
+                       : g.whole_runs ? (g.enc_per_sm == 3 ? "split-runs-enc3" : "split-runs")
+                                      : (g.enc_per_sm == 3 ? "split-enc3" : "split");
     snprintf(buf, sizeof(buf), "%s W%d IN%d H%d batches%d tiles%d %s grid%d%s", prec[g.precision], g.W, g.IN, g.hmax,
-             g.count, g.total_tiles, g.split ? (g.whole_runs ? "split-runs" : "split") : "fused", g.grid,
-             g.feat16 ? " bf16-features" : "");
+             g.count, g.total_tiles, form, g.grid, g.feat16 ? " bf16-features" : "");
     return buf;
 }
 
@@ -736,7 +749,11 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
 }
 
 // Enqueues one batched step on the context's stream (also used under capture).
-cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *stage, size_t bytes, bool timed)
+// group_ev (optional, groups + 1 events): recorded before each group's launches
+// and after the last group's, so that group gi's device time lies between
+// group_ev[gi] and group_ev[gi + 1].
+cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *stage, size_t bytes, bool timed,
+                            cudaEvent_t *group_ev = nullptr)
 {
     const size_t items_bytes = p.items.size() * sizeof(WorkItem);
     const WorkItem *d_items = reinterpret_cast<const WorkItem *>(c->d_work);
@@ -745,7 +762,10 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     if (e == cudaSuccess)
         e = launch_zero_losses(d_items, (int)p.items.size(), c->stream);
     const WorkItem unused{};
-    for (const Group &g : p.groups) {
+    for (size_t gi = 0; gi < p.groups.size(); ++gi) {
+        const Group &g = p.groups[gi];
+        if (group_ev && e == cudaSuccess)
+            e = cudaEventRecord(group_ev[gi], c->stream);
         if (e != cudaSuccess || g.total_tiles == 0)
             continue;
         const WorkList wl{d_items + g.first, g.count, g.total_tiles, g.hmax, g.split ? 1 : 0, g.feat16};
@@ -754,8 +774,9 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
         if (g.split) {
             if (timed)
                 timed_begin(c, PRENOM_KERNEL_SAMPLE_ENCODE, &ev);
-            e = launch_sample_encode(unused, wl, g.precision,
-                                     grid_sample_encode(c, g.total_tiles, p.items[g.first].bd.rays_per_tile),
+            e = launch_sample_encode(unused, wl, g.precision, g.enc_per_sm,
+                                     grid_sample_encode(c, g.total_tiles, p.items[g.first].bd.rays_per_tile,
+                                                        g.enc_per_sm),
                                      c->stream);
             if (timed)
                 timed_end(c, PRENOM_KERNEL_SAMPLE_ENCODE, ev);
@@ -777,6 +798,8 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
         }
     }
     c->cur_group = -1;
+    if (group_ev && e == cudaSuccess)
+        e = cudaEventRecord(group_ev[p.groups.size()], c->stream);
     if (e == cudaSuccess && p.adam_grid > 0) {
         AdamArgs a = p.adam;
         for (int s = 0; s < a.n_segs; ++s)
@@ -826,12 +849,13 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         } else if (it != c->tune_best.end()) {
             cand = it->second;
         } else {
-            cand = (int)c->tune_ms[gkeys.back()].size() % kTuneN;  // two rounds over the candidates
+            cand = (int)c->tune_ms[gkeys.back()].size() % tune_n(split_allowed);  // two rounds over the candidates
             tuning = true;
         }
         g.grid = group_grid(c, g, cand, split_allowed);
         g.split = cand_split(g, cand, split_allowed);
         g.whole_runs = cand_whole_runs(cand, split_allowed);
+        g.enc_per_sm = cand_enc_per_sm(cand, split_allowed);
     }
     // buffers of the split groups (planned before any staging or capture)
     size_t split_need = 0;
@@ -890,18 +914,26 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         return PRENOM_OK;  // nothing to capture (still tuning, timing on, legacy stream or graphs off)
     if (tuning) {
         c->n_tune_calls++;
-        cudaEvent_t t0, t1;
-        cudaEventCreate(&t0);
-        cudaEventCreate(&t1);
-        cudaEventRecord(t0, c->stream);
-        e = enqueue_batched(c, p, c->h_stage[b], bytes, false);
-        cudaEventRecord(t1, c->stream);
-        cudaEventSynchronize(t1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, t0, t1);
-        cudaEventDestroy(t0);
-        cudaEventDestroy(t1);
-        for (size_t gi = 0; gi < p.groups.size(); ++gi) {  // whole-step time, charged to each tuned group
+        // each group is charged its own launches' device time, so that groups of one
+        // step settle on candidates of their own
+        std::vector<cudaEvent_t> gev(p.groups.size() + 1, nullptr);
+        for (cudaEvent_t &x : gev)
+            if (e == cudaSuccess)
+                e = cudaEventCreate(&x);
+        if (e == cudaSuccess)
+            e = enqueue_batched(c, p, c->h_stage[b], bytes, false, gev.data());
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(gev.back());
+        std::vector<float> gms(p.groups.size(), 0.f);
+        for (size_t gi = 0; gi < p.groups.size() && e == cudaSuccess; ++gi)
+            e = cudaEventElapsedTime(&gms[gi], gev[gi], gev[gi + 1]);
+        for (cudaEvent_t x : gev)
+            if (x)
+                cudaEventDestroy(x);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "autotuner step");
+        for (size_t gi = 0; gi < p.groups.size(); ++gi) {
+            const float ms = gms[gi];
             std::vector<float> &v = c->tune_ms[gkeys[gi]];
             if (c->tune_best.count(gkeys[gi]) || split_forced)
                 continue;
@@ -910,13 +942,14 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
                 continue;
             }
             v.push_back(ms);
-            if ((int)v.size() == kTuneRounds * kTuneN) {  // keep the candidate with the best of its rounds
+            const int nc = tune_n(split_allowed);
+            if ((int)v.size() == kTuneRounds * nc) {  // keep the candidate with the best of its rounds
                 int best = 0;
                 float best_ms = INFINITY;
                 for (size_t k = 0; k < v.size(); ++k)
                     if (v[k] < best_ms) {
                         best_ms = v[k];
-                        best = (int)(k % kTuneN);
+                        best = (int)(k % nc);
                     }
                 c->tune_best[gkeys[gi]] = best;
             }
@@ -924,7 +957,8 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
     } else if (use_graph) {
         std::string key = std::to_string(b) + ":" + std::to_string(bytes) + ":" + std::to_string(p.adam_grid);
         for (const Group &g : p.groups)
-            key += "|" + group_key(g) + "/" + std::to_string(g.grid) + (g.split ? (g.whole_runs ? "w" : "s") : "f");
+            key += "|" + group_key(g) + "/" + std::to_string(g.grid) + (g.split ? (g.whole_runs ? "w" : "s") : "f") +
+                   std::to_string(g.enc_per_sm);
         for (int32_t id : p.touched)
             key += "," + std::to_string(id);
         char tail[96];
@@ -1345,7 +1379,7 @@ int prenom_autotune(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_ba
     // the autotuner's calls, as gradient-only steps (no Adam, no step count)
     prenom_train_opts t = *op;
     t.flags |= PRENOM_FLAG_NO_ADAM;
-    for (int i = 0; i < 2 + kTuneN * kTuneRounds; ++i) {
+    for (int i = 0; i < 2 + kTuneNSplit * kTuneRounds; ++i) {
         const bool pending = tuning_pending(c, batches, n_batches, t, &rc);
         if (rc)
             return rc;
@@ -1778,8 +1812,9 @@ int prenom_tuning_report(prenom_ctx *c, char *buf, size_t cap)
     for (const auto &kv : c->tune_ms) {
         r += kv.first + ":";
         char tmp[48];
+        const bool split_key = kv.first.size() >= 2 && kv.first.compare(kv.first.size() - 2, 2, "/s") == 0;
         for (size_t k = 0; k < kv.second.size(); ++k) {
-            snprintf(tmp, sizeof(tmp), " c%d=%.4f", (int)(k % kTuneN), kv.second[k]);
+            snprintf(tmp, sizeof(tmp), " c%d=%.4f", (int)(k % tune_n(split_key)), kv.second[k]);
             r += tmp;
         }
         auto it = c->tune_best.find(kv.first);

@@ -112,7 +112,10 @@ cudaError_t launch_fused_tc_fp16(const WorkItem &one, const WorkList &wl, int W,
 // Split execution of a mixed-precision training step: sampling + encoding,
 // then the tensor-core kernel without its scatter, then the hash scatter.
 // wl.items == nullptr means the single item `one`.
-cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int precision, int grid, cudaStream_t st);
+// per_sm: 4 or 3 resident CTAs per SM (the registers budget of the variant; the
+// grid is sized by the caller to match)
+cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int precision, int per_sm, int grid,
+                                 cudaStream_t st);
 // whole_runs: lanes of one cell summed over whole runs instead of chunks of four.
 cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st,
                                 bool whole_runs = false);

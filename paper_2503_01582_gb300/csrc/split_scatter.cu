@@ -81,14 +81,16 @@ __global__ void __launch_bounds__(kThreads, 5)
     }
 }
 
-cudaError_t launch_sample_encode_fp16(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st);
-cudaError_t launch_sample_encode_bf16(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st);
+cudaError_t launch_sample_encode_fp16(const WorkItem &one, const WorkList &wl, int per_sm, int grid, cudaStream_t st);
+cudaError_t launch_sample_encode_bf16(const WorkItem &one, const WorkList &wl, int per_sm, int grid, cudaStream_t st);
 
-cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int precision, int grid, cudaStream_t st)
+cudaError_t launch_sample_encode(const WorkItem &one, const WorkList &wl, int precision, int per_sm, int grid,
+                                 cudaStream_t st)
 {
     if (precision == 0)
-        return launch_sample_encode_t<2>(one, wl, grid, st);
-    return precision == 2 ? launch_sample_encode_bf16(one, wl, grid, st) : launch_sample_encode_fp16(one, wl, grid, st);
+        return launch_sample_encode_t<2>(one, wl, per_sm, grid, st);
+    return precision == 2 ? launch_sample_encode_bf16(one, wl, per_sm, grid, st)
+                          : launch_sample_encode_fp16(one, wl, per_sm, grid, st);
 }
 
 cudaError_t launch_hash_scatter(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st, bool whole_runs)

@@ -42,8 +42,11 @@ __host__ __device__ __forceinline__ int enc_rays_per_warp(int nr)
 // FMT: 0 FP16 or 1 BF16 image in the tensor-core kernel's operand layout, 2 FP32
 // feature-major image [IN][kSplitTile] for the FP32 kernel.
 // F16: the items' gathers read the BF16 copies of their tables (FMT 0 or 1 only).
-template <int FMT, bool F16>
-__global__ void __launch_bounds__(kThreads, 4)
+// MINB: resident CTAs per SM the registers are budgeted for (4: 64 registers a
+// thread; 3: more registers and fewer warps, which suits gathers that hit in
+// L1 and L2 better than gathers that go to DRAM; the autotuner picks per group).
+template <int FMT, bool F16, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     sample_encode_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
     using Hf = Half<FMT == 1>;
@@ -159,15 +162,21 @@ __global__ void __launch_bounds__(kThreads, 4)
 }
 
 template <int FMT>
-cudaError_t launch_sample_encode_t(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
+cudaError_t launch_sample_encode_t(const WorkItem &one, const WorkList &wl, int per_sm, int grid, cudaStream_t st)
 {
     if constexpr (FMT != 2) {
         if (wl.feat16) {
-            sample_encode_kernel<FMT, true><<<grid, kThreads, 0, st>>>(one, wl);
+            if (per_sm == 3)
+                sample_encode_kernel<FMT, true, 3><<<grid, kThreads, 0, st>>>(one, wl);
+            else
+                sample_encode_kernel<FMT, true, 4><<<grid, kThreads, 0, st>>>(one, wl);
             return cudaGetLastError();
         }
     }
-    sample_encode_kernel<FMT, false><<<grid, kThreads, 0, st>>>(one, wl);
+    if (per_sm == 3)
+        sample_encode_kernel<FMT, false, 3><<<grid, kThreads, 0, st>>>(one, wl);
+    else
+        sample_encode_kernel<FMT, false, 4><<<grid, kThreads, 0, st>>>(one, wl);
     return cudaGetLastError();
 }
 
