@@ -214,7 +214,8 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * Adam launch then updates every object.
  * A single batch takes the same path.  The first calls of a new group
  * signature (kernel variant, and batch and tile counts rounded down to powers
- * of two; one untimed call, then two rounds over the candidates) try the
+ * of two; one untimed call, then three rounds over the candidates, each
+ * candidate judged by its median) try the
  * split form and several work-chunk sizes (tiles per CTA) and keep the
  * fastest; afterwards, on a non-default stream and with timing off, the whole
  * step is captured once per exact signature as a CUDA graph and replayed
@@ -373,7 +374,7 @@ PRENOM_API int prenom_canonical_yaw(prenom_ctx *ctx, int32_t obj, const float *p
 /* Runs, ahead of training, what the first calls of prenom_train_step() with
  * these batches and options would otherwise do inside the training loop: the
  * autotuner's calls for every group signature not yet tuned (one untimed call,
- * then two rounds over the candidates), run as gradient-only steps -- no Adam
+ * then three rounds over the candidates), run as gradient-only steps -- no Adam
  * update, no change of theta, Adam moments or step counts; the gradients they
  * accumulate and any 16-bit overflow flag they raise are cleared afterwards --
  * and the capture of the step's CUDA graph for both staging buffers (when

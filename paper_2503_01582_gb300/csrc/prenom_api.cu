@@ -590,7 +590,7 @@ struct Plan {
 constexpr int kTuneTpc[] = {0, 16, 8, 4};
 constexpr int kTuneTpcTc[] = {0, 0, 0, 16, 0, 0};
 constexpr int kTuneNSplit = 6, kTuneNFused = 4;
-constexpr int kTuneRounds = 2;  // each candidate is timed this many times (one whole step each)
+constexpr int kTuneRounds = 3;  // each candidate is timed this many times (one step each); the median counts
 constexpr size_t kMaxGraphs = 64;  // captured step graphs kept per context
 
 int tune_n(bool split_allowed) { return split_allowed ? kTuneNSplit : kTuneNFused; }
@@ -943,14 +943,19 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
             }
             v.push_back(ms);
             const int nc = tune_n(split_allowed);
-            if ((int)v.size() == kTuneRounds * nc) {  // keep the candidate with the best of its rounds
+            if ((int)v.size() == kTuneRounds * nc) {  // keep the candidate with the lowest median over its rounds
                 int best = 0;
                 float best_ms = INFINITY;
-                for (size_t k = 0; k < v.size(); ++k)
-                    if (v[k] < best_ms) {
-                        best_ms = v[k];
-                        best = (int)(k % nc);
+                for (int k = 0; k < nc; ++k) {
+                    float r[kTuneRounds];
+                    for (int q = 0; q < kTuneRounds; ++q)
+                        r[q] = v[(size_t)q * nc + k];
+                    std::sort(r, r + kTuneRounds);
+                    if (r[kTuneRounds / 2] < best_ms) {
+                        best_ms = r[kTuneRounds / 2];
+                        best = k;
                     }
+                }
                 c->tune_best[gkeys[gi]] = best;
             }
         }

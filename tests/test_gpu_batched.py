@@ -92,12 +92,13 @@ def test_batched_gradients_match_per_object_and_oracle(pkg):
 
 
 def test_batched_adam_graph_replay_and_autotuner(pkg):
-    """Sixteen batched steps on a side stream: the first thirteen tune (one
-    untimed call, then two rounds over the six candidates: the split form with
+    """Twenty-four batched steps on a side stream: the first nineteen tune (one
+    untimed call, then three rounds over the six candidates: the split form with
     two scatter variants and two encoder occupancies, the fused kernel with two
-    work-chunk sizes), the rest replay a captured graph while the ray buffers change; the losses and
-    parameters follow the same objects stepped one at a time (with
-    PRENOM_FLAG_CHECK_FINITE, i.e. one launch per object, untuned)."""
+    work-chunk sizes), the rest replay a captured graph while the ray buffers
+    change; the losses and parameters follow the same objects stepped one at a
+    time (with PRENOM_FLAG_CHECK_FINITE, i.e. one launch per object, untuned),
+    whose copies restart from the batched state after 12 steps."""
     import torch
 
     objs = _setup()
@@ -111,7 +112,7 @@ def test_batched_adam_graph_replay_and_autotuner(pkg):
     sets = [[_batch(o, i) for o, i in zip(src, ids_b)] for src in (objs, alt)]
     torch.cuda.synchronize()
     at12 = None
-    for step in range(16):
+    for step in range(24):
         src = objs if step % 2 == 0 else alt
         with torch.cuda.stream(stream):
             ctx_b.train_step(sets[step % 2], opts, loss_b)
@@ -124,19 +125,22 @@ def test_batched_adam_graph_replay_and_autotuner(pkg):
         if step == 11:
             at12 = [(ctx_b.get_state(ib).cpu().numpy(), ctx_s.get_state(i_s).cpu().numpy())
                     for ib, i_s in zip(ids_b, ids_s)]
+            # rounding-level differences that Adam amplifies make the two copies drift apart
+            # over many steps: restart the per-object copies from the batched state, so that
+            # every later step is again compared from identical parameters and moments
+            for ib, i_s in zip(ids_b, ids_s):
+                for w in (pkg.PRENOM_STATE_THETA, pkg.PRENOM_STATE_ADAM_M, pkg.PRENOM_STATE_ADAM_V):
+                    ctx_s.set_state(i_s, w, ctx_b.get_state(ib, w))
     assert ctx_b.capture_count()[0] > 0  # the last steps replayed captured graphs
     for k in range(len(objs)):
-        assert ctx_b.get_step(ids_b[k]) == 16
+        assert ctx_b.get_step(ids_b[k]) == 24
         # Adam normalises each entry, so an entry whose gradient is at rounding level may step either
-        # way (by at most lr per step), and such differences feed later gradients: compare in bulk
-        # after 12 steps, and bound every entry by Adam's step size after 12 and 16
-        tb, ts = at12[k]
-        close = np.abs(tb - ts) <= 1e-4 * np.abs(ts).max() + 1e-6
-        assert np.mean(close) > 0.99, (k, np.mean(close))
-        assert np.abs(tb - ts).max() <= 2 * 1e-2 * 12 * 1.01, k
-        tb = ctx_b.get_state(ids_b[k]).cpu().numpy()
-        ts = ctx_s.get_state(ids_s[k]).cpu().numpy()
-        assert np.abs(tb - ts).max() <= 2 * 1e-2 * 16 * 1.01, k
+        # way (by at most lr per step): compare in bulk, and bound every entry by Adam's step size,
+        # over the 12 steps before and the 12 steps after the restart
+        for tb, ts in (at12[k], (ctx_b.get_state(ids_b[k]).cpu().numpy(), ctx_s.get_state(ids_s[k]).cpu().numpy())):
+            close = np.abs(tb - ts) <= 1e-4 * np.abs(ts).max() + 1e-6
+            assert np.mean(close) > 0.99, (k, np.mean(close))
+            assert np.abs(tb - ts).max() <= 2 * 1e-2 * 12 * 1.01, k
     ctx_b.close()
     ctx_s.close()
 
