@@ -78,6 +78,10 @@ struct prenom_ctx {
     size_t h_stage_cap = 0;
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     int stage_idx = 0;
+    // the groups of a batched step after the first run on streams of their own,
+    // forked from the context's stream and joined back before Adam
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_ev;  // [0] the fork, [1 + i] the join of side stream i
     struct CachedGraph {
         cudaGraphExec_t exec;
         uint64_t last_use;
@@ -749,6 +753,27 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
 }
 
 // Enqueues one batched step on the context's stream (also used under capture).
+// Side streams and events for the concurrent groups of a batched step (created
+// outside any graph capture).
+cudaError_t ensure_side(prenom_ctx *c, size_t n_groups)
+{
+    const size_t n_side = n_groups > 1 ? n_groups - 1 : 0;
+    cudaError_t e = cudaSuccess;
+    while (e == cudaSuccess && c->side.size() < n_side) {
+        cudaStream_t s2 = nullptr;
+        e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            c->side.push_back(s2);
+    }
+    while (e == cudaSuccess && c->side_ev.size() < n_side + 1) {
+        cudaEvent_t ev2 = nullptr;
+        e = cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            c->side_ev.push_back(ev2);
+    }
+    return e;
+}
+
 // group_ev (optional, groups + 1 events): recorded before each group's launches
 // and after the last group's, so that group gi's device time lies between
 // group_ev[gi] and group_ev[gi + 1].
@@ -762,8 +787,18 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     if (e == cudaSuccess)
         e = launch_zero_losses(d_items, (int)p.items.size(), c->stream);
     const WorkItem unused{};
+    // groups run concurrently (their buffers are disjoint), except when kernels or
+    // groups are timed one by one; the side streams exist already (ensure_side)
+    const bool fork = !timed && !group_ev && c->stream != nullptr && p.groups.size() > 1 &&
+                      c->side.size() + 1 >= p.groups.size() && c->side_ev.size() >= p.groups.size();
+    const size_t n_side = fork ? p.groups.size() - 1 : 0;
+    if (fork && e == cudaSuccess)
+        e = cudaEventRecord(c->side_ev[0], c->stream);
+    for (size_t i = 0; i < n_side && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0);
     for (size_t gi = 0; gi < p.groups.size(); ++gi) {
         const Group &g = p.groups[gi];
+        cudaStream_t st = (fork && gi > 0) ? c->side[gi - 1] : c->stream;
         if (group_ev && e == cudaSuccess)
             e = cudaEventRecord(group_ev[gi], c->stream);
         if (e != cudaSuccess || g.total_tiles == 0)
@@ -777,7 +812,7 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
             e = launch_sample_encode(unused, wl, g.precision, g.enc_per_sm,
                                      grid_sample_encode(c, g.total_tiles, p.items[g.first].bd.rays_per_tile,
                                                         g.enc_per_sm),
-                                     c->stream);
+                                     st);
             if (timed)
                 timed_end(c, PRENOM_KERNEL_SAMPLE_ENCODE, ev);
             if (e != cudaSuccess)
@@ -785,19 +820,27 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
         }
         if (timed)
             timed_begin(c, PRENOM_KERNEL_TRAIN, &ev);
-        e = g.precision == PRENOM_PRECISION_FP32 ? launch_fused_fp32_list(wl, g.W, g.IN, g.S, g.grid, c->stream)
-                                                 : launch_fused_tc_list(wl, g.W, g.IN, g.precision, g.grid, c->stream);
+        e = g.precision == PRENOM_PRECISION_FP32 ? launch_fused_fp32_list(wl, g.W, g.IN, g.S, g.grid, st)
+                                                 : launch_fused_tc_list(wl, g.W, g.IN, g.precision, g.grid, st);
         if (timed)
             timed_end(c, PRENOM_KERNEL_TRAIN, ev);
         if (g.split && e == cudaSuccess) {
             if (timed)
                 timed_begin(c, PRENOM_KERNEL_SCATTER, &ev);
-            e = launch_hash_scatter(unused, wl, grid_scatter(c, g.total_tiles), c->stream, g.whole_runs);
+            e = launch_hash_scatter(unused, wl, grid_scatter(c, g.total_tiles), st, g.whole_runs);
             if (timed)
                 timed_end(c, PRENOM_KERNEL_SCATTER, ev);
         }
     }
     c->cur_group = -1;
+    // the join (also after an error, so that a capture in progress ends with every stream joined)
+    for (size_t i = 0; i < n_side && i + 1 < c->side_ev.size(); ++i) {
+        cudaError_t e2 = cudaEventRecord(c->side_ev[1 + i], c->side[i]);
+        if (e2 == cudaSuccess)
+            e2 = cudaStreamWaitEvent(c->stream, c->side_ev[1 + i], 0);
+        if (e == cudaSuccess)
+            e = e2;
+    }
     if (group_ev && e == cudaSuccess)
         e = cudaEventRecord(group_ev[p.groups.size()], c->stream);
     if (e == cudaSuccess && p.adam_grid > 0) {
@@ -973,7 +1016,9 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         if (it == c->graphs.end()) {
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
-            e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+            e = ensure_side(c, p.groups.size());
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 const cudaError_t e1 = enqueue_batched(c, p, c->h_stage[b], bytes, false);
                 e = cudaStreamEndCapture(c->stream, &graph);
@@ -1006,7 +1051,9 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         e = cudaGraphLaunch(it->second.exec, c->stream);
     } else {
         const int64_t before = c->launches;  // timed launches count themselves; the total is set below
-        e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing);
+        e = c->timing ? cudaSuccess : ensure_side(c, p.groups.size());
+        if (e == cudaSuccess)
+            e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing);
         c->launches = before;
     }
     if (e == cudaSuccess)
@@ -1137,6 +1184,10 @@ void prenom_destroy(prenom_ctx *c)
         if (c->stage_ev[i])
             cudaEventDestroy(c->stage_ev[i]);
     }
+    for (cudaStream_t s2 : c->side)
+        cudaStreamDestroy(s2);
+    for (cudaEvent_t ev2 : c->side_ev)
+        cudaEventDestroy(ev2);
     cudaFree(c->d_work);
     cudaFree(c->split_buf);
     cudaFree(c->query_buf);
