@@ -752,7 +752,6 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
     return PRENOM_OK;
 }
 
-// Enqueues one batched step on the context's stream (also used under capture).
 // Side streams and events for the concurrent groups of a batched step (created
 // outside any graph capture).
 cudaError_t ensure_side(prenom_ctx *c, size_t n_groups)
@@ -774,6 +773,7 @@ cudaError_t ensure_side(prenom_ctx *c, size_t n_groups)
     return e;
 }
 
+// Enqueues one batched step on the context's stream (also used under capture).
 // group_ev (optional, groups + 1 events): recorded before each group's launches
 // and after the last group's, so that group gi's device time lies between
 // group_ev[gi] and group_ev[gi + 1].
