@@ -15,7 +15,9 @@ collective: objects are independent).
 
 Timing: after the set-up (autotuner, graph capture) W warm-up steps, K timed
 steps from initialisation (`from_init`), untimed training until every object has
-taken TRAIN_AGE steps, then the K headline steps.
+taken TRAIN_AGE steps, the autotuner once more on the trained objects
+(PRENOM_FLAG_RETUNE; set-up, it changes no state), 3 warm-up steps, then the K
+headline steps.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on the same workload instead (bounded ray sample per step, extrapolated).
@@ -52,11 +54,12 @@ CATEGORY_ARCHS = [(17, 32, 1), (16, 32, 2), (19, 64, 3), (18, 64, 2), (14, 16, 1
                   (15, 16, 2), (19, 64, 3)]
 BATCHED_OBJECTS, BATCHED_NR, BATCHED_SEED, GRID_RES = 32, 48, 7, 64
 # The headline steps are timed once every object has taken at least this many
-# training steps.  From initialisation the free-space samples still carry
-# gradients; within the first 50-100 steps their densities fall below zero, the
-# ReLU stops their gradients and the scatter skips the zero addends (measured:
-# the 32-object step takes 4.44 ms at steps 5-10, 3.92 ms at 105-110, 3.86 ms at
-# 405-410).  The rate from initialisation is reported beside it.
+# training steps.  From initialisation every sample carries gradient; within the
+# first 50-100 steps the surfaces turn opaque, the transmittance of the samples
+# behind them underflows to zero, their gradients are exactly zero and the
+# scatter skips their addends (measured: the 32-object step takes 4.44 ms at
+# steps 5-10, 3.92 ms at 105-110, 3.86 ms at 405-410).  The rate from
+# initialisation is reported beside it.
 TRAIN_AGE = 100
 WORKLOAD = ("32 heterogeneous objects in one batched step: category-table architectures (L=16 F=2, T 2^14..2^19, "
             "res 16..2048, MLP width 16/32/64 with 1-3 hidden layers), 256..8192 rays per object x 48 samples "
@@ -642,7 +645,8 @@ def _single_compare(pkg, ctx, stream, prec, rank, steps, warmup):
         f = lambda i: ctx.train_step([dev[i % len(dev)]], opts, loss)  # noqa: E731
         ms0 = _time(stream, f, steps, warmup)  # from initialisation
         _time(stream, f, 0, max(3, TRAIN_AGE - warmup - steps))
-        ms = _time(stream, f, steps, 0)
+        ctx.autotune([dev[0]], pkg.make_opts(nc=NC, nr=NR, lr=1e-2, flags=pkg.PRENOM_FLAG_RETUNE))
+        ms = _time(stream, f, steps, 3)
         out[form] = {"value": N_RAYS * NR * steps / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms / steps,
                      "from_init": {"value": N_RAYS * NR * steps / (ms0 / 1e3), "ms_per_step": ms0 / steps}}
         ctx.enable_timing(True)  # per-kernel device times of the same steps, launched directly
@@ -944,9 +948,15 @@ def run_ours(args):
         t = torch.tensor([ms_init], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_init = t.item()
-    # untimed training up to TRAIN_AGE steps per object (at least 3 more warm-up steps)
+    # untimed training up to TRAIN_AGE steps per object (at least 3 more warm-up steps),
+    # then the autotuner again on the trained objects (set-up: its calls leave them as
+    # they were) and 3 warm-up steps on the graphs it captured
     age = args.warmup + args.steps + max(3, TRAIN_AGE - args.warmup - args.steps)
     _time(stream, step, 0, age - args.warmup - args.steps)
+    ctx.autotune(sets[0], pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2,
+                                        flags=form_flags | pkg.PRENOM_FLAG_RETUNE))
+    _time(stream, step, 0, 3)
+    age += 3
     tuning = ctx.tuning_report().strip()
     cap0 = ctx.capture_count()
     launches0 = ctx.launch_count()
@@ -1090,8 +1100,9 @@ def run_ours(args):
                            "objects": BATCHED_OBJECTS, "rays_per_step": n_rays, "samples_per_ray": BATCHED_NR,
                            "samples_per_step": n_smp, "params": n_params, "autotuner": tuning,
                            "groups": groups,
-                           "timed_region": "autotuner calls and graph captures ran in set-up (prenom_autotune); "
-                                           "none inside the timed steps (checked by the library's counters)",
+                           "timed_region": "autotuner calls and graph captures ran in set-up (prenom_autotune, "
+                                           "at the objects' first step and again after TRAIN_AGE steps); none "
+                                           "inside the timed steps (checked by the library's counters)",
                            "training_steps_before_timing": age,
                            "parallelism": (f"{world} ranks, each its own copy of the 32 objects" if world > 1
                                            else "1 GPU, 32 objects"),

@@ -83,6 +83,8 @@ extern "C" {
                                        form (sampling+encoding, the MLP kernel, hash scatter as three
                                        kernels); the results agree to rounding order */
 #define PRENOM_FLAG_SPLIT 16u       /* training: always the split form (not tuned) */
+#define PRENOM_FLAG_RETUNE 32u      /* prenom_autotune: forget the step's earlier tuning and tune it again
+                                       (ignored by the training calls) */
 
 /* prenom_get_state / prenom_set_state: which buffer */
 #define PRENOM_STATE_THETA 0
@@ -217,7 +219,9 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * of two; one untimed call, then three rounds over the candidates, each
  * candidate judged by its median) try the
  * split form and several work-chunk sizes (tiles per CTA) and keep the
- * fastest; afterwards, on a non-default stream and with timing off, the whole
+ * fastest; a step of several groups on a non-default stream then times its
+ * groups one after the other and concurrently on side streams (three rounds
+ * each) and keeps the faster; afterwards, on a non-default stream and with timing off, the whole
  * step is captured once per exact signature as a CUDA graph and replayed
  * (PRENOM_FLAG_NO_GRAPH disables the graph); a context keeps at most 64
  * graphs, evicting the least recently used after waiting for its stream.
@@ -374,7 +378,8 @@ PRENOM_API int prenom_canonical_yaw(prenom_ctx *ctx, int32_t obj, const float *p
 /* Runs, ahead of training, what the first calls of prenom_train_step() with
  * these batches and options would otherwise do inside the training loop: the
  * autotuner's calls for every group signature not yet tuned (one untimed call,
- * then three rounds over the candidates), run as gradient-only steps -- no Adam
+ * then three rounds over the candidates) and for the step-level choice between
+ * its groups one after the other and forked, run as gradient-only steps -- no Adam
  * update, no change of theta, Adam moments or step counts; the gradients they
  * accumulate and any 16-bit overflow flag they raise are cleared afterwards --
  * and the capture of the step's CUDA graph for both staging buffers (when
@@ -382,7 +387,12 @@ PRENOM_API int prenom_canonical_yaw(prenom_ctx *ctx, int32_t obj, const float *p
  * The next prenom_train_step() calls with batches of the same signature then
  * replay without tuning or capturing.  Same arguments and checks as
  * prenom_train_step(); batches with PRENOM_FLAG_CHECK_FINITE are neither tuned
- * nor captured, so the call does nothing for them.  Waits for the stream. */
+ * nor captured, so the call does nothing for them.  With PRENOM_FLAG_RETUNE
+ * the step's groups and its step-level choice are tuned again (the relative
+ * costs of the candidates move as objects train: once surfaces turn opaque
+ * the samples behind them carry no gradient and the scatter has less to do),
+ * and graphs are
+ * captured for the new choices.  Waits for the stream. */
 PRENOM_API int prenom_autotune(prenom_ctx *ctx, const prenom_ray_batch *batches, int32_t n_batches,
                                const prenom_train_opts *opts);
 
@@ -407,8 +417,11 @@ PRENOM_API int prenom_timing_report(prenom_ctx *ctx, char *buf, size_t cap);
  * lanes, c2 c3 the fused kernel in one wave / with 16 tiles per CTA, c4 c5 as
  * c0 c1 with the sampling-encoding kernel at 3 instead of 4 CTAs per SM; with
  * PRENOM_FLAG_FUSED: the fused kernel in one wave / 16 / 8 / 4 tiles per CTA;
- * PRENOM_FLAG_SPLIT: c0 untuned).  buf: host, cap bytes, NUL-terminated,
- * truncated to fit. */
+ * PRENOM_FLAG_SPLIT: c0 untuned); then one line per step signature of
+ * several groups: "step <its groups' signatures>:" with the whole-step times
+ * of each round one after the other ("serial=") and forked ("forked="), and
+ * the choice after "=>".  buf: host, cap bytes, NUL-terminated, truncated to
+ * fit. */
 PRENOM_API int prenom_tuning_report(prenom_ctx *ctx, char *buf, size_t cap);
 
 /* Zeroes an object's gradient buffer (stream-ordered). */

@@ -29,6 +29,7 @@ PRENOM_FLAG_CHECK_FINITE = 2
 PRENOM_FLAG_NO_GRAPH = 4
 PRENOM_FLAG_FUSED = 8
 PRENOM_FLAG_SPLIT = 16
+PRENOM_FLAG_RETUNE = 32
 
 PRENOM_STATE_THETA = 0
 PRENOM_STATE_GRAD = 1

@@ -91,6 +91,10 @@ struct prenom_ctx {
     std::map<std::string, std::vector<float>> tune_ms;  // measured ms per candidate
     std::map<std::string, int> tune_best;               // chosen candidate index
     std::set<std::string> tune_warm;                    // signatures past their untimed first call
+    // per step signature (its groups' signatures): whole-step times one after the
+    // other and forked ([2 q] and [2 q + 1] of round q), and the choice
+    std::map<std::string, std::vector<float>> fork_ms;
+    std::map<std::string, bool> fork_best;
     // split form of mixed-precision training: the buffers its kernels hand over
     unsigned char *split_buf = nullptr;
     size_t split_cap = 0;
@@ -777,8 +781,9 @@ cudaError_t ensure_side(prenom_ctx *c, size_t n_groups)
 // group_ev (optional, groups + 1 events): recorded before each group's launches
 // and after the last group's, so that group gi's device time lies between
 // group_ev[gi] and group_ev[gi + 1].
+// allow_fork: the groups after the first may run on the side streams.
 cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *stage, size_t bytes, bool timed,
-                            cudaEvent_t *group_ev = nullptr)
+                            cudaEvent_t *group_ev = nullptr, bool allow_fork = false)
 {
     const size_t items_bytes = p.items.size() * sizeof(WorkItem);
     const WorkItem *d_items = reinterpret_cast<const WorkItem *>(c->d_work);
@@ -787,9 +792,10 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     if (e == cudaSuccess)
         e = launch_zero_losses(d_items, (int)p.items.size(), c->stream);
     const WorkItem unused{};
-    // groups run concurrently (their buffers are disjoint), except when kernels or
-    // groups are timed one by one; the side streams exist already (ensure_side)
-    const bool fork = !timed && !group_ev && c->stream != nullptr && p.groups.size() > 1 &&
+    // groups run concurrently (their buffers are disjoint) where the step's tuning
+    // chose it, never when kernels or groups are timed one by one; the side streams
+    // exist already (ensure_side)
+    const bool fork = allow_fork && !timed && !group_ev && c->stream != nullptr && p.groups.size() > 1 &&
                       c->side.size() + 1 >= p.groups.size() && c->side_ev.size() >= p.groups.size();
     const size_t n_side = fork ? p.groups.size() - 1 : 0;
     if (fork && e == cudaSuccess)
@@ -900,6 +906,22 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         g.whole_runs = cand_whole_runs(cand, split_allowed);
         g.enc_per_sm = cand_enc_per_sm(cand, split_allowed);
     }
+    // once its groups are tuned, a step of several groups on a stream of its own
+    // chooses between running them one after the other and concurrently on side
+    // streams (forking fills the SMs one group's kernels leave idle, but the groups
+    // then share L2): whole steps timed both ways, three rounds, the median counts
+    std::string skey;
+    int fork_trial = -1;  // this call times the step one after the other (0) or forked (1)
+    bool allow_fork = false;
+    if (!tuning && p.groups.size() > 1 && c->stream != nullptr && !c->timing) {
+        for (const std::string &k : gkeys)
+            skey += k + "|";
+        auto fb = c->fork_best.find(skey);
+        if (fb != c->fork_best.end())
+            allow_fork = fb->second;
+        else
+            fork_trial = (int)(c->fork_ms[skey].size() % 2);
+    }
     // buffers of the split groups (planned before any staging or capture)
     size_t split_need = 0;
     for (const Group &g : p.groups)
@@ -952,10 +974,47 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
     if (!p.adam_scal.empty())
         memcpy(c->h_stage[b] + items_bytes, p.adam_scal.data(), p.adam_scal.size() * sizeof(float2));
 
-    const bool use_graph = !tuning && !c->timing && c->stream != nullptr && !(op.flags & PRENOM_FLAG_NO_GRAPH);
+    const bool use_graph = !tuning && fork_trial < 0 && !c->timing && c->stream != nullptr &&
+                           !(op.flags & PRENOM_FLAG_NO_GRAPH);
     if (capture_only && !use_graph)
         return PRENOM_OK;  // nothing to capture (still tuning, timing on, legacy stream or graphs off)
-    if (tuning) {
+    if (fork_trial >= 0) {
+        c->n_tune_calls++;
+        cudaEvent_t t0 = nullptr, t1 = nullptr;
+        e = ensure_side(c, p.groups.size());
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&t0);
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&t1);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(t0, c->stream);
+        if (e == cudaSuccess)
+            e = enqueue_batched(c, p, c->h_stage[b], bytes, false, nullptr, fork_trial == 1);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(t1, c->stream);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, t0, t1);
+        if (t0)
+            cudaEventDestroy(t0);
+        if (t1)
+            cudaEventDestroy(t1);
+        if (e != cudaSuccess)
+            return cuda_fail(c, e, "autotuner step");
+        std::vector<float> &v = c->fork_ms[skey];
+        v.push_back(ms);
+        if ((int)v.size() == 2 * kTuneRounds) {
+            float r[2][kTuneRounds];
+            for (int q = 0; q < kTuneRounds; ++q)
+                for (int f = 0; f < 2; ++f)
+                    r[f][q] = v[(size_t)2 * q + f];
+            std::sort(r[0], r[0] + kTuneRounds);
+            std::sort(r[1], r[1] + kTuneRounds);
+            c->fork_best[skey] = r[1][kTuneRounds / 2] < r[0][kTuneRounds / 2];
+        }
+    } else if (tuning) {
         c->n_tune_calls++;
         // each group is charged its own launches' device time, so that groups of one
         // step settle on candidates of their own
@@ -1004,6 +1063,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         }
     } else if (use_graph) {
         std::string key = std::to_string(b) + ":" + std::to_string(bytes) + ":" + std::to_string(p.adam_grid);
+        key += allow_fork ? "F" : "S";
         for (const Group &g : p.groups)
             key += "|" + group_key(g) + "/" + std::to_string(g.grid) + (g.split ? (g.whole_runs ? "w" : "s") : "f") +
                    std::to_string(g.enc_per_sm);
@@ -1020,7 +1080,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
             if (e == cudaSuccess)
                 e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const cudaError_t e1 = enqueue_batched(c, p, c->h_stage[b], bytes, false);
+                const cudaError_t e1 = enqueue_batched(c, p, c->h_stage[b], bytes, false, nullptr, allow_fork);
                 e = cudaStreamEndCapture(c->stream, &graph);
                 if (e == cudaSuccess)
                     e = e1;
@@ -1053,7 +1113,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         const int64_t before = c->launches;  // timed launches count themselves; the total is set below
         e = c->timing ? cudaSuccess : ensure_side(c, p.groups.size());
         if (e == cudaSuccess)
-            e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing);
+            e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing, nullptr, allow_fork);
         c->launches = before;
     }
     if (e == cudaSuccess)
@@ -1076,12 +1136,15 @@ bool tuning_pending(prenom_ctx *c, const prenom_ray_batch *batches, int n, const
     if (*rc)
         return false;
     const bool split_allowed = !(op.flags & PRENOM_FLAG_FUSED);
-    if (split_allowed && (op.flags & PRENOM_FLAG_SPLIT))
-        return false;
-    for (const Group &g : p.groups)
-        if (!c->tune_best.count(tune_key(g) + (split_allowed ? "/s" : "/f")))
+    const bool split_forced = split_allowed && (op.flags & PRENOM_FLAG_SPLIT);  // groups untuned
+    std::string skey;
+    for (const Group &g : p.groups) {
+        const std::string k = tune_key(g) + (split_allowed ? "/s" : "/f");
+        if (!split_forced && !c->tune_best.count(k))
             return true;
-    return false;
+        skey += k + "|";
+    }
+    return p.groups.size() > 1 && c->stream != nullptr && !c->timing && !c->fork_best.count(skey);
 }
 
 }  // namespace
@@ -1432,10 +1495,26 @@ int prenom_autotune(prenom_ctx *c, const prenom_ray_batch *batches, int32_t n_ba
             return rc;
     if (n_batches == 0 || (op->flags & PRENOM_FLAG_CHECK_FINITE))
         return PRENOM_OK;  // such steps are neither tuned nor captured
+    if (op->flags & PRENOM_FLAG_RETUNE) {  // forget the step's groups' and its step-level choices
+        Plan p;
+        if ((rc = plan_batched(c, batches, n_batches, *op, nullptr, p)))
+            return rc;
+        const bool split_allowed = !(op->flags & PRENOM_FLAG_FUSED);
+        std::string skey;
+        for (const Group &g : p.groups) {
+            const std::string k = tune_key(g) + (split_allowed ? "/s" : "/f");
+            c->tune_best.erase(k);
+            c->tune_ms.erase(k);
+            skey += k + "|";
+        }
+        c->fork_best.erase(skey);
+        c->fork_ms.erase(skey);
+    }
     // the autotuner's calls, as gradient-only steps (no Adam, no step count)
     prenom_train_opts t = *op;
     t.flags |= PRENOM_FLAG_NO_ADAM;
-    for (int i = 0; i < 2 + kTuneNSplit * kTuneRounds; ++i) {
+    t.flags &= ~PRENOM_FLAG_RETUNE;
+    for (int i = 0; i < 2 + (kTuneNSplit + 2) * kTuneRounds; ++i) {
         const bool pending = tuning_pending(c, batches, n_batches, t, &rc);
         if (rc)
             return rc;
@@ -1878,6 +1957,18 @@ int prenom_tuning_report(prenom_ctx *c, char *buf, size_t cap)
             snprintf(tmp, sizeof(tmp), " -> c%d", it->second);
             r += tmp;
         }
+        r += "\n";
+    }
+    for (const auto &kv : c->fork_ms) {  // steps of several groups: one after the other / forked
+        r += "step " + kv.first + ":";
+        char tmp[48];
+        for (size_t k = 0; k < kv.second.size(); ++k) {
+            snprintf(tmp, sizeof(tmp), " %s=%.4f", k % 2 ? "forked" : "serial", kv.second[k]);
+            r += tmp;
+        }
+        auto it = c->fork_best.find(kv.first);
+        if (it != c->fork_best.end())
+            r += it->second ? " => forked" : " => serial";
         r += "\n";
     }
     const size_t n = std::min(cap - 1, r.size());

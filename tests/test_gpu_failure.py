@@ -8,7 +8,7 @@
   reports PRENOM_ERR_NONFINITE and takes no Adam step;
 * prenom_autotune: the autotuner's calls and the graph captures happen there,
   leave the object's state unchanged, and none happen in the training loop
-  that follows.
+  that follows; with PRENOM_FLAG_RETUNE it tunes the step again, likewise.
 """
 
 import numpy as np
@@ -168,6 +168,22 @@ def test_autotune_leaves_the_state_and_the_loop_neither_tunes_nor_captures(pkg):
     assert ctx.capture_count() == (captures, tune_calls)
     assert all(ctx.get_step(o) == 6 for o in objs)
     assert np.all(np.isfinite(loss.cpu().numpy()))
+    # tuning again on the trained objects: more autotuner calls, the state unchanged,
+    # and the loop that follows neither tunes nor captures
+    before = [_state(ctx, pkg, o) for o in objs]
+    ctx.autotune(batches, pkg.make_opts(nc=32, nr=32, lr=1e-2, flags=pkg.PRENOM_FLAG_RETUNE))
+    ctx.sync()
+    captures2, tune_calls2 = ctx.capture_count()
+    assert tune_calls2 > tune_calls and captures2 >= captures
+    for o, st in zip(objs, before):
+        for x, y in zip(st, _state(ctx, pkg, o)):
+            np.testing.assert_array_equal(x, y)
+        assert ctx.get_step(o) == 6
+    for _ in range(3):
+        ctx.train_step(batches, opts, loss)
+    ctx.sync()
+    assert ctx.capture_count() == (captures2, tune_calls2)
+    assert all(ctx.get_step(o) == 9 for o in objs)
     ctx.close()
 
 
