@@ -117,42 +117,52 @@ __global__ void __launch_bounds__(kThreads, MINB)
             for (int a = 0; a < 3; ++a)
                 pos_two_float(rf[RF_O + a], tk, rf[RF_D + a], ph[a], pl[a]);
             const int row = meta.z + k;  // row of the tile image
-            uint32_t pk[4];  // one 16-byte chunk (4 levels) of the row, stored as soon as it is complete
+            // levels in chunks of four, one 16-byte chunk of the row each (stored as soon as
+            // it is complete); the chunk loop is not unrolled, which keeps the kernel's code
+            // within the instruction cache (the unrolled 16-level body stalled its warps on
+            // instruction fetch)
+#pragma unroll 1
+            for (int l4 = 0; l4 < kMaxLevels; l4 += 4) {
+                if (l4 >= NL && (FMT == 2 || l4 / 4 >= INP / 8))
+                    break;
+                uint32_t pk[4];
 #pragma unroll
-            for (int l = 0; l < kMaxLevels; ++l) {
-                pk[l & 3] = 0u;
-                if (l < NL) {
-                    const LevelDesc lv = od.lv[l];
-                    Corners cs;
-                    level_corners(lv, od.tmask, ph, pl, cs);
-                    float2 f[8];
-                    if constexpr (F16) {  // the tables' BF16 copy
+                for (int j = 0; j < 4; ++j) {
+                    const int l = l4 + j;
+                    pk[j] = 0u;
+                    if (l < NL) {
+                        const LevelDesc lv = od.lv[l];
+                        Corners cs;
+                        level_corners(lv, od.tmask, ph, pl, cs);
+                        float2 f[8];
+                        if constexpr (F16) {  // the tables' BF16 copy
 #pragma unroll
-                        for (int c = 0; c < 8; c += 2)
-                            gather_pair16(od.feat16 + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
-                    } else {
+                            for (int c = 0; c < 8; c += 2)
+                                gather_pair16(od.feat16 + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                        } else {
 #pragma unroll
-                        for (int c = 0; c < 8; c += 2)
-                            gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
-                    }
-                    float e0 = 0.f, e1 = 0.f;
+                            for (int c = 0; c < 8; c += 2)
+                                gather_pair(tab + lv.offset, cs.idx[c], cs.idx[c + 1], f[c], f[c + 1]);
+                        }
+                        float e0 = 0.f, e1 = 0.f;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        e0 = fmaf(cs.wt[c], f[c].x, e0);
-                        e1 = fmaf(cs.wt[c], f[c].y, e1);
-                    }
-                    if constexpr (FMT == 2) {  // consecutive lanes write consecutive samples of a feature
-                        float *fimg = reinterpret_cast<float *>(img);
-                        fimg[(2 * l) * kSplitTile + row] = e0;
-                        fimg[(2 * l + 1) * kSplitTile + row] = e1;
-                    } else {
-                        pk[l & 3] = Hf::pack2(e0 * enc, e1 * enc);
+                        for (int c = 0; c < 8; ++c) {
+                            e0 = fmaf(cs.wt[c], f[c].x, e0);
+                            e1 = fmaf(cs.wt[c], f[c].y, e1);
+                        }
+                        if constexpr (FMT == 2) {  // consecutive lanes write consecutive samples of a feature
+                            float *fimg = reinterpret_cast<float *>(img);
+                            fimg[(2 * l) * kSplitTile + row] = e0;
+                            fimg[(2 * l + 1) * kSplitTile + row] = e1;
+                        } else {
+                            pk[j] = Hf::pack2(e0 * enc, e1 * enc);
+                        }
                     }
                 }
                 // row of the tile image: INP / 8 chunks of 8 columns (16 bytes each)
                 if constexpr (FMT != 2) {
-                    if ((l & 3) == 3 && l / 4 < INP / 8)
-                        __stcs(reinterpret_cast<uint4 *>(img + il_off(row, 8 * (l / 4), INP)),
+                    if (l4 / 4 < INP / 8)
+                        __stcs(reinterpret_cast<uint4 *>(img + il_off(row, 2 * l4, INP)),
                                make_uint4(pk[0], pk[1], pk[2], pk[3]));
                 }
             }
