@@ -412,7 +412,11 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
     }
 }
 
-template <int W, int IN, bool BF16>
+// SPLIT: the split form's MLP kernel (sampling, encoding and the scatter run in
+// kernels of their own), instantiated apart from the fused kernel so that its
+// code holds only what it runs (fewer instruction-fetch stalls); it must match
+// wl.split, and each item's hand-over buffers must be present.
+template <int W, int IN, bool BF16, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 2)
     fused_tc_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
@@ -441,14 +445,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     // dW_out on the tensor cores, for every object of the launch (H <= hmax): only in
     // split mode, where the kernel gathers nothing and the wider dO buffer does not
     // take L1 cache away from the hash gathers
-    const bool tc_dwo = wl.split && tc_dw_out<W, IN>(hmax);
-    const int doa_cols = L::doa_cols(hmax, wl.split);
+    const bool tc_dwo = SPLIT && tc_dw_out<W, IN>(hmax);
+    const int doa_cols = L::doa_cols(hmax, SPLIT);
     float *OT = reinterpret_cast<float *>(DOA + kTcTile * doa_cols * 2);  // [4][SP] raw outputs
     float *dOT = OT + 4 * SP;                         // [4][SP] dL/d(raw outputs), unscaled
     float *ts = dOT + 4 * SP;
     float *rayf = ts + SP;
     float *cdfs = rayf + MAXR * kRayStride;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cdfs + L::scratch_floats(wl.split != 0));
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(cdfs + L::scratch_floats(SPLIT));
     uint64_t *mbar = reinterpret_cast<uint64_t *>(tmem_slot + 2);
 
     // buffers with padding that is never written again: W_0 (columns IN..INP),
@@ -534,7 +538,12 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int ns = nrt * nr;
         const int kdw = (ns + 15) >> 4;  // 16-sample slices of the weight-gradient products
         // ---- ray data and sampling (FP32, shared with the FP32 kernel)
-        const bool split = bd.sp_x != nullptr;  // sampling, encoding and scatter run in kernels of their own
+        constexpr bool split = SPLIT;  // sampling, encoding and scatter run in kernels of their own
+        if (SPLIT != (bd.sp_x != nullptr)) {  // a work list at odds with the variant: nothing is touched
+            if (tid == 0 && bd.status)
+                atomicExch(bd.status, 1);
+            break;  // block-uniform (cur is shared)
+        }
         if (split && pre_t == t) {  // prefetched during the previous tile
             if (tid < kChunks)
                 reinterpret_cast<uint4 *>(XA)[tid] = px0;
@@ -868,11 +877,11 @@ template <int W, int IN, bool BF16>
 cudaError_t launch_tc_t(const WorkItem &one, const WorkList &wl, int grid, cudaStream_t st)
 {
     const size_t smem = TcLayout<W, IN>::bytes(wl.items ? wl.hmax : one.od.H, wl.split != 0);
-    cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel<W, IN, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto kern = wl.split ? fused_tc_kernel<W, IN, BF16, true> : fused_tc_kernel<W, IN, BF16, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    fused_tc_kernel<W, IN, BF16><<<grid, kThreads, smem, st>>>(one, wl);
+    kern<<<grid, kThreads, smem, st>>>(one, wl);
     return cudaGetLastError();
 }
 
@@ -885,7 +894,8 @@ int tc_occupancy_t(int H, bool split)
 {
     cudaFuncAttributes fa{};
     int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0;
-    if (cudaFuncGetAttributes(&fa, fused_tc_kernel<W, IN, BF16>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+    auto kern = split ? fused_tc_kernel<W, IN, BF16, true> : fused_tc_kernel<W, IN, BF16, false>;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
