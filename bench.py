@@ -929,6 +929,12 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     ctx = pkg.Context(seed=rank, stream=stream)
     prec = args.precision
+    if args.workload == "single":  # the single full-size object alone (for profiling it), one JSON line
+        if world == 1:
+            out = _single_compare(pkg, ctx, stream, prec, rank, args.steps, args.warmup)
+            print(json.dumps({"impl": "ours", "workload": "single", **out}), flush=True)
+        ctx.close()
+        return
     form_flags = {"auto": 0, "fused": pkg.PRENOM_FLAG_FUSED, "split": pkg.PRENOM_FLAG_SPLIT}[args.form]
     bopts = pkg.make_opts(nc=BATCHED_NR, nr=BATCHED_NR, lr=1e-2, flags=form_flags)
     specs = batched_specs()
@@ -1137,6 +1143,9 @@ def main():
     ap.add_argument("--precision", default="fp16", choices=list(PRECISION))
     ap.add_argument("--form", default="auto", choices=["auto", "fused", "split"],
                     help="the autotuner's choice per group, the fused kernel, or the three-kernel split form")
+    ap.add_argument("--workload", default="batched", choices=["batched", "single"],
+                    help="batched: the 32-object headline with its comparisons; single: only the single "
+                         "full-size object (FP16 and FP32), for profiling its kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

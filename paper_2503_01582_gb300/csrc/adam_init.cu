@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
     const int64_t total = a.chunk_start[a.n_segs];
     int cur = -1;       // segment whose updated hash entries amax covers (block-uniform)
     float amax = 0.f;   // this thread's max |theta| over them
+    bool skip = false;  // the current segment's step is dropped
+    float lr_c1 = 0.f, inv_c2 = 0.f;
     for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
         int lo = 0, hi = a.n_segs - 1;
         while (lo < hi) {  // last segment whose first chunk is <= c
@@ -51,24 +53,26 @@ __global__ void __launch_bounds__(256) adam_kernel(const AdamArgs a)
                 hi = mid - 1;
         }
         const AdamSeg &sg = a.seg[lo];
-        if (lo != cur) {
+        if (lo != cur) {  // the segment's flag and factors, read once per segment, not once per chunk
             if (cur >= 0 && a.seg[cur].absmax)
                 warp_absmax_to(a.seg[cur].absmax, amax);
             cur = lo;
             amax = 0.f;
+            skip = sg.skip && *sg.skip;
+            lr_c1 = sg.lr_c1;
+            inv_c2 = sg.inv_c2;
+            if (sg.scal) {
+                const float2 s = *sg.scal;
+                lr_c1 = s.x;
+                inv_c2 = s.y;
+            }
         }
         const int64_t base = (c - a.chunk_start[lo]) * kAdamChunk;
         const int64_t end = min(base + (int64_t)kAdamChunk, sg.n);
-        if (sg.skip && *sg.skip) {  // a 16-bit gradient overflowed: drop the step, clear the gradients
+        if (skip) {  // a 16-bit gradient overflowed: drop the step, clear the gradients
             for (int64_t i = base + threadIdx.x; i < end; i += blockDim.x)
                 sg.grad[i] = 0.f;
             continue;
-        }
-        float lr_c1 = sg.lr_c1, inv_c2 = sg.inv_c2;
-        if (sg.scal) {
-            const float2 s = *sg.scal;
-            lr_c1 = s.x;
-            inv_c2 = s.y;
         }
         const int64_t n_hash = sg.absmax ? sg.n_hash : 0;  // a multiple of 4: quadruples never straddle it
         // one quadruple of each array per thread (a 1024-float chunk is one pass of 256 threads)
