@@ -139,59 +139,119 @@ def batched_totals(specs):
     return samples, sum(sp["rays"] for sp in specs)
 
 
+# NVML clock-event reason bits (nvml.h, nvmlClocksEventReason*) that the record names
+NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """SM clock and clock-event (throttle) reasons during the timed region.
+
+    Read through NVML (the driver's libnvidia-ml, queried every 5 ms from a
+    thread) where it loads, so that a timed region of a few tens of ms still
+    holds several samples; else nvidia-smi every 100 ms.  Only reads: no
+    setting of the GPU is changed."""
 
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.005
 
     def __init__(self, gpu_id: str):
         self.gpu_id = gpu_id
         self.proc = None
+        self.rows = []  # (wall time, sm MHz, max sm MHz, [reason names])
+        self.source = None
+
+    def _nvml_start(self) -> bool:
+        import ctypes
+        import threading
+
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return False
+            get_sm, get_max = lib.nvmlDeviceGetClockInfo, lib.nvmlDeviceGetMaxClockInfo
+            try:
+                get_reasons = lib.nvmlDeviceGetCurrentClocksEventReasons
+            except AttributeError:  # the older name of the same query
+                get_reasons = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            handle = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByUUID(self.gpu_id.encode(), ctypes.byref(handle)) != 0:
+                lib.nvmlShutdown()
+                return False
+        except Exception:
+            return False
+        self._lib, self._handle = lib, handle
+        self._stop = threading.Event()
+
+        def loop():
+            sm, mx, reasons = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self._stop.is_set():
+                ok = (get_sm(handle, 1, ctypes.byref(sm)) == 0 and  # 1: NVML_CLOCK_SM
+                      get_max(handle, 1, ctypes.byref(mx)) == 0 and get_reasons(handle, ctypes.byref(reasons)) == 0)
+                if ok:
+                    names = [nm for bit, nm in NVML_REASONS.items() if reasons.value & bit]
+                    self.rows.append((time.time(), float(sm.value), float(mx.value), names))
+                time.sleep(self.PERIOD_S)
+
+        self._thread = threading.Thread(target=loop, daemon=True)
+        self._thread.start()
+        self.source = "nvml, every 5 ms"
+        return True
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except Exception:
-            self.proc = None
+        if not self._nvml_start():
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                     "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.source = "nvidia-smi, every 100 ms"
+            except Exception:
+                self.proc = None
         time.sleep(0.3)
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
+        time.sleep(0.25)
+        if self.source and self.source.startswith("nvml"):
+            self._stop.set()
+            self._thread.join(timeout=5)
+            self._lib.nvmlShutdown()
         if self.proc is not None:
-            time.sleep(0.25)
             self.proc.terminate()
             try:
                 out, _ = self.proc.communicate(timeout=5)
             except Exception:
                 self.proc.kill()
                 out = ""
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+            self.rows = self.parse_smi(out.splitlines())
         return False
+
+    @staticmethod
+    def parse_smi(lines):
+        import datetime
+
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
+        for ln in lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]),
+                             [nm for nm, v in zip(names, parts[5:9]) if v.lower() == "active"]))
+            except ValueError:
+                continue
+        return rows
 
     def mark(self, t0: float, t1: float):
         """Wall-clock bounds of the timed region (samples outside it are dropped)."""
         self.window = (t0, t1)
 
     def summary(self):
-        import datetime
-
-        rows = []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
+        rows = list(self.rows)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         t0, t1 = getattr(self, "window", (rows[0][0], rows[-1][0]))
@@ -200,10 +260,10 @@ class ClockSampler:
         if not inside:  # region shorter than the sampling period: nearest sample
             mid = 0.5 * (t0 + t1)
             inside = [min(rows, key=lambda r: abs(r[0] - mid))]
-            note = "nearest sample (timed region shorter than the 100 ms sampling period)"
-        reasons = sorted({nm for r in inside for nm, v in zip(names, r[3]) if v.lower() == "active"})
+            note = "nearest sample (timed region shorter than the sampling period)"
+        reasons = sorted({nm for r in inside for nm in r[3]})
         return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
-                "reasons": reasons, "samples": len(inside), "note": note}
+                "reasons": reasons, "samples": len(inside), "note": note, "source": self.source}
 
 
 def gpu_identifier(dev: int) -> str:

@@ -262,7 +262,7 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4])
 }
 
 constexpr int kTcTile = 128;       // samples per tile = MMA M
-constexpr int kTcCols = 256;       // TMEM columns allocated per CTA
+constexpr int kTcCols = 256;       // most TMEM columns a CTA allocates
 constexpr int kDaCols = 64;        // columns of the dH buffer (dW MMAs use M = 64)
 
 // dW_out (4 x W) on the tensor cores, at dw_col(H): for W = 64 as its transpose
@@ -277,10 +277,18 @@ __host__ __device__ __forceinline__ constexpr bool tc_dwo_transposed()
     return W == kDaCols;
 }
 
+// TMEM columns of R0, the region that holds in turn a forward layer (W), the
+// output layer (16), a backward product (W) and dX (the padded encoding width).
+template <int W, int IN>
+__host__ __device__ __forceinline__ constexpr int tc_r0()
+{
+    return W > (IN < 16 ? 16 : IN) ? W : (IN < 16 ? 16 : IN);
+}
+
 template <int W, int IN>
 __host__ __device__ __forceinline__ bool tc_dw_out(int H)
 {
-    return 64 + (IN < 16 ? 16 : IN) + (H - 1) * W + (tc_dwo_transposed<W>() ? 16 : W) <= kTcCols;
+    return tc_r0<W, IN>() + (IN < 16 ? 16 : IN) + (H - 1) * W + (tc_dwo_transposed<W>() ? 16 : W) <= kTcCols;
 }
 
 template <int W, int IN>
@@ -308,14 +316,39 @@ struct TcLayout {
     }
 };
 
-// TMEM column of each accumulator region: R0 (64 columns) holds the current
-// forward layer, the output layer, then the current backward product; the dW
-// accumulators follow (M = 64 layout: row m in lane 32*(m/16) + m%16).
+// TMEM column of each accumulator region: R0 (tc_r0 columns) holds the
+// current forward layer, the output layer, then the current backward product
+// and dX; the dW accumulators follow (M = 64 layout: row m in lane
+// 32*(m/16) + m%16).
 template <int W, int IN>
-__device__ __forceinline__ uint32_t dw_col(int layer)
+__host__ __device__ __forceinline__ uint32_t dw_col(int layer)
 {
     constexpr int INP = TcLayout<W, IN>::INP;
-    return layer == 0 ? 64u : (uint32_t)(64 + INP + (layer - 1) * W);
+    constexpr int R0 = tc_r0<W, IN>();
+    return layer == 0 ? (uint32_t)R0 : (uint32_t)(R0 + INP + (layer - 1) * W);
+}
+
+// TMEM columns a CTA allocates for a launch whose deepest MLP has H hidden
+// layers: R0, the dW accumulators and, where it is formed on the tensor cores,
+// dW_out, rounded up to a power of two (at least 32).  A width-16 or width-32
+// MLP of at most two hidden layers needs 128, so up to four CTAs share an SM's
+// 512 columns; a width-64 MLP needs 256.
+template <int W, int IN>
+__host__ __device__ __forceinline__ int tc_cols(int H, bool split)
+{
+    const int need = (int)dw_col<W, IN>(H) + ((split && tc_dw_out<W, IN>(H)) ? (tc_dwo_transposed<W>() ? 16 : W) : 0);
+    int cols = 32;
+    while (cols < need)
+        cols *= 2;
+    return cols;
+}
+
+// Resident CTAs per SM that the split form's MLP kernel budgets its registers
+// for: three for widths up to 32 (80 registers a thread), two otherwise.
+template <int W, bool SPLIT>
+__host__ __device__ __forceinline__ constexpr int tc_min_blocks()
+{
+    return (SPLIT && W <= 32) ? 3 : 2;
 }
 
 
@@ -417,7 +450,7 @@ __device__ __forceinline__ void tc_flush_object(const ObjDesc &od, const BatchDe
 // code holds only what it runs (fewer instruction-fetch stalls); it must match
 // wl.split, and each item's hand-over buffers must be present.
 template <int W, int IN, bool BF16, bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, tc_min_blocks<W, SPLIT>())
     fused_tc_kernel(const __grid_constant__ WorkItem one, const WorkList wl)
 {
     using L = TcLayout<W, IN>;
@@ -470,9 +503,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    const uint32_t ncols = (uint32_t)tc_cols<W, IN>(hmax, SPLIT);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
-                     "r"(kTcCols));
+                     "r"(ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_sync();
@@ -870,7 +904,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         tc_flush_object<W, IN>(cur.od, cur.bd, lane_base, !first_dw, tc_dwo, dwo_acc, loss_acc, inv_scale, inv_enc);
     tc_sync();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
 template <int W, int IN, bool BF16>
@@ -885,10 +919,12 @@ cudaError_t launch_tc_t(const WorkItem &one, const WorkList &wl, int grid, cudaS
     return cudaGetLastError();
 }
 
-// Resident CTAs per SM of a kernel variant: two when two CTAs' dynamic and
-// static shared memory (each with the per-block reservation) and registers fit
-// the SM, else one; never more, since each CTA holds kTcCols of the SM's 512
-// TMEM columns.  0 when a device query fails.
+// Resident CTAs per SM of a kernel variant for a launch whose deepest MLP has
+// H hidden layers: as many as the SM's shared memory (each CTA's dynamic and
+// static shared memory with the per-block reservation), its registers and its
+// 512 TMEM columns hold (at least one, at most four).  A CTA holds its TMEM
+// columns for its whole life, so a count the columns did not bound would leave
+// the surplus CTAs waiting in their allocation.  0 when a device query fails.
 template <int W, int IN, bool BF16>
 int tc_occupancy_t(int H, bool split)
 {
@@ -902,7 +938,9 @@ int tc_occupancy_t(int H, bool split)
         return 0;
     const size_t per_cta = TcLayout<W, IN>::bytes(H, split) + fa.sharedSizeBytes + (size_t)reserved;
     const long long regs_cta = (long long)((fa.numRegs + 7) / 8 * 8) * kThreads;
-    return (2 * per_cta <= (size_t)smem_sm && 2 * regs_cta <= regs_sm) ? 2 : 1;
+    const long long by_smem = (long long)smem_sm / (long long)per_cta, by_regs = regs_sm / regs_cta;
+    const long long by_tmem = 512 / tc_cols<W, IN>(H, split);
+    return (int)std::max(1LL, std::min(std::min(by_smem, by_regs), std::min(by_tmem, 4LL)));
 }
 
 template <bool BF16>

@@ -93,3 +93,24 @@ def test_oracle_refuses_arrays_of_the_wrong_size(orc):
         orc.batch(a, theta[:-1], grid, rays, 8, 8, u=u, c_rand=cr)
     with pytest.raises(ValueError):
         orc.sample_ray(grid, rays["o"][0], rays["d"][0], 8, 16, 1e-4, u[0])
+
+
+def test_clock_record_window_and_reasons(bench):
+    """The clock record keeps the samples inside the timed region, takes their
+    median SM clock and names every reason seen; with none inside it falls back
+    to the nearest sample."""
+    lines = [f"2026/12/04 10:00:00.{ms:03d}, {mhz}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {cap}"
+             for ms, mhz, cap in [(100, 1900, "Not Active"), (200, 2070, "Active"), (300, 2070, "Not Active"),
+                                  (400, 1500, "Not Active")]]
+    c = bench.ClockSampler("GPU-test")
+    c.rows = c.parse_smi(lines)
+    assert [r[3] for r in c.rows] == [[], ["sw_power_cap"], [], []]
+    t = [r[0] for r in c.rows]
+    c.mark(t[0] + 0.05, t[2] + 0.01)  # the samples at .200 and .300
+    rec = c.summary()
+    assert rec["samples"] == 2 and rec["sm_mhz"] == 2070.0 and rec["reasons"] == ["sw_power_cap"]
+    c.mark(t[3] + 0.01, t[3] + 0.02)  # after the last sample: the nearest one
+    rec = c.summary()
+    assert rec["samples"] == 1 and rec["sm_mhz"] == 1500.0 and "nearest" in rec["note"]
+    assert set(bench.NVML_REASONS.values()) == {"sw_power_cap", "hw_slowdown", "sw_thermal_slowdown",
+                                                "hw_thermal_slowdown"}
