@@ -584,6 +584,10 @@ struct Plan {
     std::vector<float2> adam_scal;  // (lr_c1, inv_c2) per touched object
     AdamArgs adam{};                // constant across steps (factors read from device)
     int adam_grid = 0;
+    // per group: its objects' segments of `adam` (indices into touched) and their
+    // parameter count; a forked step runs each group's Adam on the group's stream
+    std::vector<std::vector<int>> group_segs;
+    std::vector<int64_t> group_params;
     ScaleList scales{};
 };
 
@@ -722,6 +726,20 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
     for (int i = 0; i < n; ++i)
         if (std::find(p.touched.begin(), p.touched.end(), batches[i].obj) == p.touched.end())
             p.touched.push_back(batches[i].obj);
+    for (const Group &g : p.groups) {  // an object's batches all fall in one group (its architecture's)
+        std::vector<int> segs;
+        int64_t params = 0;
+        for (int j = g.first; j < g.first + g.count; ++j) {
+            const int32_t obj = batches[order[j]].obj;
+            const int s = (int)(std::find(p.touched.begin(), p.touched.end(), obj) - p.touched.begin());
+            if (std::find(segs.begin(), segs.end(), s) == segs.end()) {
+                segs.push_back(s);
+                params += c->objs[obj].n;
+            }
+        }
+        p.group_segs.push_back(segs);
+        p.group_params.push_back(params);
+    }
     if ((int)p.touched.size() > kMaxAdamSegs)
         return fail(c, PRENOM_ERR_INVALID_ARG, "a batched step updates at most %d objects", kMaxAdamSegs);
     if (!(op.flags & PRENOM_FLAG_NO_ADAM)) {
@@ -761,10 +779,11 @@ int plan_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const pr
 cudaError_t ensure_side(prenom_ctx *c, size_t n_groups)
 {
     const size_t n_side = n_groups > 1 ? n_groups - 1 : 0;
-    cudaError_t e = cudaSuccess;
+    int least = 0, greatest = 0;  // greatest is the numerically lowest
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     while (e == cudaSuccess && c->side.size() < n_side) {
-        cudaStream_t s2 = nullptr;
-        e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+        cudaStream_t s2 = nullptr;  // side stream i at the i-th greatest priority
+        e = cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, std::min(greatest + (int)c->side.size(), least));
         if (e == cudaSuccess)
             c->side.push_back(s2);
     }
@@ -781,9 +800,14 @@ cudaError_t ensure_side(prenom_ctx *c, size_t n_groups)
 // group_ev (optional, groups + 1 events): recorded before each group's launches
 // and after the last group's, so that group gi's device time lies between
 // group_ev[gi] and group_ev[gi + 1].
-// allow_fork: the groups after the first may run on the side streams.
+// allow_fork: the groups may run concurrently: the group with the most
+// parameters on the side stream of the greatest priority, the next on the next
+// side stream, the one with the fewest on the context's stream; each forked
+// group's Adam follows its kernels on its own stream, so that the Adam passes
+// (bound by HBM) overlap the other groups' kernels (bound by L1, L2 and
+// latency) instead of waiting for the join.  *forked: whether it forked.
 cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *stage, size_t bytes, bool timed,
-                            cudaEvent_t *group_ev = nullptr, bool allow_fork = false)
+                            cudaEvent_t *group_ev = nullptr, bool allow_fork = false, bool *forked = nullptr)
 {
     const size_t items_bytes = p.items.size() * sizeof(WorkItem);
     const WorkItem *d_items = reinterpret_cast<const WorkItem *>(c->d_work);
@@ -798,13 +822,27 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     const bool fork = allow_fork && !timed && !group_ev && c->stream != nullptr && p.groups.size() > 1 &&
                       c->side.size() + 1 >= p.groups.size() && c->side_ev.size() >= p.groups.size();
     const size_t n_side = fork ? p.groups.size() - 1 : 0;
+    if (forked)
+        *forked = fork;
+    // stream slot of each group when forked: by parameter count, largest first
+    std::vector<size_t> slot(p.groups.size());
+    {
+        std::vector<size_t> rank(p.groups.size());
+        for (size_t gi = 0; gi < rank.size(); ++gi)
+            rank[gi] = gi;
+        std::stable_sort(rank.begin(), rank.end(),
+                         [&](size_t a, size_t b) { return p.group_params[a] > p.group_params[b]; });
+        for (size_t r = 0; r < rank.size(); ++r)
+            slot[rank[r]] = r;
+    }
+    const bool group_adam = fork && p.adam_grid > 0;
     if (fork && e == cudaSuccess)
         e = cudaEventRecord(c->side_ev[0], c->stream);
     for (size_t i = 0; i < n_side && e == cudaSuccess; ++i)
         e = cudaStreamWaitEvent(c->side[i], c->side_ev[0], 0);
     for (size_t gi = 0; gi < p.groups.size(); ++gi) {
         const Group &g = p.groups[gi];
-        cudaStream_t st = (fork && gi > 0) ? c->side[gi - 1] : c->stream;
+        cudaStream_t st = (fork && slot[gi] < n_side) ? c->side[slot[gi]] : c->stream;
         if (group_ev && e == cudaSuccess)
             e = cudaEventRecord(group_ev[gi], c->stream);
         if (e != cudaSuccess || g.total_tiles == 0)
@@ -838,6 +876,26 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
                 timed_end(c, PRENOM_KERNEL_SCATTER, ev);
         }
     }
+    // each forked group's Adam, on the group's stream after its kernels (also for a
+    // group without tiles: its objects still take their step)
+    for (size_t gi = 0; gi < p.groups.size() && group_adam && e == cudaSuccess; ++gi) {
+        cudaStream_t st = slot[gi] < n_side ? c->side[slot[gi]] : c->stream;
+        if (!p.group_segs[gi].empty()) {
+            AdamArgs a{};
+            a.beta1 = p.adam.beta1;
+            a.beta2 = p.adam.beta2;
+            a.eps = p.adam.eps;
+            a.n_segs = (int32_t)p.group_segs[gi].size();
+            a.chunk_start[0] = 0;
+            for (int k = 0; k < a.n_segs; ++k) {
+                const int sidx = p.group_segs[gi][k];
+                a.seg[k] = p.adam.seg[sidx];
+                a.seg[k].scal = d_scal + sidx;
+                a.chunk_start[k + 1] = a.chunk_start[k] + (a.seg[k].n + kAdamChunk - 1) / kAdamChunk;
+            }
+            e = launch_adam(a, (int)std::min<int64_t>(a.chunk_start[a.n_segs], (int64_t)c->n_sm * 16), st);
+        }
+    }
     c->cur_group = -1;
     // the join (also after an error, so that a capture in progress ends with every stream joined)
     for (size_t i = 0; i < n_side && i + 1 < c->side_ev.size(); ++i) {
@@ -850,28 +908,37 @@ cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *s
     if (group_ev && e == cudaSuccess)
         e = cudaEventRecord(group_ev[p.groups.size()], c->stream);
     if (e == cudaSuccess && p.adam_grid > 0) {
-        AdamArgs a = p.adam;
-        for (int s = 0; s < a.n_segs; ++s)
-            a.seg[s].scal = d_scal + s;
-        cudaEvent_t ev;
-        if (timed)
-            timed_begin(c, PRENOM_KERNEL_ADAM, &ev);
-        e = launch_adam(a, p.adam_grid, c->stream);
-        if (timed)
-            timed_end(c, PRENOM_KERNEL_ADAM, ev);
+        if (!group_adam) {
+            AdamArgs a = p.adam;
+            for (int s = 0; s < a.n_segs; ++s)
+                a.seg[s].scal = d_scal + s;
+            cudaEvent_t ev;
+            if (timed)
+                timed_begin(c, PRENOM_KERNEL_ADAM, &ev);
+            e = launch_adam(a, p.adam_grid, c->stream);
+            if (timed)
+                timed_end(c, PRENOM_KERNEL_ADAM, ev);
+        }
         if (e == cudaSuccess)
             e = launch_loss_scale_update_list(p.scales, c->stream);
     }
     return e;
 }
 
-int launches_of(const Plan &p)
+int launches_of(const Plan &p, bool forked)
 {
     int n = 1;  // loss reset
     for (const Group &g : p.groups)
         n += g.total_tiles > 0 ? (g.split ? 3 : 1) : 0;
-    if (p.adam_grid > 0)
-        n += 1 + (p.scales.n > 0);
+    if (p.adam_grid > 0) {
+        int adam = 1;
+        if (forked) {  // one Adam per group with objects
+            adam = 0;
+            for (size_t gi = 0; gi < p.groups.size(); ++gi)
+                adam += p.group_segs[gi].empty() ? 0 : 1;
+        }
+        n += adam + (p.scales.n > 0);
+    }
     return n;
 }
 
@@ -978,6 +1045,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
                            !(op.flags & PRENOM_FLAG_NO_GRAPH);
     if (capture_only && !use_graph)
         return PRENOM_OK;  // nothing to capture (still tuning, timing on, legacy stream or graphs off)
+    bool forked = false;  // the step's groups run concurrently (and each its own Adam)
     if (fork_trial >= 0) {
         c->n_tune_calls++;
         cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -989,7 +1057,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         if (e == cudaSuccess)
             e = cudaEventRecord(t0, c->stream);
         if (e == cudaSuccess)
-            e = enqueue_batched(c, p, c->h_stage[b], bytes, false, nullptr, fork_trial == 1);
+            e = enqueue_batched(c, p, c->h_stage[b], bytes, false, nullptr, fork_trial == 1, &forked);
         if (e == cudaSuccess)
             e = cudaEventRecord(t1, c->stream);
         if (e == cudaSuccess)
@@ -1080,13 +1148,13 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
             if (e == cudaSuccess)
                 e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                const cudaError_t e1 = enqueue_batched(c, p, c->h_stage[b], bytes, false, nullptr, allow_fork);
+                const cudaError_t e1 = enqueue_batched(c, p, c->h_stage[b], bytes, false, nullptr, allow_fork, &forked);
                 e = cudaStreamEndCapture(c->stream, &graph);
                 if (e == cudaSuccess)
                     e = e1;
             }
-            if (e == cudaSuccess)
-                e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e == cudaSuccess)  // the forked groups keep their side streams' priorities
+                e = cudaGraphInstantiateWithFlags(&exec, graph, cudaGraphInstantiateFlagUseNodePriority);
             if (graph)
                 cudaGraphDestroy(graph);
             if (e != cudaSuccess)
@@ -1104,6 +1172,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
             it = c->graphs.emplace(key, prenom_ctx::CachedGraph{exec, 0}).first;
         }
         it->second.last_use = ++c->graph_tick;
+        forked = allow_fork && p.groups.size() > 1;  // as when the graph was captured (side streams made first)
         if (capture_only) {  // kept for the step that will use this staging buffer
             c->stage_idx ^= 1;
             return PRENOM_OK;
@@ -1113,7 +1182,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         const int64_t before = c->launches;  // timed launches count themselves; the total is set below
         e = c->timing ? cudaSuccess : ensure_side(c, p.groups.size());
         if (e == cudaSuccess)
-            e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing, nullptr, allow_fork);
+            e = enqueue_batched(c, p, c->h_stage[b], bytes, c->timing, nullptr, allow_fork, &forked);
         c->launches = before;
     }
     if (e == cudaSuccess)
@@ -1121,7 +1190,7 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
     if (e != cudaSuccess)
         return cuda_fail(c, e, "batched step");
     c->stage_idx ^= 1;
-    c->launches += launches_of(p);
+    c->launches += launches_of(p, forked);
     if (!(op.flags & PRENOM_FLAG_NO_ADAM))
         for (int32_t id : p.touched)
             c->objs[id].step += 1;
