@@ -55,6 +55,18 @@ extern "C" {
 #define PRENOM_ERR_CUDA (-3)           /* a CUDA runtime call or a launch failed */
 #define PRENOM_ERR_DEVICE_TIMEOUT (-4) /* a bounded device-side wait gave up */
 #define PRENOM_ERR_NONFINITE (-5)      /* a checked loss was NaN or infinite */
+#define PRENOM_ERR_DEVICE_BOUNDS (-6)  /* debug build: an index left its array (access skipped) */
+
+/* Debug build.  The same sources compiled with -DPRENOM_DEBUG_BOUNDS make
+ * libprenom_debug.so (paper_2503_01582_gb300.build.build(debug_bounds=True)),
+ * with the same entry points.  Its kernels test every hash-table corner index
+ * against its level's entry count, every prior-grid voxel index against R^3
+ * and every ray index against the batch's ray count where the index is
+ * formed; an index outside skips its access and marks the context's device
+ * status word, which prenom_sync() reports as PRENOM_ERR_DEVICE_BOUNDS.  No
+ * check traps or faults.  The regular library has no such tests: its indices
+ * are in range by construction (positions clamped to the unit cube, cells to
+ * the level's resolution, hashes masked to T - 1, rays counted from the batch). */
 
 #define PRENOM_PRECISION_FP32 0 /* FP32 features, MLP and accumulation */
 /* Mixed precision: the MLP runs on the tensor cores with 16-bit operands and
@@ -427,7 +439,10 @@ PRENOM_API int prenom_tuning_report(prenom_ctx *ctx, char *buf, size_t cap);
 /* Zeroes an object's gradient buffer (stream-ordered). */
 PRENOM_API int prenom_zero_grads(prenom_ctx *ctx, int32_t obj);
 
-/* Waits for the context's stream; returns the first asynchronous error. */
+/* Waits for the context's stream; returns the first asynchronous error, or
+ * PRENOM_ERR_DEVICE_TIMEOUT (a bounded device wait gave up) or
+ * PRENOM_ERR_DEVICE_BOUNDS (debug build only) from the device status word,
+ * which it then clears. */
 PRENOM_API int prenom_sync(prenom_ctx *ctx);
 
 /* Kernel timing: when enabled, every library launch is bracketed by CUDA

@@ -10,7 +10,10 @@ import ctypes as C
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libprenom.so")
+# PRENOM_DEBUG_BOUNDS=1 in the environment selects the debug build (bounds-checked
+# kernels, same entry points), which must have been built.
+DEBUG_LIB_PATH = os.path.join(_PKG, "libprenom_debug.so")
+LIB_PATH = DEBUG_LIB_PATH if os.environ.get("PRENOM_DEBUG_BOUNDS") == "1" else os.path.join(_PKG, "libprenom.so")
 
 PRENOM_OK = 0
 PRENOM_ERR_INVALID_ARG = -1
@@ -18,6 +21,7 @@ PRENOM_ERR_OOM = -2
 PRENOM_ERR_CUDA = -3
 PRENOM_ERR_DEVICE_TIMEOUT = -4
 PRENOM_ERR_NONFINITE = -5
+PRENOM_ERR_DEVICE_BOUNDS = -6
 
 PRENOM_PRECISION_FP32 = 0
 PRENOM_PRECISION_FP16 = 1

@@ -147,8 +147,44 @@ __device__ __forceinline__ void level_corners(const LevelDesc &lv, uint32_t tmas
     }
 }
 
+// Bounds checks of a PRENOM_DEBUG_BOUNDS build.  The regular build has none: its
+// indices are in range by construction (positions clamped to the unit cube,
+// cells to [0, N_l - 1], hashes masked to T - 1, rays and tiles counted from the
+// batch).  The debug build tests each table, grid and ray index where it is
+// formed; an index outside its array sets kStatusBounds in the status word
+// (prenom_sync then returns PRENOM_ERR_DEVICE_BOUNDS) and its access is
+// skipped, never a trap or a fault.
+#ifdef PRENOM_DEBUG_BOUNDS
+__device__ __forceinline__ bool bounds_ok(bool ok, int32_t *status)
+{
+    if (!ok && status)
+        atomicOr(status, kStatusBounds);
+    return ok;
+}
+
+// Each corner must address an entry of its level: (N_l + 1)^3 entries when dense,
+// T when hashed.  An entry outside is replaced by entry 0 with weight 0.
+__device__ __forceinline__ void check_corners(const LevelDesc &lv, uint32_t tmask, Corners &cs, int32_t *status)
+{
+    const uint32_t n1 = (uint32_t)lv.res + 1u;
+    const uint32_t n = lv.dense ? n1 * n1 * n1 : tmask + 1u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (!bounds_ok(cs.idx[c] < n, status)) {
+            cs.idx[c] = 0u;
+            cs.wt[c] = 0.f;
+        }
+}
+#define PRENOM_CHECK_CORNERS(lv, tmask, cs, status) check_corners(lv, tmask, cs, status)
+#define PRENOM_BOUNDS_OK(cond, status) bounds_ok((cond), (status))
+#else
+#define PRENOM_CHECK_CORNERS(lv, tmask, cs, status) ((void)0)
+#define PRENOM_BOUNDS_OK(cond, status) true
+#endif
+
 // Prior density at x: trilinear over voxel centres, g = x R - 1/2 clamped to [0, R-1].
-__device__ __forceinline__ float prior_lookup(const float *__restrict__ grid, int R, float x, float y, float z)
+__device__ __forceinline__ float prior_lookup(const float *__restrict__ grid, int R, float x, float y, float z,
+                                              int32_t *status = nullptr)
 {
     const float rf = (float)R;
     const float q[3] = {x, y, z};
@@ -167,7 +203,10 @@ __device__ __forceinline__ float prior_lookup(const float *__restrict__ grid, in
     for (int corner = 0; corner < 8; ++corner) {
         const int bx = corner & 1, by = (corner >> 1) & 1, bz = (corner >> 2) & 1;
         const float wt = (bx ? w[0] : 1.f - w[0]) * (by ? w[1] : 1.f - w[1]) * (bz ? w[2] : 1.f - w[2]);
-        const float v = __ldg(grid + ((size_t)(c[2] + bz) * R + (c[1] + by)) * R + (c[0] + bx));
+        const size_t vox = ((size_t)(c[2] + bz) * R + (c[1] + by)) * R + (c[0] + bx);
+        if (!PRENOM_BOUNDS_OK(vox < (size_t)R * R * R, status))
+            continue;
+        const float v = __ldg(grid + vox);
         s += (wt == 0.f) ? 0.f : wt * v;
     }
     return s;

@@ -267,7 +267,7 @@ __device__ __forceinline__ void sample_ray_warp(const ObjDesc &od, const BatchDe
             if (hit && i < nc) {
                 const float ti = __fmaf_rn((float)i + 0.5f, delta, tn);
                 const float sig = prior_lookup(od.grid, od.R, __fmaf_rn(ti, d[0], o[0]), __fmaf_rn(ti, d[1], o[1]),
-                                               __fmaf_rn(ti, d[2], o[2]));
+                                               __fmaf_rn(ti, d[2], o[2]), bd.status);
                 tau = sig * delta;
             }
             run += tau;
@@ -365,6 +365,7 @@ __device__ __forceinline__ void encode_or_scatter(const ObjDesc &od, const Batch
         const LevelDesc lv = od.lv[l];
         Corners cs;
         level_corners(lv, od.tmask, ph, pl, cs);
+        PRENOM_CHECK_CORNERS(lv, od.tmask, cs, bd.status);
         if constexpr (!SCATTER) {
             float2 f[8];
 #pragma unroll
@@ -623,6 +624,8 @@ __device__ __forceinline__ void stage_item(const WorkItem &src, WorkItem &dst)
 // four threads load a ray in parallel and a tile pays about one memory latency.
 __device__ __forceinline__ void load_ray_fields(const BatchDesc &bd, int g, float *rf, int f)
 {
+    if (!PRENOM_BOUNDS_OK(g >= 0 && g < bd.n_rays, bd.status))
+        return;
     {
         if (f < 2) {
             const float *src = (f == 0 ? bd.o : bd.d) + (size_t)g * 3;

@@ -158,7 +158,7 @@ __device__ __forceinline__ bool mbar_poll(uint64_t *mbar, uint32_t parity, int32
             : "r"(smem_addr(mbar)), "r"(parity));
     }
     if (!done && status)
-        atomicExch(status, 1);
+        atomicOr(status, kStatusWait);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     return done != 0;
 }
@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, tc_min_blocks<W, SPLIT>())
         constexpr bool split = SPLIT;  // sampling, encoding and scatter run in kernels of their own
         if (SPLIT != (bd.sp_x != nullptr)) {  // a work list at odds with the variant: nothing is touched
             if (tid == 0 && bd.status)
-                atomicExch(bd.status, 1);
+                atomicOr(bd.status, kStatusWait);
             break;  // block-uniform (cur is shared)
         }
         if (split && pre_t == t) {  // prefetched during the previous tile
@@ -639,6 +639,7 @@ __global__ void __launch_bounds__(kThreads, tc_min_blocks<W, SPLIT>())
                     const LevelDesc lv = od.lv[l];
                     Corners cs;
                     level_corners(lv, od.tmask, ph, pl, cs);
+                    PRENOM_CHECK_CORNERS(lv, od.tmask, cs, bd.status);
                     float2 f[8];
                     if (od.feat16) {  // the tables' BF16 copy
 #pragma unroll
@@ -893,6 +894,7 @@ __global__ void __launch_bounds__(kThreads, tc_min_blocks<W, SPLIT>())
                 const LevelDesc lv = od.lv[l];
                 Corners cs;
                 level_corners(lv, od.tmask, ph, pl, cs);
+                PRENOM_CHECK_CORNERS(lv, od.tmask, cs, bd.status);
                 scatter_level_warp(gtab + lv.offset, active, cs, g[2 * j] * inv_scale, g[2 * j + 1] * inv_scale,
                                    lane);
             }

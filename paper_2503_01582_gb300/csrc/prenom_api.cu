@@ -55,7 +55,7 @@ struct prenom_ctx {
     std::vector<Object> objs;
     std::string err;
     float *scratch = nullptr;  // device float receiving losses nobody asked for
-    int32_t *status = nullptr; // device word set by a kernel whose bounded wait gave up
+    int32_t *status = nullptr; // device word: kStatusWait (a bounded wait gave up), kStatusBounds (debug build)
     bool timing = false;
     std::vector<TimedEv> pending;
     std::vector<cudaEvent_t> ev_free;
@@ -2068,6 +2068,9 @@ int prenom_sync(prenom_ctx *c)
         return cuda_fail(c, e, "status read");
     if (st != 0) {
         cudaMemset(c->status, 0, sizeof(int32_t));
+        if (st & kStatusBounds)
+            return fail(c, PRENOM_ERR_DEVICE_BOUNDS, "a bounds check of the debug build caught an index outside "
+                                                     "its array (the access was skipped)");
         return fail(c, PRENOM_ERR_DEVICE_TIMEOUT, "a kernel gave up waiting for its tensor-core work");
     }
     return PRENOM_OK;

@@ -15,6 +15,10 @@ constexpr int kMinNr = 4;       // samples per ray, lower bound (caps rays per t
 constexpr int kMaxNr = 128;
 constexpr int kMaxAdamSegs = 128;
 
+// Bits of a launch's device status word: a bounded wait gave up, or (in a
+// PRENOM_DEBUG_BOUNDS build) an index left its array and its access was skipped.
+constexpr int32_t kStatusWait = 1, kStatusBounds = 2;
+
 // Hash-grid level: resolution N_l, first entry of the level (in F-feature entries), dense flag.
 struct LevelDesc {
     int32_t res;
@@ -58,7 +62,7 @@ struct BatchDesc {
     int32_t *overflow;        // device flag set when a scaled 16-bit gradient is not finite
     const float *enc_scale;   // FP16: device power of two multiplying the encoding before its 16-bit cast
                               // (divided out of the first layer's products in FP32); NULL = 1
-    int32_t *status;          // device word: nonzero when a bounded wait gave up
+    int32_t *status;          // device word: kStatusWait / kStatusBounds bits (below), zero when all is well
     // split execution of a mixed-precision training step (all NULL otherwise):
     // the three kernels hand over these per-batch buffers
     float *sp_t;    // [n_rays][nr] sample depths

@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kThreads, 5)
             const LevelDesc lv = od.lv[l];
             Corners cs;
             level_corners(lv, od.tmask, ph, pl, cs);
+            PRENOM_CHECK_CORNERS(lv, od.tmask, cs, bd.status);
             const float2 g = active ? __ldcs(dx + l * kSplitTile + s) : make_float2(0.f, 0.f);  // read once
             scatter_level_warp<CHUNK_LOG2>(gtab + lv.offset, active, cs, g.x, g.y, lane);
         }

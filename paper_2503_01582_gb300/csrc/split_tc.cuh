@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
                         const LevelDesc lv = od.lv[l];
                         Corners cs;
                         level_corners(lv, od.tmask, ph, pl, cs);
+                        PRENOM_CHECK_CORNERS(lv, od.tmask, cs, bd.status);
                         float2 f[8];
                         if constexpr (F16) {  // the tables' BF16 copy
 #pragma unroll

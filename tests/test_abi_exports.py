@@ -29,6 +29,18 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_debug_bounds_build_exports_every_declared_symbol():
+    """The bounds-checked debug build (the same sources with PRENOM_DEBUG_BOUNDS)
+    compiles and exports the same entry points."""
+    from paper_2503_01582_gb300 import build
+
+    path = build.build(debug_bounds=True)
+    assert path.endswith("libprenom_debug.so")
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
 def test_binding_wraps_every_symbol():
     from paper_2503_01582_gb300 import _abi
 
