@@ -212,6 +212,28 @@ __device__ __forceinline__ float prior_lookup(const float *__restrict__ grid, in
     return s;
 }
 
+// Raises a kernel's dynamic shared-memory limit to all the device allows beside
+// its static shared memory.  The limit is a permission, not a reservation (each
+// launch takes what it asks for), and a limit that only grows keeps every
+// earlier launch of the kernel valid: a CUDA graph captured with a larger
+// launch (an object with more hidden layers) stays launchable after a later,
+// smaller launch of the same kernel, also where a tool relaunches graph nodes
+// one by one.
+template <typename K>
+cudaError_t allow_max_dynamic_smem(K kern)
+{
+    cudaFuncAttributes fa{};
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 // Fire-and-forget reductions into global memory.  The explicit .global state
 // space matters: a pointer read from a descriptor is otherwise a generic
 // address, and generic atomics are ordered against shared-memory traffic.

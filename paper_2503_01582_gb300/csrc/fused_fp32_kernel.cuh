@@ -202,8 +202,7 @@ cudaError_t launch_fused_t(const WorkItem &one, const WorkList &wl, int grid, cu
 {
     const int hmax = wl.items ? wl.hmax : one.od.H;
     const size_t smem = fused_fp32_smem_floats(W, IN, hmax, S) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fused_fp32_kernel<W, IN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(fused_fp32_kernel<W, IN, S>);
     if (e != cudaSuccess)
         return e;
     fused_fp32_kernel<W, IN, S><<<grid, kThreads, smem, st>>>(one, wl);

@@ -914,7 +914,7 @@ cudaError_t launch_tc_t(const WorkItem &one, const WorkList &wl, int grid, cudaS
 {
     const size_t smem = TcLayout<W, IN>::bytes(wl.items ? wl.hmax : one.od.H, wl.split != 0);
     auto kern = wl.split ? fused_tc_kernel<W, IN, BF16, true> : fused_tc_kernel<W, IN, BF16, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess)
         return e;
     kern<<<grid, kThreads, smem, st>>>(one, wl);
