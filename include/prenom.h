@@ -225,7 +225,9 @@ PRENOM_API int prenom_set_prior_grid(prenom_ctx *ctx, int32_t obj, const float *
  * width) and each group runs as ONE persistent launch over a work list
  * spanning all its objects (or, in the split form, sampling + encoding, the
  * MLP kernel and the hash scatter as three launches over the same list); one
- * Adam launch then updates every object.
+ * Adam launch then updates every object (when the step's groups run
+ * concurrently, one Adam launch per group, on the group's stream after its
+ * kernels).
  * A single batch takes the same path.  The first calls of a new group
  * signature (kernel variant, and batch and tile counts rounded down to powers
  * of two; one untimed call, then three rounds over the candidates, each
