@@ -286,7 +286,7 @@ __host__ __device__ __forceinline__ constexpr int tc_r0()
 }
 
 template <int W, int IN>
-__host__ __device__ __forceinline__ bool tc_dw_out(int H)
+__host__ __device__ __forceinline__ constexpr bool tc_dw_out(int H)
 {
     return tc_r0<W, IN>() + (IN < 16 ? 16 : IN) + (H - 1) * W + (tc_dwo_transposed<W>() ? 16 : W) <= kTcCols;
 }
@@ -477,8 +477,11 @@ __global__ void __launch_bounds__(kThreads, tc_min_blocks<W, SPLIT>())
     unsigned char *DOA = DA + L::da;
     // dW_out on the tensor cores, for every object of the launch (H <= hmax): only in
     // split mode, where the kernel gathers nothing and the wider dO buffer does not
-    // take L1 cache away from the hash gathers
-    const bool tc_dwo = SPLIT && tc_dw_out<W, IN>(hmax);
+    // take L1 cache away from the hash gathers.  Its columns fit beside the hidden
+    // layers' dW for every width and depth the library accepts, so the choice is the
+    // variant's (the CUDA-core dW_out path is compiled into the fused variant only)
+    static_assert(!SPLIT || tc_dw_out<W, IN>(kMaxHidden), "split mode forms dW_out on the tensor cores");
+    constexpr bool tc_dwo = SPLIT;
     const int doa_cols = L::doa_cols(hmax, SPLIT);
     float *OT = reinterpret_cast<float *>(DOA + kTcTile * doa_cols * 2);  // [4][SP] raw outputs
     float *dOT = OT + 4 * SP;                         // [4][SP] dL/d(raw outputs), unscaled

@@ -164,8 +164,8 @@ int check_arch(prenom_ctx *c, const prenom_arch *a)
         return fail(c, PRENOM_ERR_INVALID_ARG, "L = %d: this build supports L in {4, 8, 16}", a->L);
     if (a->width != 16 && a->width != 32 && a->width != 64)
         return fail(c, PRENOM_ERR_INVALID_ARG, "width = %d: must be 16, 32 or 64", a->width);
-    if (a->hidden < 1 || a->hidden > 3)
-        return fail(c, PRENOM_ERR_INVALID_ARG, "hidden = %d: must be 1..3", a->hidden);
+    if (a->hidden < 1 || a->hidden > kMaxHidden)
+        return fail(c, PRENOM_ERR_INVALID_ARG, "hidden = %d: must be 1..%d", a->hidden, kMaxHidden);
     if (a->log2T < 8 || a->log2T > 24)
         return fail(c, PRENOM_ERR_INVALID_ARG, "log2T = %d: must be 8..24", a->log2T);
     if (a->n_min < 2 || a->n_max < a->n_min || a->n_max > (1 << 20))

@@ -14,6 +14,7 @@ constexpr int kMaxNc = 256;     // prior probes per ray
 constexpr int kMinNr = 4;       // samples per ray, lower bound (caps rays per tile)
 constexpr int kMaxNr = 128;
 constexpr int kMaxAdamSegs = 128;
+constexpr int kMaxHidden = 3;   // hidden layers of an MLP, at most
 
 // Bits of a launch's device status word: a bounded wait gave up, or (in a
 // PRENOM_DEBUG_BOUNDS build) an index left its array and its access was skipped.
