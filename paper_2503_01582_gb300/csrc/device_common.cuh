@@ -133,7 +133,6 @@ __device__ __forceinline__ void level_corners(const LevelDesc &lv, uint32_t tmas
 #pragma unroll
     for (int a = 0; a < 3; ++a)
         cs.cell[a] = c[a];
-    const bool dense = lv.dense != 0;
     const uint32_t n1 = (uint32_t)lv.res + 1u;
 #pragma unroll
     for (int corner = 0; corner < 8; ++corner) {
@@ -142,8 +141,19 @@ __device__ __forceinline__ void level_corners(const LevelDesc &lv, uint32_t tmas
         const float wy = by ? w[1] : 1.f - w[1];
         const float wz = bz ? w[2] : 1.f - w[2];
         cs.wt[corner] = __fmul_rn(__fmul_rn(wx, wy), wz);
-        cs.idx[corner] = grid_index(dense, n1, tmask, (uint32_t)(c[0] + bx), (uint32_t)(c[1] + by),
-                                    (uint32_t)(c[2] + bz));
+    }
+    // the level's storage is uniform across the warp: one branch, one index formula
+    const uint32_t x = (uint32_t)c[0], y = (uint32_t)c[1], z = (uint32_t)c[2];
+    if (lv.dense) {
+#pragma unroll
+        for (int corner = 0; corner < 8; ++corner)
+            cs.idx[corner] = grid_index(true, n1, tmask, x + (corner & 1), y + ((corner >> 1) & 1),
+                                        z + ((corner >> 2) & 1));
+    } else {
+#pragma unroll
+        for (int corner = 0; corner < 8; ++corner)
+            cs.idx[corner] = grid_index(false, n1, tmask, x + (corner & 1), y + ((corner >> 1) & 1),
+                                        z + ((corner >> 2) & 1));
     }
 }
 
