@@ -803,9 +803,9 @@ cudaError_t ensure_side(prenom_ctx *c, size_t n_groups)
 // allow_fork: the groups may run concurrently: the group with the most
 // parameters on the side stream of the greatest priority, the next on the next
 // side stream, the one with the fewest on the context's stream; each forked
-// group's Adam follows its kernels on its own stream, so that the Adam passes
-// (bound by HBM) overlap the other groups' kernels (bound by L1, L2 and
-// latency) instead of waiting for the join.  *forked: whether it forked.
+// group's Adam follows its kernels on its own stream, so that a group's Adam
+// pass can start while other groups' kernels still run instead of waiting for
+// the join.  *forked: whether it forked.
 cudaError_t enqueue_batched(prenom_ctx *c, const Plan &p, const unsigned char *stage, size_t bytes, bool timed,
                             cudaEvent_t *group_ev = nullptr, bool allow_fork = false, bool *forked = nullptr)
 {
