@@ -82,8 +82,11 @@ def _check_blocks(a, g, want, precision, what=""):
     assert cos >= b["cos"] and l2 <= b["l2"], (what, cos, l2, names)
 
 
+# (the last: width 32 with three hidden layers, whose accumulators take 256 TMEM
+# columns where shallower width-32 MLPs take 128)
 ARCHS = [CFG1, dict(CFG1, L=16, log2T=15, n_max=512, width=64, hidden=2),
-         dict(CFG1, L=4, log2T=12, n_max=64, width=16, hidden=3), dict(CFG1, width=32, hidden=1, lambda_sigma=1e-2)]
+         dict(CFG1, L=4, log2T=12, n_max=64, width=16, hidden=3), dict(CFG1, width=32, hidden=1, lambda_sigma=1e-2),
+         dict(CFG1, width=32, hidden=3)]
 
 
 @pytest.mark.parametrize("precision", [1, 2])
