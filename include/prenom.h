@@ -97,6 +97,10 @@ extern "C" {
 #define PRENOM_FLAG_SPLIT 16u       /* training: always the split form (not tuned) */
 #define PRENOM_FLAG_RETUNE 32u      /* prenom_autotune: forget the step's earlier tuning and tune it again
                                        (ignored by the training calls) */
+#define PRENOM_FLAG_CONCURRENT 64u  /* batched steps of several groups on a non-default stream: run the
+                                       groups concurrently on side streams, each followed by the Adam pass
+                                       of its own objects, without the autotuner's trial of one after the
+                                       other against concurrently; the results are the same either way */
 
 /* prenom_get_state / prenom_set_state: which buffer */
 #define PRENOM_STATE_THETA 0

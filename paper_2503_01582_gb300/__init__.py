@@ -27,6 +27,7 @@ from ._abi import (  # noqa: F401
     PRENOM_FLAG_FUSED,
     PRENOM_FLAG_SPLIT,
     PRENOM_FLAG_RETUNE,
+    PRENOM_FLAG_CONCURRENT,
     PRENOM_FLAG_NO_ADAM,
     PRENOM_FLAG_NO_GRAPH,
     PRENOM_KERNEL_ADAM,

@@ -34,6 +34,7 @@ PRENOM_FLAG_NO_GRAPH = 4
 PRENOM_FLAG_FUSED = 8
 PRENOM_FLAG_SPLIT = 16
 PRENOM_FLAG_RETUNE = 32
+PRENOM_FLAG_CONCURRENT = 64
 
 PRENOM_STATE_THETA = 0
 PRENOM_STATE_GRAD = 1

@@ -984,7 +984,9 @@ int train_batched(prenom_ctx *c, const prenom_ray_batch *batches, int n, const p
         for (const std::string &k : gkeys)
             skey += k + "|";
         auto fb = c->fork_best.find(skey);
-        if (fb != c->fork_best.end())
+        if (op.flags & PRENOM_FLAG_CONCURRENT)  // the caller's choice: no trial
+            allow_fork = true;
+        else if (fb != c->fork_best.end())
             allow_fork = fb->second;
         else
             fork_trial = (int)(c->fork_ms[skey].size() % 2);
@@ -1213,7 +1215,8 @@ bool tuning_pending(prenom_ctx *c, const prenom_ray_batch *batches, int n, const
             return true;
         skey += k + "|";
     }
-    return p.groups.size() > 1 && c->stream != nullptr && !c->timing && !c->fork_best.count(skey);
+    return p.groups.size() > 1 && c->stream != nullptr && !c->timing && !(op.flags & PRENOM_FLAG_CONCURRENT) &&
+           !c->fork_best.count(skey);
 }
 
 }  // namespace

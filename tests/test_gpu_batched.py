@@ -147,6 +147,54 @@ def test_batched_adam_graph_replay_and_autotuner(pkg):
     ctx_s.close()
 
 
+def test_concurrent_groups_with_their_own_adam_passes(pkg):
+    """PRENOM_FLAG_CONCURRENT: the step's groups (FP32, FP16 and BF16 objects of
+    three widths) run concurrently on side streams, each followed by the Adam
+    pass over its own objects, as a captured graph from the second step on.
+    Every step against the same objects stepped one at a time from the same
+    state (the per-object copies take the batched parameters and Adam moments
+    before each step), with every object's step count advanced once."""
+    import torch
+
+    objs = _setup()
+    stream = torch.cuda.Stream()
+    ctx_b, ids_b = _make(pkg, objs, stream=stream)
+    ctx_s, ids_s = _make(pkg, objs)
+    flags = pkg.PRENOM_FLAG_SPLIT | pkg.PRENOM_FLAG_CONCURRENT  # untuned split form, no step-level trial
+    opts = pkg.make_opts(nc=32, nr=32, lr=1e-2, flags=flags)
+    opts_s = pkg.make_opts(nc=32, nr=32, lr=1e-2, flags=pkg.PRENOM_FLAG_CHECK_FINITE)
+    loss_b = torch.zeros(len(objs), device="cuda")
+    batches = [_batch(o, i) for o, i in zip(objs, ids_b)]
+    states = (pkg.PRENOM_STATE_THETA, pkg.PRENOM_STATE_ADAM_M, pkg.PRENOM_STATE_ADAM_V)
+    torch.cuda.synchronize()
+    for step in range(4):
+        if step > 0:
+            for ib, i_s in zip(ids_b, ids_s):
+                for w in states:
+                    ctx_s.set_state(i_s, w, ctx_b.get_state(ib, w))
+        with torch.cuda.stream(stream):
+            ctx_b.train_step(batches, opts, loss_b)
+        stream.synchronize()
+        lb = loss_b.cpu().numpy()
+        for k, (o, i) in enumerate(zip(objs, ids_s)):
+            loss_s = torch.zeros(1, device="cuda")
+            ctx_s.train_step([_batch(o, i)], opts_s, loss_s)
+            assert abs(lb[k] - loss_s.item()) <= 1e-4 * abs(loss_s.item()) + 1e-7, (step, k)
+            tb = ctx_b.get_state(ids_b[k]).cpu().numpy()
+            ts = ctx_s.get_state(i).cpu().numpy()
+            # Adam normalises each entry: an entry whose gradient is at rounding level may step
+            # either way (by at most lr), so compare in bulk and bound every entry by the step
+            close = np.abs(tb - ts) <= 1e-4 * np.abs(ts).max() + 1e-6
+            assert np.mean(close) > 0.99, (step, k, np.mean(close))
+            assert np.abs(tb - ts).max() <= 2 * 1e-2 * 1.01, (step, k)
+    assert ctx_b.capture_count()[0] > 0  # replayed as a captured graph
+    assert "step " not in ctx_b.tuning_report()  # no trial of one after the other against concurrently
+    for k in range(len(objs)):
+        assert ctx_b.get_step(ids_b[k]) == 4 and ctx_s.get_step(ids_s[k]) == 4
+    ctx_b.close()
+    ctx_s.close()
+
+
 def test_mixed_precision_objects_of_a_batch_against_oracle(pkg):
     """The FP16 / BF16 objects of the mixed batch above against the oracle within
     the mixed-precision bounds (loss relative, gradient cosine and rel-L2)."""
