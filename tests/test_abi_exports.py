@@ -109,3 +109,18 @@ def test_noalloc_step_refuses_bad_arguments_on_the_host():
     refused(base, base, base, opts=pkg.make_opts(lr=float("nan")), what="Adam constants")
     refused(base, base, base, opts=pkg.make_opts(escape_eps=float("inf")), what="escape_eps")
     refused(base, base, base, grid=base, res=2048, what="res")
+
+
+def test_binding_constants_match_the_header():
+    """Every numeric constant the header defines (error codes, precisions,
+    feature types, flags, state and kernel ids, the allocation-free limit) has
+    the same value in the binding."""
+    from paper_2503_01582_gb300 import _abi
+
+    src = open(os.path.join(ROOT, "include", "prenom.h")).read()
+    defs = re.findall(r"^#define (PRENOM_[A-Z0-9_]+)\s+(\(1u? << [0-9]+\)|\(?-?[0-9]+u?\)?)", src, flags=re.M)
+    assert len(defs) >= 30
+    for name, text in defs:
+        t = text.strip("()").replace("u", "")
+        value = (1 << int(t.split("<<")[1])) if "<<" in t else int(t)
+        assert getattr(_abi, name) == value, name
