@@ -57,8 +57,8 @@ BATCHED_OBJECTS, BATCHED_NR, BATCHED_SEED, GRID_RES = 32, 48, 7, 64
 # training steps.  From initialisation every sample carries gradient; within the
 # first 50-100 steps the surfaces turn opaque, the transmittance of the samples
 # behind them underflows to zero, their gradients are exactly zero and the
-# scatter skips their addends (measured: the 32-object step takes 4.44 ms at
-# steps 5-10, 3.92 ms at 105-110, 3.86 ms at 405-410).  The rate from
+# scatter skips their addends (measured: the 32-object step takes 3.67 ms over
+# the objects' steps 5-24 and 3.28 ms after their 100th).  The rate from
 # initialisation is reported beside it.
 TRAIN_AGE = 100
 WORKLOAD = ("32 heterogeneous objects in one batched step: category-table architectures (L=16 F=2, T 2^14..2^19, "
